@@ -1,0 +1,344 @@
+"""Pins of the CPU oracle against closed forms, hand derivations and invariants.
+
+Each test fixes the oracle to something other than itself: an exact
+discrete solution, a hand-solved small circuit, a conservation law, a
+symmetry, or the paper's own theorems (Lemma 1, Theorem 1).  They are chosen
+so that a dropped term, a wrong sign or a transposed index in the oracle
+fails at least one of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import pgsynth
+from pgsynth import GROUND, make_netlist, source_terminal as S
+from oracle import bounds, matrices, pwl, relax, transient
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+# ---------------------------------------------------------------- closed forms
+
+def test_single_node_rc_discrete_closed_form():
+    """One node, cap C to ground, pad G0 to Vdd, no load, v(0) != Vdd.
+    Backward Euler gives v_k - Vdd = (v_0 - Vdd) (1 + h G0 / C)^-k exactly (Eq. 2)."""
+    fx = _load("single_node_rc.json")
+    C, g0, vdd, v0, h, K = fx["C"], fx["G0"], fx["Vdd"], fx["v0"], fx["h"], fx["steps"]
+    net = make_netlist(1, [vdd], R=[(0, S(0), g0)], C=[(0, GROUND, C)])
+    V, _ = transient.transient(net, h, K, v0=np.array([v0]))
+    k = np.arange(K + 1)
+    exact = vdd + (v0 - vdd) * (1.0 + h * g0 / C) ** (-k)
+    np.testing.assert_allclose(V[:, 0], exact, rtol=0, atol=1e-14)
+    # continuous limit exp(-t G0/C): BE error at most O(h) (first-order method)
+    tau = C / g0
+    cont = vdd + (v0 - vdd) * np.exp(-k * h / tau)
+    err = np.max(np.abs(V[:, 0] - cont))
+    assert err < 0.5 * abs(v0 - vdd) * (h / tau)
+
+
+def test_single_node_bounds_closed_form():
+    """||M^-1||_inf = 1/(C/h + G0) and q = (C/h)/(C/h + G0) for one node."""
+    C, g0, h = 50e-15, 10.0, 10e-12
+    net = make_netlist(1, [1.0], R=[(0, S(0), g0)], C=[(0, GROUND, C)])
+    assert bounds.minv_inf_norm(net, h) == pytest.approx(1.0 / (C / h + g0), rel=1e-14)
+    assert bounds.step_gain(net, h) == pytest.approx((C / h) / (C / h + g0), rel=1e-14)
+
+
+def test_two_node_rc_hand_derived():
+    """Pad(G0) - node0 - R(g) - node1 with C1 and a constant load I at node 1.
+
+    KCL, backward Euler:
+      node0: G0 (v0 - Vdd) + g (v0 - v1) = 0
+      node1: g (v1 - v0) + C1 (v1 - v1p)/h + I = 0
+    Cramer's rule on the 2x2 system; DC: v0 = Vdd - I/G0, v1 = v0 - I/g."""
+    fx = _load("two_node_rc.json")
+    g0, g, C1, I, vdd, h = fx["G0"], fx["g"], fx["C1"], fx["I"], fx["Vdd"], fx["h"]
+    net = make_netlist(2, [vdd], R=[(0, S(0), g0), (0, 1, g)], C=[(1, GROUND, C1)],
+                       I=[(1, GROUND, [0.0, 1.0], [I, I])])
+    V, _ = transient.transient(net, h, 5, v0=np.array([vdd, vdd]))
+    v1p = vdd
+    for k in range(1, 6):
+        a11, a12, b1 = g0 + g, -g, g0 * vdd
+        a21, a22, b2 = -g, g + C1 / h, C1 / h * v1p - I
+        det = a11 * a22 - a12 * a21
+        v0 = (b1 * a22 - a12 * b2) / det
+        v1 = (a11 * b2 - b1 * a21) / det
+        np.testing.assert_allclose(V[k], [v0, v1], rtol=0, atol=1e-13)
+        v1p = v1
+    vdc = transient.dc_operating_point(net)
+    np.testing.assert_allclose(vdc, [vdd - I / g0, vdd - I / g0 - I / g], rtol=0, atol=1e-13)
+
+
+def test_ladder_dc_closed_form():
+    """A chain of N nodes with a pad at node 0 and a load I at the far end:
+    the whole load current flows through every segment, so
+    v_k = Vdd - I (1/G0 + sum_{j<k} 1/g_j)."""
+    rng = np.random.default_rng(7)
+    N, vdd, g0, I = 12, 1.1, 8.0, 2e-3
+    g = rng.uniform(0.5, 2.0, N - 1)
+    net = make_netlist(N, [vdd], R=[(0, S(0), g0)] + [(k, k + 1, g[k]) for k in range(N - 1)],
+                       I=[(N - 1, GROUND, [0.0], [I])])
+    v = transient.dc_operating_point(net)
+    exact = vdd - I * (1.0 / g0 + np.concatenate([[0.0], np.cumsum(1.0 / g)]))
+    np.testing.assert_allclose(v, exact, rtol=0, atol=1e-14)
+    # the node form (Eq. 12 with C = 0) solved by Gauss-Seidel agrees
+    vg, _ = relax.gs_dc(relax.NodeTopology(net), tol=1e-15)
+    np.testing.assert_allclose(vg, exact, rtol=0, atol=1e-12)
+
+
+def test_lc_tank_eigen_solution_and_energy_decay():
+    """One node, cap C to ground, inductor L from the node to Vdd (explicit i_l).
+
+    With x = (v - Vdd, i_l): (C/h + h/L) x1' = (C/h) x1 - x2, x2' = x2 + (h/L) x1',
+    a 2x2 linear recurrence x_{k+1} = T x_k solved by its eigen-decomposition.
+    Backward Euler is dissipative: the energy C x1^2/2 + L x2^2/2 must fall."""
+    fx = _load("lc_tank.json")
+    C, Lh, vdd, v0, h, K = fx["C"], fx["L"], fx["Vdd"], fx["v0"], fx["h"], fx["steps"]
+    net = make_netlist(1, [vdd], C=[(0, GROUND, C)], L=[(0, S(0), Lh)])
+    V, IL = transient.transient(net, h, K, v0=np.array([v0]), il0=np.zeros(1))
+    d = C / h + h / Lh
+    T = np.array([[C / h / d, -1.0 / d],
+                  [h / Lh * C / h / d, 1.0 - h / Lh / d]])
+    w, P = np.linalg.eig(T)
+    x0 = np.array([v0 - vdd, 0.0])
+    c = np.linalg.solve(P, x0)
+    for k in range(K + 1):
+        xk = np.real(P @ (c * w ** k))
+        np.testing.assert_allclose([V[k, 0] - vdd, IL[k, 0]], xk, rtol=0, atol=1e-12)
+    E = 0.5 * C * (V[:, 0] - vdd) ** 2 + 0.5 * Lh * IL[:, 0] ** 2
+    assert np.all(np.diff(E) < 0)
+    # and it oscillates (complex eigenvalues, |lambda| < 1)
+    assert np.all(np.abs(np.imag(w)) > 0) and np.all(np.abs(w) < 1)
+
+
+# ---------------------------------------------------------------- invariants
+
+def _small(cfg, **kw):
+    return pgsynth.CONFIGS[cfg](**kw)
+
+
+def test_lemma1_system_matrix_is_spd_m_matrix():
+    """Lemma 1: M = C/h + G + hL is symmetric, weakly diagonally dominant with a
+    positive diagonal and non-positive off-diagonals, hence SPD; M^-1 >= 0."""
+    for net in (_small(0, nx=9, ny=7), _small(2, nx=8, ny=6)):
+        mats = matrices.nodal_matrices(net)
+        M = mats.system_matrix(net.meta["h"]).toarray()
+        assert np.allclose(M, M.T, rtol=0, atol=0)
+        off = M - np.diag(np.diag(M))
+        assert np.all(off <= 0)
+        assert np.all(np.diag(M) > 0)
+        assert np.all(M.sum(axis=1) >= -1e-12 * np.abs(np.diag(M)))
+        np.linalg.cholesky(M)
+        assert np.all(np.linalg.inv(M) >= -1e-12)
+
+
+def test_row_sums_equal_grounded_conductance():
+    """M 1 collects only the branches that leave the trivial nodes: C/h, the
+    pad conductances and h/L of pad inductors (computed here from the element
+    lists, not from the assembly)."""
+    net = _small(2, nx=10, ny=6)
+    h = net.meta["h"]
+    mats = matrices.nodal_matrices(net)
+    rs = mats.system_matrix(h) @ np.ones(net.n_nodes)
+    expect = np.zeros(net.n_nodes)
+    for a, b, c in zip(net.c_a, net.c_b, net.c_val):
+        expect[a] += c / h
+    for a, b, g in zip(net.r_a, net.r_b, net.r_g):
+        if b < 0:
+            expect[a] += g
+    for a, b, l in zip(net.l_a, net.l_b, net.l_val):
+        if b < 0:
+            expect[a] += h / l
+    np.testing.assert_allclose(rs, expect, rtol=1e-12, atol=1e-12)
+
+
+def test_zero_load_keeps_vdd():
+    """With every load at zero and v(0) = Vdd, v = Vdd at every node and step
+    (G 1 = 0 and the pads balance), for RC and RLC."""
+    for cfg in (0, 2):
+        net = _small(cfg, nx=11, ny=9)
+        net.i_v[:] = 0.0
+        V, IL = transient.transient(net, net.meta["h"], 15)
+        np.testing.assert_allclose(V, 1.0, rtol=0, atol=1e-13)
+        if IL.size:
+            np.testing.assert_allclose(IL, 0.0, rtol=0, atol=1e-12)
+
+
+def test_global_charge_balance():
+    """Summing KCL over all trivial nodes: the current delivered by the sources
+    through pad resistors and pad inductors equals the load current plus the
+    capacitor charging current, at every step (RC and RLC)."""
+    for cfg in (0, 2):
+        net = _small(cfg, nx=10, ny=8)
+        h = net.meta["h"]
+        V, IL = transient.transient(net, h, 60)
+        Cn = np.zeros(net.n_nodes)
+        np.add.at(Cn, net.c_a, net.c_val)
+        pad_r = net.r_b < 0
+        pad_l = net.l_b < 0
+        for s in range(1, V.shape[0]):
+            v = V[s]
+            supply = np.sum(net.r_g[pad_r] * (1.0 - v[net.r_a[pad_r]]))
+            supply -= np.sum(IL[s][pad_l])  # inductor current a->b flows into the source
+            load = np.sum(pwl.pwl_values(net.i_ptr, net.i_t, net.i_v, s * h))
+            charge = np.sum(Cn * (V[s] - V[s - 1]) / h)
+            assert supply == pytest.approx(load + charge, rel=1e-9, abs=1e-12)
+
+
+def test_mirror_symmetry():
+    """Uniform segments, one central pad and a uniform load on a square grid:
+    the voltage map is invariant under x<->y and x -> nx-1-x (catches transposed
+    or shifted indices)."""
+    n = 9
+    ids = np.arange(n * n).reshape(n, n)
+    R = [(int(ids[y, x]), int(ids[y, x + 1]), 1.0) for y in range(n) for x in range(n - 1)]
+    R += [(int(ids[y, x]), int(ids[y + 1, x]), 1.0) for y in range(n - 1) for x in range(n)]
+    R += [(int(ids[4, 4]), S(0), 10.0)]
+    C = [(int(i), GROUND, 20e-15) for i in range(n * n)]
+    I = [(int(i), GROUND, [0.0, 50e-12], [0.0, 1e-4]) for i in range(n * n)]
+    net = make_netlist(n * n, [1.0], R=R, C=C, I=I)
+    V, _ = transient.transient(net, 5e-12, 20)
+    for s in (5, 20):
+        m = V[s].reshape(n, n)
+        np.testing.assert_allclose(m, m.T, atol=1e-14)
+        np.testing.assert_allclose(m, m[:, ::-1], atol=1e-14)
+        assert m[4, 4] == m.max()
+
+
+def test_three_level_form_matches_explicit_form():
+    """Eq. 11 (three-level, no inductor state) and Eq. 10 (explicit i_l) are the
+    same recurrence once v(0), v(1) agree: trajectories match to rounding."""
+    net = _small(2, nx=9, ny=8)
+    h = net.meta["h"]
+    V, _ = transient.transient(net, h, 80)
+    for s, v in transient.simulate_three_level(net, h, 80, V[0], V[1]):
+        np.testing.assert_allclose(v, V[s], rtol=0, atol=1e-11)
+
+
+def test_large_inductance_limit_is_rc():
+    """L -> infinity removes the inductive paths: an RLC grid with huge L
+    reproduces the RC grid without those inductors."""
+    net = _small(2, nx=8, ny=7)
+    h = net.meta["h"]
+    big = pgsynth.Netlist(**{**net.__dict__, "l_val": np.full_like(net.l_val, 1e9)})
+    rc = pgsynth.Netlist(**{**net.__dict__, "l_a": net.l_a[:0], "l_b": net.l_b[:0],
+                            "l_val": net.l_val[:0]})
+    V1, _ = transient.transient(big, h, 40)
+    V2, _ = transient.transient(rc, h, 40)
+    np.testing.assert_allclose(V1, V2, rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------- Theorem 1
+
+@pytest.mark.parametrize("omega", [1.0, 1.6])
+def test_gauss_seidel_converges_to_direct_rc(omega):
+    """Theorem 1 / Eq. 17: the node-by-node GS/SOR of Algorithm 1 converges to
+    the unique solution of the BE system (RC)."""
+    net = _small(0, nx=7, ny=6)
+    h = net.meta["h"]
+    topo = relax.NodeTopology(net)
+    V, IL = transient.transient(net, h, 30)
+    for s in (10, 20, 30):
+        v, _, _ = relax.gs_step_explicit(topo, h, V[s - 1], IL[s - 1], s * h, omega=omega,
+                                         tol=1e-15)
+        np.testing.assert_allclose(v, V[s], rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("omega", [1.0, 1.5])
+def test_gauss_seidel_converges_to_direct_rlc(omega):
+    """Same for RLC, in both the explicit-i_l node form and Eq. 14."""
+    net = _small(2, nx=6, ny=5)
+    h = net.meta["h"]
+    topo = relax.NodeTopology(net)
+    V, IL = transient.transient(net, h, 40)
+    for s in (15, 30, 40):
+        v, il, _ = relax.gs_step_explicit(topo, h, V[s - 1], IL[s - 1], s * h, omega=omega,
+                                          tol=1e-15)
+        np.testing.assert_allclose(v, V[s], rtol=0, atol=1e-11)
+        np.testing.assert_allclose(il, IL[s], rtol=1e-9, atol=1e-12)
+        v3, _ = relax.gs_step_three_level(topo, h, V[s - 1], V[s - 2], s * h, omega=omega,
+                                          tol=1e-15)
+        np.testing.assert_allclose(v3, V[s], rtol=0, atol=1e-10)
+
+
+# ---------------------------------------------------------------- PWL and solver
+
+def test_pwl_vectorised_matches_loop_and_breakpoints():
+    rng = np.random.default_rng(3)
+    ptr, ts, vs = [0], [], []
+    for _ in range(200):
+        k = int(rng.integers(1, 6))
+        t = np.sort(rng.uniform(0, 1e-9, k))
+        if k > 2 and rng.random() < 0.3:
+            t[1] = t[2]                       # a zero-length segment (a jump)
+        ts.extend(t); vs.extend(rng.uniform(-1e-3, 1e-3, k)); ptr.append(len(ts))
+    ptr, ts, vs = np.array(ptr), np.array(ts), np.array(vs)
+    for t in np.concatenate([rng.uniform(-1e-10, 1.2e-9, 50), ts[:40]]):
+        got = pwl.pwl_values(ptr, ts, vs, t)
+        for e in range(len(ptr) - 1):
+            assert got[e] == pwl.pwl_scalar(ts[ptr[e]:ptr[e + 1]], vs[ptr[e]:ptr[e + 1]], t)
+    # triangular source: 0 before t0, the peak at t0+tr, half the peak mid-fall
+    tri = (np.array([0, 3]), np.array([1.0, 2.0, 4.0]), np.array([0.0, 5.0, 0.0]))
+    assert pwl.pwl_values(*tri, 0.5)[0] == 0.0
+    assert pwl.pwl_values(*tri, 2.0)[0] == 5.0
+    assert pwl.pwl_values(*tri, 3.0)[0] == 2.5
+    assert pwl.pwl_values(*tri, 1.5)[0] == 2.5
+    assert pwl.pwl_values(*tri, 9.0)[0] == 0.0
+
+
+def test_sparse_and_dense_solvers_agree():
+    net = _small(0, nx=50, ny=45)   # 2250 nodes -> sparse path
+    mats = matrices.nodal_matrices(net)
+    M = mats.system_matrix(net.meta["h"])
+    assert M.shape[0] > transient.DENSE_MAX
+    b = np.random.default_rng(1).standard_normal(M.shape[0])
+    x = transient.DirectSolver(M).solve(b)
+    np.testing.assert_allclose(M @ x, b, rtol=0, atol=1e-10)
+    xd = np.linalg.solve(M.toarray(), b)
+    np.testing.assert_allclose(x, xd, rtol=1e-10, atol=1e-13)
+
+
+# ---------------------------------------------------------------- generator
+
+def test_generator_config0_counts_and_ranges():
+    net = pgsynth.config0()
+    c = net.counts()
+    assert c["n"] == 10000 and c["p"] == 1
+    assert c["R"] == 19800 + 100          # 2*100*99 segments + 100 pads
+    assert c["C"] == 10000 and c["I"] == 2000 and c["L"] == 0
+    seg = net.r_b >= 0
+    assert net.r_g[seg].min() >= 0.5 and net.r_g[seg].max() <= 2.0
+    assert np.all(net.r_g[~seg] == 10.0)
+    pads = net.r_a[~seg]
+    assert np.all((pads % 100) % 10 == 0) and np.all((pads // 100) % 10 == 0)
+    assert 10e-15 <= net.c_val.min() and net.c_val.max() <= 100e-15
+    assert len(np.unique(net.i_a)) == 2000
+    t = net.i_t.reshape(-1, 3); v = net.i_v.reshape(-1, 3)
+    assert np.all(v[:, 0] == 0) and np.all(v[:, 2] == 0) and v[:, 1].max() <= 1e-3
+    assert np.all(np.diff(t, axis=1) >= 20e-12) and np.all(np.diff(t, axis=1) <= 100e-12)
+    assert t[:, 0].min() >= 0 and t[:, 0].max() <= 1e-9
+    # same seed, same netlist; different seed, different draw
+    assert np.array_equal(pgsynth.config0().r_g, net.r_g)
+    assert not np.array_equal(pgsynth.config0(seed=5).r_g, net.r_g)
+
+
+def test_generator_multilayer_counts():
+    nx, ny = 64, 40
+    net = pgsynth.config1(nx=nx, ny=ny)
+    c = net.counts()
+    seg = 3 * (2 * nx * ny - nx - ny)
+    vias = 2 * nx * ny
+    pads = len(range(0, nx, 32)) * len(range(0, ny, 32))
+    assert c["R"] == seg + vias + pads
+    assert c["C"] == nx * ny and c["I"] == round(0.3 * nx * ny)
+    assert np.all(net.c_a < nx * ny)                  # decaps on the bottom layer
+    assert np.all(net.r_a[net.r_b < 0] >= 2 * nx * ny)  # pads on the top layer
+    r = pgsynth.config2(nx=32, ny=32).counts()
+    assert r["L"] == 32 * 32 + 4  # every via and every pad
