@@ -1,0 +1,335 @@
+"""Benchmark: backward-Euler transient of the 1024x1024x3 RC power grid.
+
+One benchmark step is one whole transient of the workload: 1000 backward-Euler
+steps of 5 ps on the 3,145,728-node 3-layer RC grid (FP32 SOR sweeps with FP64
+residual and defect correction), every step certified to the 1e-6 V error
+target, starting from the DC operating point.  The reported value is
+transient (BE) steps per second; node-sweeps/s, the roofline of the
+persistent kernel, an end-to-end figure through host buffers, and the CPU
+oracle's rate on a bounded sample ride along in the same JSON line.
+
+Multi-GPU (``--gpus N`` under torchrun): every rank runs an independent
+replica of the workload (the path does not shard one grid across GPUs); the
+value is the total over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "node-sweeps/s & transient steps/s at 1e-6 V max error; % of HBM roofline"
+WORKLOAD = "rc_grid_1024x1024x3"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=1024)
+    ap.add_argument("--ny", type=int, default=1024)
+    ap.add_argument("--nsteps", type=int, default=1000, help="BE steps per transient")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        if not self.lines:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1])); smax = float(f[2])
+            except (ValueError, IndexError):
+                continue
+            for k, name in enumerate(names):
+                if len(f) > 5 + k and f[5 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(st, n, mn, n_src, mixed: bool, nsteps: int, extrap: bool = True) -> float:
+    """Bytes the method must move for the work recorded in ``st``.
+
+    per node-sweep (FP32 sweep on the correction): 16 + 4 m/n  (delta r/w, r, 1/D, each weight once)
+    per node-sweep (FP64 sweep):                   32 + 8 m/n
+    per node, outer FP64 pass:   52 + 8 m/n (mixed) or 56 + 8 m/n (FP64)
+    per node, step start (RHS, warm start, residual): 56 + 8 m/n (+8 with extrapolation)
+                                  + 56 B per PWL source (index + 3 breakpoints)
+    per node, step end (read v once for the outputs): 8
+    """
+    sweep_b = (16 + 4 * mn) if mixed else (32 + 8 * mn)
+    outer_b = (52 if mixed else 56) + 8 * mn
+    start_b = 56 + (8 if extrap else 0) + 8 * mn
+    return (st["total_sweeps"] * sweep_b * n + st["total_outer"] * outer_b * n
+            + nsteps * (start_b * n + 56 * n_src + 8 * n))
+
+
+# ------------------------------------------------------------------ reference arm (the CPU oracle)
+
+def oracle_sample_rate(nx: int, ny: int, nsteps: int, timeout: float = 600.0) -> dict:
+    """Time the FP64 oracle (direct solves) on a sample of the workload recipe in a
+    fresh single-threaded process; returns seconds for setup and for ``nsteps`` steps."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+import pgsynth
+from oracle import transient, matrices
+net = pgsynth.config1(nx={nx}, ny={ny})
+h = net.meta["h"]
+t0 = time.perf_counter()
+mats = matrices.nodal_matrices(net)
+it = transient.simulate(net, h, {nsteps}, mats=mats)
+next(it)                       # DC point
+t1 = time.perf_counter()
+s, v, _ = next(it)             # first step includes the factorisation
+t2 = time.perf_counter()
+for s, v, _ in it:
+    pass
+t3 = time.perf_counter()
+print(json.dumps(dict(n=net.n_nodes, setup_s=t2 - t0, steps=s - 1, steps_s=t3 - t2)))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=timeout, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_entry(n_full: int, unit_steps: bool = True) -> dict:
+    nx = int(os.environ.get("PG_ORACLE_SAMPLE_NX", "256"))
+    nsteps = int(os.environ.get("PG_ORACLE_SAMPLE_STEPS", "60"))
+    d = oracle_sample_rate(nx, nx, nsteps)
+    rate_sample = d["steps"] / d["steps_s"]                    # BE steps/s on the sample
+    value = rate_sample * d["n"] / n_full                      # scaled to the full grid (linear in n)
+    return {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": (f"config-1 recipe at {nx}x{nx}x3 ({d['n']} nodes), {d['steps']} BE steps after the "
+                       f"factorisation ({d['setup_s']:.1f} s, excluded), FP64 sparse LU solves, 1 thread; "
+                       f"rate scaled by n_sample/n_full (optimistic for a direct solver)")}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    n_full = args.nx * args.ny * 3
+    times = []
+    nx = int(os.environ.get("PG_ORACLE_SAMPLE_NX", "256"))
+    nsteps = int(os.environ.get("PG_ORACLE_SAMPLE_STEPS", "60"))
+    for k in range(args.warmup + args.steps):
+        d = oracle_sample_rate(nx, nx, nsteps)
+        if k >= args.warmup:
+            times.append(d)
+    steps_s = sum(d["steps"] for d in times) / sum(d["steps_s"] for d in times)
+    value = steps_s * times[0]["n"] / n_full
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(d["steps_s"] for d in times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{nx}x{nx}x3", "be_steps_per_sample": nsteps,
+                       "l2": "host CPU run"},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"config-1 recipe at {nx}x{nx}x3, {nsteps} BE steps per bench step, "
+                                       "factorisation excluded, rate scaled by n_sample/n_full"},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    import pgsynth
+    from paper_1409_7166_gb300 import binding as B
+    from paper_1409_7166_gb300.build import build
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build()
+    B.lib()
+
+    net = pgsynth.config1(nx=args.nx, ny=args.ny)
+    h = net.meta["h"]
+    n = net.n_nodes
+    mn = (len(net.r_g) - int(np.sum(net.r_b < 0))) / n          # trivial-trivial branches per node
+    n_src = len(net.i_a)
+    nsteps = args.nsteps
+    t0 = time.time()
+    grid = B.Grid(net, precision=B.PG_PREC_MIXED)
+    stream = torch.cuda.Stream()
+    B.pg_set_stream(grid.handle, stream.cuda_stream)
+    vmin = torch.empty(nsteps, dtype=torch.float64, device="cuda")
+    vnode = torch.empty(nsteps, dtype=torch.int32, device="cuda")
+    st0 = B.pg_transient(grid.handle, h, 1)           # per-h setup (coefficients, omega, kappa, q)
+    setup_s = time.time() - t0
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
+
+    def one_step():
+        B.pg_reset(grid.handle)                        # back to the DC operating point at t = 0
+        return B.pg_transient(grid.handle, h, nsteps, vmin=vmin, vmin_node=vnode)
+
+    for _ in range(args.warmup):
+        one_step()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))                  # evict L2 before each timed step (not timed)
+                ev[k][0].record(stream)
+                st = one_step()
+                ev[k][1].record(stream)
+            stats.append(st.as_dict())
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = sum(ms) / 1e3
+    t_max = t_local
+    if dist:
+        tt = torch.tensor([t_local], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * args.steps * nsteps / t_max                          # BE steps/s, all ranks
+    sweeps = sum(s["total_sweeps"] for s in stats)
+    node_sweeps = world * sweeps * n / t_max
+    dev_ms = [s["device_ms"] for s in stats]
+
+    # roofline of the persistent kernel (the only kernel of consequence in the timed region)
+    peak, peak_kind = load_peaks()
+    alg = [algorithmic_bytes(s, n, mn, n_src, True, nsteps) for s in stats]
+    achieved = sum(alg) / (sum(dev_ms) / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "peak_kind": peak_kind,
+            "bytes_per_launch": sum(alg) / len(alg), "kernel": "persistent_kernel<true>"}
+
+    # end to end: new load scenario from pinned host memory, outputs back to host, every step
+    e2e = None
+    if not args.no_e2e:
+        it_h = torch.from_numpy(net.i_t).pin_memory()
+        iv_h = torch.from_numpy(net.i_v).pin_memory()
+        vmin_h = torch.empty(nsteps, dtype=torch.float64).pin_memory()
+        vnode_h = torch.empty(nsteps, dtype=torch.int32).pin_memory()
+        torch.cuda.synchronize()
+        te = []
+        for k in range(max(2, min(args.steps, 3))):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            B.pg_update_sources(grid.handle, it_h, iv_h)
+            B.pg_reset(grid.handle)
+            B.pg_transient(grid.handle, h, nsteps, vmin=vmin_h, vmin_node=vnode_h)
+            torch.cuda.synchronize()
+            te.append(time.perf_counter() - a)
+        e2e = {"value": world * nsteps * len(te) / sum(te), "unit": "steps/s",
+               "h2d_bytes_per_step": int(it_h.numel() * 8 + iv_h.numel() * 8),
+               "d2h_bytes_per_step": int(nsteps * (8 + 4))}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline_entry(n)
+        except Exception as exc:  # keep the GPU line even if the oracle sample fails
+            cpu = {"value": None, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nodes": n, "be_steps": nsteps, "h_ps": h * 1e12,
+                       "precision": "FP32 sweeps, FP64 residual + defect correction", "tol_V": 1e-6,
+                       "l2": "flushed between timed steps (256 MB write); working set > L2",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "node_sweeps_per_s": node_sweeps,
+            "sweeps_per_transient": sweeps / args.steps,
+            "max_step_bound_V": max(s["max_step_bound"] for s in stats),
+            "err_bound_V": max(s["err_bound"] for s in stats),
+            "omega": stats[0]["omega"], "kappa": stats[0]["kappa"], "q": stats[0]["q"],
+            "setup_s": setup_s,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    grid.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

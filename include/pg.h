@@ -1,0 +1,223 @@
+/*
+ * pg.h -- C ABI of the GB300 power-grid transient library (libpg).
+ *
+ * What it computes (Yang, Wang, Azevedo, Wang, "An Efficient Topology-Based
+ * Algorithm for Transient Analysis of Power Grid"):
+ *
+ *   For an RC or RLC power grid with trivial nodes v, ideal supply nodes v_d,
+ *   grounded capacitors C, conductance matrix G (pads included), inductor
+ *   matrix L = A_l^T Ldiag^-1 A_l and piecewise-linear load currents I_s,
+ *   each backward-Euler step of length h solves the SPD system
+ *
+ *       M v(t+h) = (C/h) v(t) - A_l^T i_l(t) - A_i^T I_s(t+h) - G_s v_d - h L_s v_d,
+ *       M = C/h + G + h L                                   (Eq. 2, Eq. 10-11)
+ *
+ *   then advances the inductor currents
+ *
+ *       i_l(t+h) = i_l(t) + h Ldiag^-1 (A_l v(t+h) + A_ls v_d)     (Eq. 10).
+ *
+ *   The system is solved without assembling M, by the node-local update of
+ *   Eq. 15-17 (Gauss-Seidel / SOR, Theorem 1) in red-black or multicolour
+ *   order on the GPU.  The signs of the source terms follow KVL (Eq. 7).
+ *
+ * Conventions shared by every call:
+ *   - Units are SI: S, F, H, s, A, V.
+ *   - A branch terminal is an int32: t >= 0 is trivial node t, PG_GROUND (-1)
+ *     is ground, PG_SOURCE(k) = -2-k is source node k (the split of the
+ *     incidence matrix into A and A_s, Eq. 4-5).
+ *   - "device" pointers are CUDA device (or managed) memory on the grid's
+ *     device; "host" pointers are ordinary or pinned host memory.  The library
+ *     never frees memory it did not allocate.
+ *   - Calls are ordered on the grid's stream (pg_set_stream); calls that
+ *     return statistics synchronise that stream before returning.
+ *   - Errors are returned as pg_status; pg_status_str names them.  A failed
+ *     call leaves the grid usable unless it returned PG_ERR_CUDA.
+ */
+#ifndef PG_H
+#define PG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PG_GROUND (-1)
+#define PG_SOURCE(k) (-2 - (k))
+
+typedef enum pg_status {
+    PG_OK = 0,
+    PG_ERR_INVALID_ARG = 1,    /* bad index, non-positive element value, bad option */
+    PG_ERR_FLOATING_NODE = 2,  /* topological assumption 2 or 3 violated (Section III-B) */
+    PG_ERR_OOM = 3,            /* device or host allocation failed */
+    PG_ERR_CUDA = 4,           /* a CUDA runtime call failed */
+    PG_ERR_NOT_CONVERGED = 5,  /* relaxation hit its sweep cap or produced a non-finite value */
+    PG_ERR_TIMEOUT = 6,        /* the device-wide barrier exceeded its time limit */
+    PG_ERR_UNSUPPORTED = 7     /* input outside the per-node form, e.g. node-to-node capacitor */
+} pg_status;
+
+/*
+ * Netlist (Section III-A, Eq. 4-8).  Structure of arrays; every branch is
+ * oriented a -> b.  Capacitors must have exactly one trivial terminal (the
+ * grounded C_i of Eq. 12).  A current source drives its PWL current from a
+ * to b through the source, so a load drawing I(t) from node k is a = k,
+ * b = PG_GROUND.  Source e owns PWL breakpoints i_t/i_v[i_ptr[e] .. i_ptr[e+1]);
+ * times must be non-decreasing; the value is held constant before the first
+ * and after the last breakpoint and is linear in between.
+ * lat_nx/lat_ny/lat_nl: optional lattice shape (node (x,y,l) = (l*ny+y)*nx+x)
+ * or 0; informational only.
+ * pg_create_grid copies everything; the caller may free the arrays after it
+ * returns.  All pointers are host pointers.
+ */
+typedef struct pg_netlist {
+    int32_t n_nodes;
+    int32_t n_sources;
+    const double* vdd;                 /* [n_sources] source-node voltages */
+    int64_t n_r; const int32_t* r_a; const int32_t* r_b; const double* r_g;
+    int64_t n_c; const int32_t* c_a; const int32_t* c_b; const double* c_val;
+    int64_t n_l; const int32_t* l_a; const int32_t* l_b; const double* l_val;
+    int64_t n_i; const int32_t* i_a; const int32_t* i_b;
+    const int64_t* i_ptr;              /* [n_i + 1] */
+    const double* i_t; const double* i_v;
+    int32_t lat_nx, lat_ny, lat_nl;
+} pg_netlist;
+
+typedef enum pg_precision {
+    PG_PREC_FP64 = 0,   /* FP64 sweeps */
+    PG_PREC_MIXED = 1   /* FP32 sweeps on the correction, FP64 residual and defect correction */
+} pg_precision;
+
+#define PG_DEBUG_SKIP_ARRIVAL 1  /* test hook: block 0 never arrives at the first device barrier */
+
+typedef struct pg_options {
+    int32_t precision;        /* pg_precision */
+    double omega;             /* SOR factor (Eq. 17) in (0, 2); 0 = Young's formula from an estimated
+                                 Jacobi spectral radius */
+    double tol;               /* target max-abs voltage error of every step against the exact
+                                 backward-Euler trajectory, V (0 -> 1e-6) */
+    double step_tol;          /* per-step solve target, V; 0 -> derived from tol: RC grids use
+                                 0.5 (1 - q) tol, grids with inductors use 1e-4 tol */
+    int32_t max_sweeps;       /* cap on relaxation sweeps per step (0 -> 20000) */
+    int32_t warm_start;       /* 0: V(s-1) as in Algorithm 1; 1: linear extrapolation (default) */
+    double inner_reduction;   /* PG_PREC_MIXED: residual reduction asked of one FP32 inner solve
+                                 (0 -> 1e-3); an inner solve also ends when it stalls */
+    int32_t threads_per_block;/* 0 -> 256 */
+    int32_t blocks_per_sm;    /* 0 -> as many as fit */
+    double barrier_timeout_s; /* device barrier time limit (0 -> 2 s) */
+    int32_t debug_flags;      /* PG_DEBUG_* test hooks; 0 in production */
+} pg_options;
+
+/* Fill *opt with the defaults listed above. */
+void pg_default_options(pg_options* opt);
+
+typedef struct pg_grid pg_grid;
+
+/*
+ * Validate a netlist against the paper's topological assumptions
+ * (Section III-B: every trivial node has a non-current-source branch; each
+ * connected sub-circuit, Fig. 1, reaches a source or ground through a
+ * resistor or inductor), colour it, pack it for the device, and allocate the
+ * grid's device memory on the current CUDA device.  *out receives the handle
+ * (NULL on error).  opt may be NULL for defaults.
+ * Errors: PG_ERR_INVALID_ARG, PG_ERR_FLOATING_NODE, PG_ERR_UNSUPPORTED,
+ * PG_ERR_OOM, PG_ERR_CUDA.
+ */
+pg_status pg_create_grid(const pg_netlist* nl, const pg_options* opt, pg_grid** out);
+
+/* Free every resource of the grid (synchronises its stream).  NULL is a no-op. */
+void pg_destroy(pg_grid* g);
+
+/* Static string naming a status code. */
+const char* pg_status_str(pg_status s);
+
+/* Detail message of the last failing call on the calling thread (valid until
+ * that thread's next failing call). */
+const char* pg_last_error(void);
+
+/* Order subsequent work on this cudaStream_t (NULL = legacy default stream). */
+pg_status pg_set_stream(pg_grid* g, void* stream);
+
+/* Node count, inductor count, colour count and permuted (padded) node count. */
+pg_status pg_grid_info(const pg_grid* g, int32_t* n_nodes, int32_t* n_inductors,
+                       int32_t* n_colours, int32_t* n_padded);
+
+/*
+ * Set the transient state: node voltages v[n_nodes] and inductor currents
+ * il[n_l] (either may be NULL: NULL v keeps the DC operating point rule, NULL il
+ * means zero currents), at step index `step` (time = step * h).  Pointers are
+ * host memory when on_host != 0, else device memory.
+ */
+pg_status pg_set_state(pg_grid* g, const double* v, const double* il, int64_t step, int32_t on_host);
+
+/* Copy the current state out (same conventions); *step receives the step index. */
+pg_status pg_get_state(pg_grid* g, double* v, double* il, int64_t* step, int32_t on_host);
+
+/* Forget the state: the next pg_transient starts from the DC operating point at t = 0. */
+pg_status pg_reset(pg_grid* g);
+
+/*
+ * Replace the PWL breakpoint values of the current sources (same i_ptr layout
+ * as the netlist).  i_t and/or i_v may be NULL to keep them.  Host or device
+ * memory per on_host.  Used to run many current scenarios on one grid.
+ */
+pg_status pg_update_sources(pg_grid* g, const double* i_t, const double* i_v, int32_t on_host);
+
+/* Per-step outputs of pg_transient.  Any pointer may be NULL.  Rows are in
+ * step order, columns in the caller's node numbering. */
+typedef struct pg_output {
+    int32_t on_host;      /* 0: the pointers below are device memory; 1: host memory */
+    double* v_all;        /* [nsteps x n_nodes] node voltages after each step */
+    double* il_all;       /* [nsteps x n_l] inductor currents after each step */
+    double* vmin;         /* [nsteps] smallest node voltage (worst IR drop) */
+    int32_t* vmin_node;   /* [nsteps] node attaining it (smallest id on ties) */
+    int32_t n_probes;
+    const int32_t* probes;/* [n_probes] node ids (same memory kind as the outputs) */
+    double* probe_v;      /* [nsteps x n_probes] */
+} pg_output;
+
+typedef struct pg_run_stats {
+    int64_t steps_done;
+    int64_t total_sweeps;       /* relaxation sweeps summed over the steps */
+    int32_t max_sweeps_step;    /* most sweeps any single step needed */
+    int32_t max_outer_step;     /* most defect-correction passes any step needed */
+    int64_t total_outer;
+    double max_step_bound;      /* largest certified per-step error bound, V */
+    double err_bound;           /* bound on the accumulated error (RC: sum rule with q), V */
+    int64_t failed_step;        /* step index of a failure, -1 if none */
+    double omega;               /* SOR factor used */
+    double rho_jacobi;          /* estimated Jacobi spectral radius (lower bound) */
+    double kappa;               /* upper bound of ||M^-1 D||_inf used by the stopping rule */
+    double q;                   /* upper bound of ||M^-1 C/h||_inf (RC error gain per step) */
+    double step_tol;            /* per-step target actually used, V */
+    double device_ms;           /* device time of the persistent launch(es), ms */
+} pg_run_stats;
+
+/*
+ * Run nsteps backward-Euler steps of length h (Algorithm 1) from the current
+ * state; if no state is set, first compute the DC operating point at t = 0
+ * (capacitors open, inductors carrying i_l(0) = 0; Section IV-B) and take it
+ * as step 0.  Changing h re-assembles the per-h coefficients (D, weights,
+ * C/h, h/L) and the stopping-rule constants.  Each step is solved until its
+ * certified error bound is below the per-step target.  out and stats may be
+ * NULL.  Errors: PG_ERR_INVALID_ARG, PG_ERR_NOT_CONVERGED (stats->failed_step
+ * set; the state is left at the last good step), PG_ERR_TIMEOUT, PG_ERR_CUDA.
+ */
+pg_status pg_transient(pg_grid* g, double h, int32_t nsteps, const pg_output* out,
+                       pg_run_stats* stats);
+
+/* One step (pg_transient with nsteps = 1); v_out (device, [n_nodes]) may be NULL. */
+pg_status pg_step(pg_grid* g, double h, double* v_out, pg_run_stats* stats);
+
+/*
+ * Solve M x = b once for the assembled h (b, x: device, [n_nodes], caller
+ * numbering) to the absolute error target `tol` (V-like units of x), starting
+ * from x = 0.  Exposes the relaxation kernel on its own.
+ */
+pg_status pg_solve(pg_grid* g, double h, const double* b, double* x, double tol,
+                   pg_run_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PG_H */

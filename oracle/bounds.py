@@ -34,3 +34,15 @@ def step_gain(net, h: float, mats=None) -> float:
     c = mats.C.diagonal() / h
     y = DirectSolver(mats.system_matrix(h)).solve(c)
     return float(np.max(y))
+
+
+def scaled_minv_inf_norm(net, h: float, mats=None) -> float:
+    """``||M^-1 D||_inf = max_i (M^-1 D 1)_i`` with ``D = diag(M)`` (exact, by a direct solve).
+
+    Used with the scaled residual ``max_i |r_i| / D_i``:
+    ``||v - v*||_inf <= ||M^-1 D||_inf * max_i |r_i| / D_i`` because ``M^-1 D >= 0``.
+    """
+    mats = mats or nodal_matrices(net)
+    M = mats.system_matrix(h)
+    x = DirectSolver(M).solve(M.diagonal())
+    return float(np.max(x))

@@ -1,0 +1,831 @@
+// The C ABI (include/pg.h): grid lifetime, per-h coefficient assembly
+// (Eq. 14: diagonal sum g + h sum 1/L + C/h and off-diagonal g + h/L), the
+// stopping-rule constants, DC initial conditions (Section IV-B) and the
+// transient driver (Algorithm 1), which runs as one persistent launch.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "pg_internal.h"
+
+using namespace pg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+// Copy of the caller's netlist (needed to derive the DC sub-problem).
+struct NetCopy {
+    int32_t n = 0, p = 0;
+    std::vector<double> vdd;
+    std::vector<int32_t> r_a, r_b, c_a, c_b, l_a, l_b, i_a, i_b;
+    std::vector<double> r_g, c_val, l_val, i_t, i_v;
+    std::vector<int64_t> i_ptr;
+    int32_t nx = 0, ny = 0, nl = 0;
+
+    void from(const pg_netlist* nl_) {
+        n = nl_->n_nodes; p = nl_->n_sources;
+        vdd.assign(nl_->vdd, nl_->vdd + p);
+        auto cp = [](auto& dst, auto* src, int64_t m) { dst.assign(src, src + m); };
+        cp(r_a, nl_->r_a, nl_->n_r); cp(r_b, nl_->r_b, nl_->n_r); cp(r_g, nl_->r_g, nl_->n_r);
+        cp(c_a, nl_->c_a, nl_->n_c); cp(c_b, nl_->c_b, nl_->n_c); cp(c_val, nl_->c_val, nl_->n_c);
+        cp(l_a, nl_->l_a, nl_->n_l); cp(l_b, nl_->l_b, nl_->n_l); cp(l_val, nl_->l_val, nl_->n_l);
+        cp(i_a, nl_->i_a, nl_->n_i); cp(i_b, nl_->i_b, nl_->n_i);
+        if (nl_->n_i) {
+            cp(i_ptr, nl_->i_ptr, nl_->n_i + 1);
+            cp(i_t, nl_->i_t, nl_->i_ptr[nl_->n_i]); cp(i_v, nl_->i_v, nl_->i_ptr[nl_->n_i]);
+        } else {
+            i_ptr.assign(1, 0);
+        }
+        nx = nl_->lat_nx; ny = nl_->lat_ny; nl = nl_->lat_nl;
+    }
+    // The DC network at t = 0: capacitors open, inductors carrying i_l(0) = 0 (open).
+    pg_netlist dc_view() const {
+        pg_netlist d{};
+        d.n_nodes = n; d.n_sources = p; d.vdd = vdd.data();
+        d.n_r = (int64_t)r_g.size(); d.r_a = r_a.data(); d.r_b = r_b.data(); d.r_g = r_g.data();
+        d.n_i = (int64_t)i_a.size(); d.i_a = i_a.data(); d.i_b = i_b.data();
+        d.i_ptr = i_ptr.data(); d.i_t = i_t.data(); d.i_v = i_v.data();
+        return d;
+    }
+};
+
+double pwl_at(const NetCopy& nc, int64_t e, double t) {
+    int64_t lo = nc.i_ptr[e], hi = nc.i_ptr[e + 1] - 1;
+    if (t <= nc.i_t[lo]) return nc.i_v[lo];
+    if (t > nc.i_t[hi]) return nc.i_v[hi];
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) / 2;
+        if (t <= nc.i_t[mid]) hi = mid; else lo = mid;
+    }
+    return nc.i_v[lo] + (nc.i_v[hi] - nc.i_v[lo]) * ((t - nc.i_t[lo]) / (nc.i_t[hi] - nc.i_t[lo]));
+}
+
+}  // namespace
+
+struct pg_grid {
+    Packed P;
+    NetCopy nc;
+    pg_options opt{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int n_sm = 0;
+    int blocks = 1, threads = 256;
+    bool mixed = false;
+    std::vector<void*> allocs;
+    DevGrid dg{};
+    DevState ds{};
+    DevCtl dc{};
+    double* d_x = nullptr;        // scratch [n] for setup solves (caller numbering)
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // per-h
+    double h = -1.0;
+    double omega = 0.0, rho = 0.0, kappa = 0.0, q = 0.0, step_tol = 0.0, target = 0.0;
+    // transient state
+    bool has_state = false;
+    int64_t step = 0;
+    int vL = 0, vP = 1;
+    bool have_prev = false;
+    bool dc_trivial = false;      // DC point is v = Vdd everywhere (see compute_dc_trivial)
+    double dc_vdd = 0.0;
+    std::unique_ptr<pg_grid> dcgrid;  // DC sub-problem, built on first use
+
+    template <typename T>
+    T* alloc(size_t count) {
+        if (count == 0) count = 1;
+        void* p = nullptr;
+        if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) return nullptr;
+        allocs.push_back(p);
+        return static_cast<T*>(p);
+    }
+    ~pg_grid() {
+        if (stream) cudaStreamSynchronize(stream); else cudaDeviceSynchronize();
+        for (void* p : allocs) cudaFree(p);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+    }
+};
+
+namespace {
+
+constexpr int kSetupSweeps = 200000;
+
+pg_status cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return PG_ERR_CUDA;
+}
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+template <typename T>
+pg_status upload(pg_grid* g, T* dst, const std::vector<T>& src) {
+    if (src.empty()) return PG_OK;
+    CK(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, g->stream));
+    return PG_OK;
+}
+
+void compute_dc_trivial(pg_grid* g) {
+    // v(0) = V everywhere solves the DC system exactly when every branch to a
+    // fixed potential goes to a source of the same voltage V (none to ground)
+    // and no load draws current at t = 0: then G (V 1) = -G_s v_d.
+    const NetCopy& nc = g->nc;
+    bool ok = nc.p > 0;
+    double V = ok ? nc.vdd[0] : 0.0;
+    for (int k = 0; k < nc.p && ok; ++k) ok = nc.vdd[k] == V;
+    auto fixed_ok = [&](int32_t a, int32_t b) {
+        if ((a >= 0) == (b >= 0)) return true;
+        int32_t o = a >= 0 ? b : a;
+        return o != PG_GROUND;
+    };
+    for (size_t e = 0; e < nc.r_g.size() && ok; ++e) ok = fixed_ok(nc.r_a[e], nc.r_b[e]);
+    for (size_t e = 0; e < nc.l_val.size() && ok; ++e) ok = fixed_ok(nc.l_a[e], nc.l_b[e]);
+    for (size_t e = 0; e + 1 < nc.i_ptr.size() && ok; ++e) ok = pwl_at(nc, (int64_t)e, 0.0) == 0.0;
+    g->dc_trivial = ok;
+    g->dc_vdd = V;
+}
+
+pg_status alloc_device(pg_grid* g) {
+    const Packed& P = g->P;
+    const int np = P.n_pad;
+    DevGrid& d = g->dg;
+    d.n_pad = np; d.ncol = P.ncol; d.n_slices = P.n_slices; d.n_real = P.n;
+    std::vector<int32_t> cs(P.ncol + 1);
+    for (int c = 0; c <= P.ncol; ++c) cs[c] = P.colour_start[c] / kSlice;
+    int32_t* colour_slice = g->alloc<int32_t>(cs.size());
+    int64_t* slice_off = g->alloc<int64_t>(P.slice_off.size());
+    int32_t* slice_w = g->alloc<int32_t>(P.slice_w.size());
+    int32_t* slice_doff = g->alloc<int32_t>(P.slice_doff.size());
+    int32_t* dia_off = g->alloc<int32_t>(P.dia_off.size());
+    int32_t* ell_col = g->alloc<int32_t>(P.n_ell);
+    int32_t* orig = g->alloc<int32_t>(np);
+    int32_t* ld_ptr = g->alloc<int32_t>(P.ld_ptr.size());
+    int32_t* ld_idx = g->alloc<int32_t>(P.ld_idx.size());
+    int64_t* pwl_ptr = g->alloc<int64_t>(P.pwl_ptr.size());
+    double* pwl_t = g->alloc<double>(P.pwl_t.size());
+    double* pwl_v = g->alloc<double>(P.pwl_v.size());
+    int32_t* ind_a = g->alloc<int32_t>(P.n_l);
+    int32_t* ind_b = g->alloc<int32_t>(P.n_l);
+    double* ind_hl = g->alloc<double>(P.n_l);
+    int32_t* ind_ptr = g->alloc<int32_t>(P.ind_ptr.size());
+    int32_t* ind_idx = g->alloc<int32_t>(P.ind_idx.size());
+    double* vdd = g->alloc<double>(P.vdd.size());
+    double* w64 = g->alloc<double>(P.n_ell);
+    double* D64 = g->alloc<double>(np);
+    double* invD64 = g->alloc<double>(np);
+    double* ch = g->alloc<double>(np);
+    double* cinj = g->alloc<double>(np);
+    float* w32 = g->mixed ? g->alloc<float>(P.n_ell) : nullptr;
+    float* invD32 = g->mixed ? g->alloc<float>(np) : nullptr;
+    if (!colour_slice || !slice_off || !slice_w || !slice_doff || !dia_off || !ell_col || !orig || !ld_ptr ||
+        !ld_idx || !pwl_ptr || !pwl_t || !pwl_v || !ind_a || !ind_b || !ind_hl || !ind_ptr || !ind_idx || !vdd ||
+        !w64 || !D64 || !invD64 || !ch || !cinj || (g->mixed && (!w32 || !invD32)))
+        return PG_ERR_OOM;
+    d.colour_slice = colour_slice; d.slice_off = slice_off; d.slice_w = slice_w; d.slice_doff = slice_doff;
+    d.dia_off = dia_off; d.ell_col = ell_col; d.orig = orig; d.ld_ptr = ld_ptr; d.ld_idx = ld_idx;
+    d.pwl_ptr = pwl_ptr; d.pwl_t = pwl_t; d.pwl_v = pwl_v; d.n_l = P.n_l; d.ind_a = ind_a; d.ind_b = ind_b;
+    d.ind_hl = ind_hl; d.ind_ptr = ind_ptr; d.ind_idx = ind_idx; d.vdd = vdd;
+    d.w64 = w64; d.D64 = D64; d.invD64 = invD64; d.ch = ch; d.cinj = cinj; d.w32 = w32; d.invD32 = invD32;
+    pg_status s;
+    if ((s = upload(g, colour_slice, cs)) || (s = upload(g, slice_off, P.slice_off)) ||
+        (s = upload(g, slice_w, P.slice_w)) || (s = upload(g, slice_doff, P.slice_doff)) ||
+        (s = upload(g, dia_off, P.dia_off)) || (s = upload(g, ell_col, P.ell_col)) || (s = upload(g, orig, P.orig)) ||
+        (s = upload(g, ld_ptr, P.ld_ptr)) || (s = upload(g, ld_idx, P.ld_idx)) ||
+        (s = upload(g, pwl_ptr, P.pwl_ptr)) || (s = upload(g, pwl_t, P.pwl_t)) || (s = upload(g, pwl_v, P.pwl_v)) ||
+        (s = upload(g, ind_a, P.ind_a)) || (s = upload(g, ind_b, P.ind_b)) || (s = upload(g, ind_ptr, P.ind_ptr)) ||
+        (s = upload(g, ind_idx, P.ind_idx)) || (s = upload(g, vdd, P.vdd)))
+        return s;
+
+    DevState& st = g->ds;
+    for (int k = 0; k < 3; ++k) {
+        st.v[k] = g->alloc<double>(np);
+        if (!st.v[k]) return PG_ERR_OOM;
+        CK(cudaMemsetAsync(st.v[k], 0, np * sizeof(double), g->stream));
+    }
+    st.il = g->alloc<double>(P.n_l);
+    st.r64 = g->alloc<double>(np);
+    if (!st.il || !st.r64) return PG_ERR_OOM;
+    CK(cudaMemsetAsync(st.il, 0, std::max(1, P.n_l) * sizeof(double), g->stream));
+    if (g->mixed) {
+        st.r32 = g->alloc<float>(np);
+        st.d32[0] = g->alloc<float>(np);
+        st.d32[1] = g->alloc<float>(np);
+        if (!st.r32 || !st.d32[0] || !st.d32[1]) return PG_ERR_OOM;
+    } else {
+        st.d64[0] = g->alloc<double>(np);
+        st.d64[1] = g->alloc<double>(np);
+        if (!st.d64[0] || !st.d64[1]) return PG_ERR_OOM;
+    }
+    g->d_x = g->alloc<double>(P.n);
+    if (!g->d_x) return PG_ERR_OOM;
+
+    // launch shape: every warp gets the same number of slices per colour sweep
+    int bps = 0;
+    CK(persistent_occupancy(g->mixed, g->threads, &bps));
+    if (g->opt.blocks_per_sm > 0) bps = std::min(bps, g->opt.blocks_per_sm);
+    if (bps < 1) { g_last_error = "kernel does not fit on an SM"; return PG_ERR_CUDA; }
+    const int wpb = g->threads / 32;
+    const int max_warps = g->n_sm * bps * wpb;
+    int smax = 1;
+    for (int c = 0; c < P.ncol; ++c) smax = std::max(smax, cs[c + 1] - cs[c]);
+    const int rounds = (smax + max_warps - 1) / max_warps;
+    const int warps = (smax + rounds - 1) / rounds;
+    g->blocks = std::max(1, std::min(g->n_sm * bps, (warps + wpb - 1) / wpb));
+
+    DevCtl& c = g->dc;
+    c.bar_count = g->alloc<unsigned>(1);
+    c.bar_gen = g->alloc<unsigned>(1);
+    c.err = g->alloc<int32_t>(1);
+    c.red = g->alloc<unsigned long long>(kRedSlots);
+    c.blk_min = g->alloc<unsigned long long>(2 * g->blocks);
+    c.blk_arg = g->alloc<int32_t>(2 * g->blocks);
+    c.stats = g->alloc<double>(kStatCount);
+    if (!c.bar_count || !c.bar_gen || !c.err || !c.red || !c.blk_min || !c.blk_arg || !c.stats) return PG_ERR_OOM;
+    CK(cudaMemsetAsync(c.bar_gen, 0, sizeof(unsigned), g->stream));
+    CK(cudaEventCreate(&g->ev0));
+    CK(cudaEventCreate(&g->ev1));
+    CK(cudaStreamSynchronize(g->stream));
+    return PG_OK;
+}
+
+// Per-h coefficients of Eq. 14 (node form of M = C/h + G + h L).
+pg_status assemble_h(pg_grid* g, double h) {
+    const Packed& P = g->P;
+    const int np = P.n_pad;
+    std::vector<double> D(np, 0.0), iD(np, 0.0), ch(np, 0.0), cinj(np, 0.0);
+    for (int i = 0; i < np; ++i) {
+        const int o = P.orig[i];
+        if (o < 0) continue;
+        double s = 0.0;
+        for (int64_t a = P.adj_ptr[o]; a < P.adj_ptr[o + 1]; ++a) s += P.adj_g[a] + h * P.adj_il[a];
+        const double d = s + P.g_gnd[o] + h * P.il_gnd[o] + P.cap[o] / h;
+        D[i] = d; iD[i] = 1.0 / d; ch[i] = P.cap[o] / h; cinj[i] = P.inj_g[o] + h * P.inj_il[o];
+    }
+    std::vector<double> w(P.n_ell, 0.0);
+    for (int64_t e = 0; e < P.n_ell; ++e) {
+        const int64_t a = P.ell_adj[e];
+        if (a >= 0) w[e] = P.adj_g[a] + h * P.adj_il[a];
+    }
+    std::vector<double> hl(P.n_l);
+    for (int e = 0; e < P.n_l; ++e) hl[e] = h * P.ind_invL[e];
+    pg_status s;
+    if ((s = upload(g, const_cast<double*>(g->dg.D64), D)) || (s = upload(g, const_cast<double*>(g->dg.invD64), iD)) ||
+        (s = upload(g, const_cast<double*>(g->dg.ch), ch)) || (s = upload(g, const_cast<double*>(g->dg.cinj), cinj)) ||
+        (s = upload(g, const_cast<double*>(g->dg.w64), w)) || (s = upload(g, const_cast<double*>(g->dg.ind_hl), hl)))
+        return s;
+    if (g->mixed) {
+        std::vector<float> w32(P.n_ell), iD32(np);
+        for (int64_t e = 0; e < P.n_ell; ++e) w32[e] = (float)w[e];
+        for (int i = 0; i < np; ++i) iD32[i] = (float)iD[i];
+        if ((s = upload(g, const_cast<float*>(g->dg.w32), w32)) || (s = upload(g, const_cast<float*>(g->dg.invD32), iD32)))
+            return s;
+    }
+    CK(cudaStreamSynchronize(g->stream));
+    return PG_OK;
+}
+
+RunParams base_params(const pg_grid* g) {
+    RunParams rp{};
+    rp.mixed = g->mixed;
+    rp.h = g->h;
+    rp.omega = g->omega;
+    rp.kappa = g->kappa;
+    rp.target = g->target;
+    rp.inner_reduction = g->opt.inner_reduction;
+    rp.max_sweeps = g->opt.max_sweeps;
+    rp.max_outer = 50;
+    rp.timeout_ns = (long long)(g->opt.barrier_timeout_s * 1e9);
+    rp.debug_flags = g->opt.debug_flags;
+    rp.cur = g->vL; rp.prev = g->vP;
+    rp.warm_extrap = g->opt.warm_start;
+    return rp;
+}
+
+// One persistent launch; reads back the status word and statistics.
+pg_status run(pg_grid* g, const RunParams& rp, double* stats, float* ms) {
+    CK(cudaMemsetAsync(g->dc.bar_count, 0, sizeof(unsigned), g->stream));
+    CK(cudaMemsetAsync(g->dc.err, 0, sizeof(int32_t), g->stream));
+    CK(cudaMemsetAsync(g->dc.red, 0, kRedSlots * sizeof(unsigned long long), g->stream));
+    CK(cudaEventRecord(g->ev0, g->stream));
+    CK(launch_persistent(g->mixed, g->dg, g->ds, g->dc, rp, g->blocks, g->threads, g->stream));
+    CK(cudaEventRecord(g->ev1, g->stream));
+    int32_t err = 0;
+    CK(cudaMemcpyAsync(&err, g->dc.err, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaMemcpyAsync(stats, g->dc.stats, kStatCount * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    if (ms) CK(cudaEventElapsedTime(ms, g->ev0, g->ev1));
+    if (err == PG_ERR_TIMEOUT) { g_last_error = "device barrier timed out"; return PG_ERR_TIMEOUT; }
+    if (err == PG_ERR_NOT_CONVERGED) { g_last_error = "relaxation did not converge"; return PG_ERR_NOT_CONVERGED; }
+    if (err != 0) { g_last_error = "device error"; return PG_ERR_CUDA; }
+    return PG_OK;
+}
+
+// Solve M x = rhs (rhs: device, permuted) from x = 0 to max|r|/D <= tgt; x (caller order) -> g->d_x.
+pg_status solve_internal(pg_grid* g, const double* rhs_perm, double tgt, double* final_R) {
+    RunParams rp = base_params(g);
+    rp.max_sweeps = std::max(g->opt.max_sweeps, kSetupSweeps);   // setup solves ignore the per-step cap
+    rp.mode = kModeSolve;
+    rp.nsteps = 1;
+    rp.step0 = 0;
+    rp.target = tgt;
+    rp.have_prev = 0;
+    rp.warm_extrap = 0;
+    rp.solve_out = g->d_x;
+    g->ds.rhs = rhs_perm;
+    double stats[kStatCount];
+    pg_status s = run(g, rp, stats, nullptr);
+    g->ds.rhs = nullptr;
+    if (final_R) *final_R = stats[kStatLastR];
+    return s;
+}
+
+double host_max(pg_grid* g, const double* dptr, int n, pg_status* s) {
+    std::vector<double> x(n);
+    if (cudaMemcpy(x.data(), dptr, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        *s = PG_ERR_CUDA;
+        return 0.0;
+    }
+    double m = -INFINITY;
+    for (double v : x) m = std::max(m, v);
+    return m;
+}
+
+// Jacobi spectral radius by power iteration on (I + D^-1 W)/2 (Rayleigh quotient: a lower bound).
+pg_status estimate_rho(pg_grid* g, double* rho) {
+    const int np = g->P.n_pad, iters = 300;
+    double *x = nullptr, *y = nullptr, *acc = nullptr;
+    unsigned long long* mx = nullptr;
+    struct Scratch {
+        std::vector<void*> p;
+        ~Scratch() { for (void* q : p) cudaFree(q); }
+    } scratch;
+    auto take = [&](void** q, size_t bytes) {
+        if (cudaMalloc(q, bytes) != cudaSuccess) return false;
+        scratch.p.push_back(*q);
+        return true;
+    };
+    if (!take((void**)&x, np * sizeof(double)) || !take((void**)&y, np * sizeof(double)) ||
+        !take((void**)&acc, 2 * iters * sizeof(double)) || !take((void**)&mx, iters * sizeof(unsigned long long)))
+        return PG_ERR_OOM;
+    std::vector<double> ones(np, 0.0);
+    for (int i = 0; i < np; ++i) ones[i] = g->P.orig[i] >= 0 ? 1.0 : 0.0;
+    pg_status s;
+    if ((s = upload(g, x, ones))) return s;
+    CK(cudaMemsetAsync(acc, 0, 2 * iters * sizeof(double), g->stream));
+    CK(cudaMemsetAsync(mx, 0, iters * sizeof(unsigned long long), g->stream));
+    const int blocks = std::max(1, std::min(g->n_sm * 4, (g->P.n_slices + 7) / 8));
+    for (int k = 0; k < iters; ++k) {
+        CK(launch_power_step(g->dg, x, y, k ? mx + (k - 1) : nullptr, acc + 2 * k, mx + k, blocks, g->stream));
+        std::swap(x, y);
+    }
+    std::vector<double> a(2 * iters);
+    CK(cudaMemcpyAsync(a.data(), acc, a.size() * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    const double num = a[2 * (iters - 1)], den = a[2 * (iters - 1) + 1];
+    *rho = den > 0.0 ? std::min(std::max(num / den, 0.0), 1.0) : 0.0;
+    return PG_OK;
+}
+
+// Per-h setup: coefficients, omega, and the stopping-rule constants kappa, q.
+pg_status prepare_h(pg_grid* g, double h) {
+    if (g->h == h) return PG_OK;
+    if (!(h > 0.0) || !std::isfinite(h)) { g_last_error = "h must be > 0"; return PG_ERR_INVALID_ARG; }
+    pg_status s = assemble_h(g, h);
+    if (s) return s;
+    g->h = h;
+    if (g->opt.omega > 0.0) {
+        g->omega = g->opt.omega;
+        g->rho = 0.0;
+    } else {
+        if ((s = estimate_rho(g, &g->rho))) return s;
+        const double r = std::min(g->rho, 1.0 - 1e-12);
+        g->omega = g->P.ncol == 2 ? 2.0 / (1.0 + std::sqrt(1.0 - r * r)) : 1.0;
+    }
+    // kappa >= ||M^-1 D||_inf: solve M x = D 1 to max|r|/D <= 1e-3, then bound the remainder.
+    g->kappa = 1.0;
+    double R = 0.0;
+    const double save_omega = g->omega;
+    if ((s = solve_internal(g, g->dg.D64, 1e-3, &R))) { g->h = -1.0; return s; }
+    double xm = host_max(g, g->d_x, g->P.n, &s);
+    if (s) return s;
+    g->kappa = xm / (1.0 - R);
+    // q >= ||M^-1 C/h||_inf: solve M y = (C/h) 1 and bound the remainder with kappa.
+    double cmax = 0.0;
+    for (int i = 0; i < g->P.n; ++i) cmax = std::max(cmax, g->P.cap[i] / h);
+    if (cmax > 0.0) {
+        // a remainder of at most 1e-6 on q: max|r|/D <= 1e-6 / kappa
+        if ((s = solve_internal(g, g->dg.ch, 1e-6 / g->kappa, &R))) { g->h = -1.0; return s; }
+        const double ym = host_max(g, g->d_x, g->P.n, &s);
+        if (s) return s;
+        g->q = ym + g->kappa * R;
+    } else {
+        g->q = 0.0;
+    }
+    g->omega = save_omega;
+    const double tol = g->opt.tol;
+    if (g->opt.step_tol > 0.0) g->step_tol = g->opt.step_tol;
+    else if (g->P.n_l > 0 || !(g->q < 1.0)) g->step_tol = 1e-4 * tol;
+    else g->step_tol = 0.5 * (1.0 - g->q) * tol;
+    const double slack = 1e-13;   // rounding allowance on max|r|/D (V)
+    g->target = g->step_tol / g->kappa - slack;
+    if (!(g->target > 0.0)) {
+        g_last_error = "tolerance below the rounding floor (kappa " + std::to_string(g->kappa) + ", q " +
+                       std::to_string(g->q) + ", step_tol " + std::to_string(g->step_tol) + ")";
+        g->h = -1.0;
+        return PG_ERR_INVALID_ARG;
+    }
+    return PG_OK;
+}
+
+pg_status set_state_host(pg_grid* g, const double* v, const double* il, int64_t step) {
+    const Packed& P = g->P;
+    std::vector<double> vp(P.n_pad, 0.0);
+    for (int i = 0; i < P.n_pad; ++i)
+        if (P.orig[i] >= 0) vp[i] = v[P.orig[i]];
+    g->vL = 0; g->vP = 1;
+    pg_status s;
+    if ((s = upload(g, g->ds.v[0], vp))) return s;
+    if (P.n_l) {
+        if (il) CK(cudaMemcpyAsync(g->ds.il, il, P.n_l * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+        else CK(cudaMemsetAsync(g->ds.il, 0, P.n_l * sizeof(double), g->stream));
+    }
+    CK(cudaStreamSynchronize(g->stream));
+    g->has_state = true;
+    g->step = step;
+    g->have_prev = false;
+    return PG_OK;
+}
+
+// State from a device vector in caller numbering (src) or a constant (src == nullptr).
+pg_status set_state_device(pg_grid* g, const double* src, double fill, const double* il, int64_t step) {
+    g->vL = 0; g->vP = 1;
+    CK(launch_permute_in(g->dg.orig, src, fill, g->ds.v[0], g->P.n_pad, g->n_sm, g->stream));
+    if (g->P.n_l) {
+        if (il) CK(cudaMemcpyAsync(g->ds.il, il, g->P.n_l * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+        else CK(cudaMemsetAsync(g->ds.il, 0, g->P.n_l * sizeof(double), g->stream));
+    }
+    g->has_state = true;
+    g->step = step;
+    g->have_prev = false;
+    return PG_OK;
+}
+
+pg_status create_impl(const pg_netlist* nl, const pg_options* opt, std::unique_ptr<pg_grid>& out);
+
+// DC operating point at t = 0 (Section IV-B, first step): capacitors open, i_l(0) = 0.
+pg_status dc_init(pg_grid* g) {
+    if (g->dc_trivial) return set_state_device(g, nullptr, g->dc_vdd, nullptr, 0);
+    if (!g->dcgrid) {
+        pg_netlist d = g->nc.dc_view();
+        pg_options o = g->opt;
+        o.precision = PG_PREC_FP64;
+        o.omega = 0.0;
+        o.step_tol = 0.0;
+        std::unique_ptr<pg_grid> sub;
+        pg_status s = create_impl(&d, &o, sub);
+        if (s == PG_ERR_FLOATING_NODE)
+            g_last_error = "DC operating point needs every sub-circuit tied to a source or ground by a resistor: " +
+                           g_last_error;
+        if (s) return s;
+        sub->stream = g->stream;
+        g->dcgrid = std::move(sub);
+    }
+    pg_grid* d = g->dcgrid.get();
+    d->stream = g->stream;
+    double vmean = 0.0;
+    for (double x : g->nc.vdd) vmean += x;
+    vmean = g->nc.vdd.empty() ? 0.0 : vmean / g->nc.vdd.size();
+    pg_status s;
+    // The DC network has no C and no L, so its coefficients do not depend on h (any h > 0
+    // assembles them); its solve target follows the main grid's per-step target.
+    d->opt.step_tol = g->step_tol > 0.0 ? g->step_tol : 0.5 * g->opt.tol;
+    if ((s = prepare_h(d, 1.0))) return s;
+    if ((s = set_state_device(d, nullptr, vmean, nullptr, -1))) return s;
+    RunParams rp = base_params(d);
+    rp.mode = kModeTransient;
+    rp.nsteps = 1;
+    rp.step0 = -1;   // one step landing on t = 0
+    rp.have_prev = 0;
+    rp.solve_out = d->d_x;
+    double stats[kStatCount];
+    if ((s = run(d, rp, stats, nullptr))) return s;
+    return set_state_device(g, d->d_x, 0.0, nullptr, 0);
+}
+
+pg_status create_impl(const pg_netlist* nl, const pg_options* opt, std::unique_ptr<pg_grid>& out) {
+    std::unique_ptr<pg_grid> g(new pg_grid());
+    pg_default_options(&g->opt);
+    if (opt) g->opt = *opt;
+    pg_options& o = g->opt;
+    if (o.precision != PG_PREC_FP64 && o.precision != PG_PREC_MIXED) { g_last_error = "bad precision"; return PG_ERR_INVALID_ARG; }
+    if (o.omega < 0.0 || o.omega >= 2.0 || !std::isfinite(o.omega)) {
+        g_last_error = "omega must be in (0, 2) (Eq. 17), or 0 for automatic";
+        return PG_ERR_INVALID_ARG;
+    }
+    if (o.tol <= 0.0) o.tol = 1e-6;
+    if (o.max_sweeps <= 0) o.max_sweeps = 20000;
+    if (o.inner_reduction <= 0.0) o.inner_reduction = 1e-3;
+    if (o.threads_per_block <= 0) o.threads_per_block = 256;
+    if (o.threads_per_block != 256) { g_last_error = "threads_per_block must be 256"; return PG_ERR_INVALID_ARG; }
+    if (o.barrier_timeout_s <= 0.0) o.barrier_timeout_s = 2.0;
+    g->threads = o.threads_per_block;
+    g->mixed = o.precision == PG_PREC_MIXED;
+    std::string why;
+    pg_status s = build_packed(nl, &g->P, &why);
+    if (s) { g_last_error = why; return s; }
+    g->nc.from(nl);
+    compute_dc_trivial(g.get());
+    CK(cudaGetDevice(&g->device));
+    CK(cudaDeviceGetAttribute(&g->n_sm, cudaDevAttrMultiProcessorCount, g->device));
+    int coop = 0;
+    CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device));
+    if (!coop) { g_last_error = "device lacks cooperative launch"; return PG_ERR_CUDA; }
+    if ((s = alloc_device(g.get()))) return s;
+    out = std::move(g);
+    return PG_OK;
+}
+
+pg_status fill_stats(pg_grid* g, const double* st, float ms, pg_run_stats* out) {
+    if (!out) return PG_OK;
+    std::memset(out, 0, sizeof(*out));
+    out->steps_done = (int64_t)st[kStatSteps];
+    out->total_sweeps = (int64_t)st[kStatSweeps];
+    out->max_sweeps_step = (int32_t)st[kStatMaxSweeps];
+    out->total_outer = (int64_t)st[kStatOuter];
+    out->max_outer_step = (int32_t)st[kStatMaxOuter];
+    out->max_step_bound = g->kappa * (st[kStatMaxBound] + 1e-13);
+    out->err_bound = (g->P.n_l == 0 && g->q < 1.0) ? out->max_step_bound / (1.0 - g->q) : NAN;
+    out->failed_step = (int64_t)st[kStatFailedStep];
+    out->omega = g->omega;
+    out->rho_jacobi = g->rho;
+    out->kappa = g->kappa;
+    out->q = g->q;
+    out->step_tol = g->step_tol;
+    out->device_ms = ms;
+    return PG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pg_default_options(pg_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = PG_PREC_FP64;
+    o->omega = 0.0;
+    o->tol = 1e-6;
+    o->step_tol = 0.0;
+    o->max_sweeps = 20000;
+    o->warm_start = 1;
+    o->inner_reduction = 1e-3;
+    o->threads_per_block = 256;
+    o->blocks_per_sm = 0;
+    o->barrier_timeout_s = 2.0;
+    o->debug_flags = 0;
+}
+
+const char* pg_status_str(pg_status s) {
+    switch (s) {
+        case PG_OK: return "PG_OK";
+        case PG_ERR_INVALID_ARG: return "PG_ERR_INVALID_ARG";
+        case PG_ERR_FLOATING_NODE: return "PG_ERR_FLOATING_NODE";
+        case PG_ERR_OOM: return "PG_ERR_OOM";
+        case PG_ERR_CUDA: return "PG_ERR_CUDA";
+        case PG_ERR_NOT_CONVERGED: return "PG_ERR_NOT_CONVERGED";
+        case PG_ERR_TIMEOUT: return "PG_ERR_TIMEOUT";
+        case PG_ERR_UNSUPPORTED: return "PG_ERR_UNSUPPORTED";
+    }
+    return "PG_ERR_UNKNOWN";
+}
+
+// Human-readable detail of the last error on this thread (not part of the
+// stable ABI contract; useful in bindings and logs).
+const char* pg_last_error(void) { return g_last_error.c_str(); }
+
+pg_status pg_create_grid(const pg_netlist* nl, const pg_options* opt, pg_grid** out) {
+    if (!out) return PG_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::unique_ptr<pg_grid> g;
+    pg_status s;
+    try {
+        s = create_impl(nl, opt, g);
+    } catch (const std::bad_alloc&) {
+        g_last_error = "host allocation failed";
+        return PG_ERR_OOM;
+    }
+    if (s) return s;
+    *out = g.release();
+    return PG_OK;
+}
+
+void pg_destroy(pg_grid* g) { delete g; }
+
+pg_status pg_set_stream(pg_grid* g, void* stream) {
+    if (!g) return PG_ERR_INVALID_ARG;
+    g->stream = static_cast<cudaStream_t>(stream);
+    if (g->dcgrid) g->dcgrid->stream = g->stream;
+    return PG_OK;
+}
+
+pg_status pg_grid_info(const pg_grid* g, int32_t* n, int32_t* nl, int32_t* ncol, int32_t* npad) {
+    if (!g) return PG_ERR_INVALID_ARG;
+    if (n) *n = g->P.n;
+    if (nl) *nl = g->P.n_l;
+    if (ncol) *ncol = g->P.ncol;
+    if (npad) *npad = g->P.n_pad;
+    return PG_OK;
+}
+
+pg_status pg_set_state(pg_grid* g, const double* v, const double* il, int64_t step, int32_t on_host) {
+    if (!g) return PG_ERR_INVALID_ARG;
+    if (!v) {
+        g->has_state = false;
+        return PG_OK;
+    }
+    if (!on_host) return set_state_device(g, v, 0.0, il, step);
+    return set_state_host(g, v, il, step);
+}
+
+pg_status pg_get_state(pg_grid* g, double* v, double* il, int64_t* step, int32_t on_host) {
+    if (!g) return PG_ERR_INVALID_ARG;
+    if (!g->has_state) { g_last_error = "no state"; return PG_ERR_INVALID_ARG; }
+    const Packed& P = g->P;
+    if (v) {
+        std::vector<double> vp(P.n_pad), out(P.n);
+        CK(cudaMemcpyAsync(vp.data(), g->ds.v[g->vL], P.n_pad * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+        for (int i = 0; i < P.n_pad; ++i)
+            if (P.orig[i] >= 0) out[P.orig[i]] = vp[i];
+        if (on_host) std::memcpy(v, out.data(), P.n * sizeof(double));
+        else CK(cudaMemcpy(v, out.data(), P.n * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    if (il && P.n_l) {
+        CK(cudaMemcpyAsync(il, g->ds.il, P.n_l * sizeof(double),
+                           on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+    }
+    if (step) *step = g->step;
+    return PG_OK;
+}
+
+pg_status pg_reset(pg_grid* g) {
+    if (!g) return PG_ERR_INVALID_ARG;
+    g->has_state = false;
+    return PG_OK;
+}
+
+pg_status pg_update_sources(pg_grid* g, const double* i_t, const double* i_v, int32_t on_host) {
+    if (!g) return PG_ERR_INVALID_ARG;
+    const size_t m = g->P.pwl_t.size();
+    if (m == 0) return PG_OK;
+    auto pull = [&](const double* src, std::vector<double>& dst) -> pg_status {
+        if (on_host) std::memcpy(dst.data(), src, m * sizeof(double));
+        else CK(cudaMemcpy(dst.data(), src, m * sizeof(double), cudaMemcpyDeviceToHost));
+        return PG_OK;
+    };
+    std::vector<double> t = g->nc.i_t, v = g->nc.i_v;
+    pg_status s;
+    if (i_t && (s = pull(i_t, t))) return s;
+    if (i_v && (s = pull(i_v, v))) return s;
+    for (size_t e = 0; e + 1 < g->nc.i_ptr.size(); ++e)
+        for (int64_t k = g->nc.i_ptr[e]; k < g->nc.i_ptr[e + 1]; ++k) {
+            if (!std::isfinite(t[k]) || !std::isfinite(v[k])) { g_last_error = "non-finite PWL"; return PG_ERR_INVALID_ARG; }
+            if (k > g->nc.i_ptr[e] && t[k] < t[k - 1]) { g_last_error = "PWL times must be non-decreasing"; return PG_ERR_INVALID_ARG; }
+        }
+    if (i_t) {
+        CK(cudaMemcpyAsync(const_cast<double*>(g->dg.pwl_t), i_t, m * sizeof(double),
+                           on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, g->stream));
+        g->nc.i_t = t;
+    }
+    if (i_v) {
+        CK(cudaMemcpyAsync(const_cast<double*>(g->dg.pwl_v), i_v, m * sizeof(double),
+                           on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, g->stream));
+        g->nc.i_v = v;
+    }
+    compute_dc_trivial(g);
+    g->dcgrid.reset();
+    return PG_OK;
+}
+
+pg_status pg_transient(pg_grid* g, double h, int32_t nsteps, const pg_output* out, pg_run_stats* stats) {
+    if (!g || nsteps < 0) return PG_ERR_INVALID_ARG;
+    pg_status s = prepare_h(g, h);
+    if (s) return s;
+    if (!g->has_state && (s = dc_init(g))) return s;
+    if (nsteps == 0) {
+        double z[kStatCount] = {0};
+        z[kStatFailedStep] = -1;
+        return fill_stats(g, z, 0.f, stats);
+    }
+    RunParams rp = base_params(g);
+    rp.mode = kModeTransient;
+    rp.nsteps = nsteps;
+    rp.step0 = g->step;
+    rp.have_prev = g->have_prev;
+    const Packed& P = g->P;
+    // outputs: device pointers directly, or device staging for host pointers
+    const bool host = out && out->on_host;
+    std::vector<void*> tmp;
+    auto stage = [&](void* user, size_t bytes) -> void* {
+        if (!user) return nullptr;
+        if (!host) return user;
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+        tmp.push_back(p);
+        return p;
+    };
+    auto cleanup = [&]() { for (void* p : tmp) cudaFree(p); };
+    int32_t* probes_perm = nullptr;
+    if (out) {
+        rp.v_all = (double*)stage(out->v_all, (size_t)nsteps * P.n * sizeof(double));
+        rp.il_all = P.n_l ? (double*)stage(out->il_all, (size_t)nsteps * P.n_l * sizeof(double)) : nullptr;
+        rp.vmin = (double*)stage(out->vmin, (size_t)nsteps * sizeof(double));
+        rp.vmin_node = (int32_t*)stage(out->vmin_node, (size_t)nsteps * sizeof(int32_t));
+        if (out->n_probes > 0 && out->probes && out->probe_v) {
+            std::vector<int32_t> pr(out->n_probes);
+            if (host) std::memcpy(pr.data(), out->probes, pr.size() * sizeof(int32_t));
+            else if (cudaMemcpy(pr.data(), out->probes, pr.size() * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                cleanup();
+                return PG_ERR_CUDA;
+            }
+            for (auto& x : pr) {
+                if (x < 0 || x >= P.n) { cleanup(); g_last_error = "probe out of range"; return PG_ERR_INVALID_ARG; }
+                x = P.perm[x];
+            }
+            if (cudaMalloc((void**)&probes_perm, pr.size() * sizeof(int32_t)) != cudaSuccess) { cleanup(); return PG_ERR_OOM; }
+            tmp.push_back(probes_perm);
+            cudaMemcpy(probes_perm, pr.data(), pr.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+            rp.n_probes = out->n_probes;
+            rp.probes_perm = probes_perm;
+            rp.probe_v = (double*)stage(out->probe_v, (size_t)nsteps * out->n_probes * sizeof(double));
+        }
+        if ((out->v_all && !rp.v_all) || (out->vmin && !rp.vmin)) { cleanup(); return PG_ERR_OOM; }
+    }
+    double st[kStatCount];
+    float ms = 0.f;
+    s = run(g, rp, st, &ms);
+    // advance the state by the steps that completed
+    const int64_t done = (int64_t)st[kStatSteps];
+    for (int64_t k = 0; k < done; ++k) {
+        const int vF = 3 - g->vL - g->vP;
+        g->vP = g->vL;
+        g->vL = vF;
+    }
+    g->step += done;
+    if (done > 0) g->have_prev = true;
+    if (host && out) {
+        auto back = [&](void* user, void* dev, size_t bytes) {
+            if (user && dev && bytes) cudaMemcpy(user, dev, bytes, cudaMemcpyDeviceToHost);
+        };
+        back(out->v_all, rp.v_all, (size_t)done * P.n * sizeof(double));
+        back(out->il_all, rp.il_all, (size_t)done * P.n_l * sizeof(double));
+        back(out->vmin, rp.vmin, (size_t)done * sizeof(double));
+        back(out->vmin_node, rp.vmin_node, (size_t)done * sizeof(int32_t));
+        back(out->probe_v, rp.probe_v, (size_t)done * rp.n_probes * sizeof(double));
+    }
+    cleanup();
+    fill_stats(g, st, ms, stats);
+    return s;
+}
+
+pg_status pg_step(pg_grid* g, double h, double* v_out, pg_run_stats* stats) {
+    pg_output o{};
+    o.v_all = v_out;
+    return pg_transient(g, h, 1, v_out ? &o : nullptr, stats);
+}
+
+pg_status pg_solve(pg_grid* g, double h, const double* b, double* x, double tol, pg_run_stats* stats) {
+    if (!g || !b || !x || !(tol > 0.0)) return PG_ERR_INVALID_ARG;
+    pg_status s = prepare_h(g, h);
+    if (s) return s;
+    const Packed& P = g->P;
+    std::vector<double> hb(P.n), bp(P.n_pad, 0.0);
+    CK(cudaMemcpy(hb.data(), b, P.n * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < P.n_pad; ++i)
+        if (P.orig[i] >= 0) bp[i] = hb[P.orig[i]];
+    double* d_b = nullptr;
+    CK(cudaMalloc(&d_b, P.n_pad * sizeof(double)));
+    cudaMemcpy(d_b, bp.data(), P.n_pad * sizeof(double), cudaMemcpyHostToDevice);
+    RunParams rp = base_params(g);
+    rp.mode = kModeSolve;
+    rp.nsteps = 1;
+    rp.target = tol / g->kappa - 1e-13;
+    rp.solve_out = x;
+    g->ds.rhs = d_b;
+    double st[kStatCount];
+    float ms = 0.f;
+    if (!(rp.target > 0.0)) { cudaFree(d_b); g->ds.rhs = nullptr; return PG_ERR_INVALID_ARG; }
+    s = run(g, rp, st, &ms);
+    g->ds.rhs = nullptr;
+    cudaFree(d_b);
+    fill_stats(g, st, ms, stats);
+    return s;
+}
+
+}  // extern "C"

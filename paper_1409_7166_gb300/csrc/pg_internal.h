@@ -1,0 +1,169 @@
+// Internal structures shared by the host builder, the C ABI and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pg.h"
+
+namespace pg {
+
+constexpr int kVec = 4;                 // nodes per thread (128-bit vector loads)
+constexpr int kSlice = 32 * kVec;       // nodes per SELL slice (one warp)
+constexpr int kMaxColours = 16;
+constexpr int kRedSlots = 4;            // rotating reduction slots
+
+// ---------------------------------------------------------------- host side
+
+// Result of validation, colouring and packing (independent of h).
+struct Packed {
+    int32_t n = 0;          // caller's nodes
+    int32_t n_pad = 0;      // permuted nodes incl. padding (multiple of kSlice)
+    int32_t p = 0;          // source nodes
+    int32_t ncol = 0;
+    int32_t colour_start[kMaxColours + 1] = {0};  // node index, multiple of kSlice
+    std::vector<int32_t> perm;        // caller id -> permuted index
+    std::vector<int32_t> orig;        // permuted index -> caller id (-1 = padding)
+    std::vector<double> vdd;
+
+    // merged neighbour lists in caller numbering (CSR): conductance part and 1/L part
+    std::vector<int64_t> adj_ptr;
+    std::vector<int32_t> adj_nbr;
+    std::vector<double> adj_g, adj_il;
+    // per caller node: grounded parts
+    std::vector<double> g_gnd, il_gnd, cap, inj_g, inj_il;
+
+    // SELL slices over the permuted index space
+    int32_t n_slices = 0;
+    std::vector<int64_t> slice_off;   // [n_slices+1] element offset of the slice's slots
+    std::vector<int32_t> slice_w;     // slots per node in the slice
+    std::vector<int32_t> slice_doff;  // [n_slices+1] offset into dia_off (== itself if explicit)
+    std::vector<int32_t> dia_off;     // per diagonal slice: slice_w column offsets
+    std::vector<int32_t> ell_col;     // explicit columns (only explicit slices fill them)
+    std::vector<int64_t> ell_adj;     // slot -> adjacency entry (-1 = empty slot)
+    int64_t n_ell = 0;
+    int32_t n_dia_slices = 0;
+
+    // loads: per permuted node CSR of signed source ids (+(e+1) leaves the node, -(e+1) enters)
+    std::vector<int32_t> ld_ptr, ld_idx;
+    std::vector<int64_t> pwl_ptr;
+    std::vector<double> pwl_t, pwl_v;
+
+    // inductors
+    int32_t n_l = 0;
+    std::vector<int32_t> ind_a, ind_b;        // permuted node, or terminal code (< 0)
+    std::vector<double> ind_invL;
+    std::vector<int32_t> ind_ptr, ind_idx;    // per permuted node CSR of signed inductor ids
+
+    // components (connected sub-circuits, Fig. 1)
+    int32_t n_comp = 0;
+    std::vector<uint8_t> comp_has_r_anchor;
+    std::vector<int32_t> comp_of;             // caller id -> component
+};
+
+pg_status build_packed(const pg_netlist* nl, Packed* out, std::string* why);
+
+// ---------------------------------------------------------------- device side
+
+// Everything one launch of the persistent kernel reads or writes.
+struct DevGrid {
+    int32_t n_pad, ncol, n_slices, n_real;
+    const int32_t* colour_slice;   // [ncol + 1] first slice of each colour (device copy)
+    const int64_t* slice_off;
+    const int32_t* slice_w;
+    const int32_t* slice_doff;
+    const int32_t* dia_off;
+    const int32_t* ell_col;
+    const double* w64;
+    const float* w32;
+    const double* D64;
+    const double* invD64;
+    const float* invD32;
+    const double* ch;        // C_i / h
+    const double* cinj;      // constant source injection: sum g Vk + h sum Vk / L
+    const int32_t* orig;
+    const int32_t* ld_ptr;
+    const int32_t* ld_idx;
+    const int64_t* pwl_ptr;
+    const double* pwl_t;
+    const double* pwl_v;
+    int32_t n_l;
+    const int32_t* ind_a;
+    const int32_t* ind_b;
+    const double* ind_hl;    // h / L
+    const int32_t* ind_ptr;
+    const int32_t* ind_idx;
+    const double* vdd;
+};
+
+enum Mode : int32_t { kModeTransient = 0, kModeSolve = 1 };
+
+struct DevState {
+    double* v[3];            // rotating node-voltage buffers (permuted)
+    double* il;              // inductor currents
+    double* r64;             // FP64 residual b - M v
+    float* r32;              // FP32 copy of the residual (mixed precision)
+    double* d64[2];          // correction buffers (FP64 sweeps)
+    float* d32[2];           // correction buffers (FP32 sweeps)
+    const double* rhs;       // kModeSolve: right-hand side (permuted)
+};
+
+struct DevCtl {
+    unsigned int* bar_count;
+    unsigned int* bar_gen;
+    int32_t* err;
+    unsigned long long* red;        // [kRedSlots] max reductions (double bits)
+    unsigned long long* blk_min;    // [2 * nblocks] per-block min keys (double bits, ordered)
+    int32_t* blk_arg;               // [2 * nblocks]
+    double* stats;                  // device statistics, see kStat*
+};
+
+enum Stat : int {
+    kStatSteps = 0, kStatSweeps, kStatMaxSweeps, kStatOuter, kStatMaxOuter,
+    kStatMaxBound, kStatFailedStep, kStatLastR, kStatCount
+};
+
+struct RunParams {
+    int32_t mode;
+    int32_t mixed;            // 1: FP32 sweeps
+    int32_t nsteps;
+    int64_t step0;            // absolute index of the state at launch (time = step * h)
+    double h;
+    int32_t cur, prev, prev2; // buffer indices of v at launch: current (= step0), previous
+    int32_t have_prev;        // previous step exists (for extrapolation)
+    int32_t warm_extrap;
+    double omega;
+    double kappa;             // bound constant ||M^-1 D||_inf
+    double target;            // per-step target on max |r_i| / D_i  (= step_tol / kappa)
+    double inner_reduction;
+    int32_t max_sweeps;
+    int32_t max_outer;
+    double slack;             // rounding allowance added to the certified bound
+    long long timeout_ns;
+    int32_t debug_flags;
+    // outputs (device pointers, may be null)
+    double* v_all;
+    double* il_all;
+    double* vmin;
+    int32_t* vmin_node;
+    int32_t n_probes;
+    const int32_t* probes_perm;
+    double* probe_v;
+    double* solve_out;        // kModeSolve: x in caller numbering
+};
+
+}  // namespace pg
+
+// ---------------------------------------------------------------- launch helpers (pg_kernels.cu)
+#include <cuda_runtime.h>
+
+namespace pg {
+cudaError_t launch_persistent(bool mixed, const DevGrid& g, const DevState& st, const DevCtl& ctl,
+                              const RunParams& rp, int blocks, int threads, cudaStream_t stream);
+cudaError_t persistent_occupancy(bool mixed, int threads, int* blocks_per_sm);
+cudaError_t launch_power_step(const DevGrid& g, const double* x, double* y, const unsigned long long* xmax_prev,
+                              double* acc, unsigned long long* ymax, int blocks, cudaStream_t stream);
+cudaError_t launch_permute_in(const int32_t* orig, const double* src, double fill, double* dst, int n_pad,
+                              int n_sm, cudaStream_t stream);
+}  // namespace pg

@@ -1,0 +1,221 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Every comparison is element by element against the oracle's direct-solve
+trajectory on the same seeded netlist.  The tolerance is the contract's
+1e-6 V max-abs on node voltages; the library's own certified bound must also
+be below it.
+"""
+import numpy as np
+import pytest
+
+import pgsynth
+from pgsynth import GROUND, make_netlist, source_terminal as S
+from oracle import bounds, transient
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_V = 1e-6
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1409_7166_gb300 import binding
+    return binding
+
+
+def run_gpu(B, net, h, nsteps, precision, **opts):
+    with B.Grid(net, precision=precision, **opts) as g:
+        B.pg_set_stream(g.handle, torch.cuda.current_stream().cuda_stream)
+        V = torch.empty((nsteps, net.n_nodes), dtype=torch.float64, device="cuda")
+        nl = len(net.l_val)
+        IL = torch.empty((nsteps, max(nl, 1)), dtype=torch.float64, device="cuda") if nl else None
+        vmin = torch.empty(nsteps, dtype=torch.float64, device="cuda")
+        vnode = torch.empty(nsteps, dtype=torch.int32, device="cuda")
+        st = B.pg_transient(g.handle, h, nsteps, v_all=V, il_all=IL, vmin=vmin, vmin_node=vnode)
+        torch.cuda.synchronize()
+        return (V.cpu().numpy(), None if IL is None else IL.cpu().numpy(), vmin.cpu().numpy(),
+                vnode.cpu().numpy(), st)
+
+
+def check_against_oracle(B, net, h, nsteps, precision, **opts):
+    Vo, ILo = transient.transient(net, h, nsteps)
+    V, IL, vmin, vnode, st = run_gpu(B, net, h, nsteps, precision, **opts)
+    err = np.max(np.abs(V - Vo[1:]))
+    assert err <= TOL_V, f"max |v - v_oracle| = {err:.3e} V"
+    if IL is not None:
+        il_err = np.max(np.abs(IL - ILo[1:]))
+        assert il_err <= 1e-3 * max(np.max(np.abs(ILo)), 1e-6), f"inductor current error {il_err:.3e} A"
+    # per-step worst drop: the value matches; the node attains the minimum of the GPU field
+    np.testing.assert_allclose(vmin, Vo[1:].min(axis=1), rtol=0, atol=TOL_V)
+    assert np.all(V[np.arange(nsteps), vnode] == vmin)
+    assert st.steps_done == nsteps and st.failed_step == -1
+    assert st.max_step_bound <= st.step_tol * 1.0000001
+    return err, st
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_config0_full_size(B, precision):
+    """RC 100x100 mesh, 100 steps of 10 ps: every node, every step."""
+    net = pgsynth.config0()
+    err, st = check_against_oracle(B, net, net.meta["h"], net.meta["nsteps"], precision)
+    assert st.err_bound <= TOL_V
+
+
+def test_config1_recipe_ragged(B):
+    """3-layer recipe at 97x61x3 (odd sides: colours of unequal size, ragged last slice),
+    FP32 sweeps with FP64 defect correction."""
+    net = pgsynth.config1(nx=97, ny=61)
+    check_against_oracle(B, net, net.meta["h"], 60, 1)
+
+
+def test_config2_recipe_rlc(B):
+    """RLC recipe (R||L vias and pads) at 40x33x2, FP64, 300 steps of 2 ps."""
+    net = pgsynth.config2(nx=40, ny=33)
+    check_against_oracle(B, net, net.meta["h"], 300, 0)
+
+
+def test_config3_recipe_batched(B):
+    """Several independent grids of uneven size in one netlist (components)."""
+    net = pgsynth.config3(n_grids=5, side_lo=17, side_hi=45)
+    check_against_oracle(B, net, net.meta["h"], 40, 1)
+
+
+def test_non_bipartite_multicolour(B):
+    """A triangulated mesh is not 2-colourable: the greedy multicolour path."""
+    n = 12
+    ids = np.arange(n * n).reshape(n, n)
+    rng = np.random.default_rng(5)
+    R = []
+    for y in range(n):
+        for x in range(n):
+            if x + 1 < n: R.append((ids[y, x], ids[y, x + 1], rng.uniform(0.5, 2)))
+            if y + 1 < n: R.append((ids[y, x], ids[y + 1, x], rng.uniform(0.5, 2)))
+            if x + 1 < n and y + 1 < n: R.append((ids[y, x], ids[y + 1, x + 1], rng.uniform(0.5, 2)))
+    R += [(ids[0, 0], S(0), 10.0), (ids[n - 1, n - 1], S(0), 10.0)]
+    C = [(int(i), GROUND, rng.uniform(10e-15, 100e-15)) for i in range(n * n)]
+    I = [(int(i), GROUND, [0.0, 30e-12, 90e-12], [0.0, rng.uniform(0, 1e-3), 0.0])
+         for i in rng.choice(n * n, 30, replace=False)]
+    net = make_netlist(n * n, [1.0], R=R, C=C, I=I)
+    info_net = net
+    err, st = check_against_oracle(B, info_net, 10e-12, 20, 0)
+    with B.Grid(net) as g:
+        assert g.info["n_colours"] >= 3
+
+
+def test_nontrivial_dc_initial_condition(B):
+    """Resistors to ground and loads already on at t = 0: the DC operating point
+    (capacitors open) is solved on the device before the first step."""
+    net = pgsynth.config0(nx=23, ny=19)
+    extra = np.arange(0, net.n_nodes, 37, dtype=np.int32)
+    net.r_a = np.concatenate([net.r_a, extra])
+    net.r_b = np.concatenate([net.r_b, np.full(extra.size, GROUND, np.int32)])
+    net.r_g = np.concatenate([net.r_g, np.full(extra.size, 0.05)])
+    net.i_v = net.i_v.copy()
+    net.i_v[0::3] = 2e-4                      # every load starts at 0.2 mA
+    check_against_oracle(B, net, net.meta["h"], 30, 0)
+
+
+def test_single_node_closed_form(B):
+    """One node (a slice of one real node and 127 padding nodes): the exact
+    discrete decay v_k - Vdd = (v0 - Vdd)(1 + h G0/C)^-k."""
+    C0, g0, h = 50e-15, 10.0, 1e-15
+    net = make_netlist(1, [1.0], R=[(0, S(0), g0)], C=[(0, GROUND, C0)])
+    with B.Grid(net) as g:
+        B.pg_set_state(g.handle, np.array([0.5]))
+        V = np.zeros((40, 1))
+        B.pg_transient(g.handle, h, 40, v_all=V)
+    k = np.arange(1, 41)
+    np.testing.assert_allclose(V[:, 0], 1.0 - 0.5 * (1 + h * g0 / C0) ** (-k), rtol=0, atol=TOL_V)
+
+
+def test_zero_load_is_exactly_vdd(B):
+    net = pgsynth.config1(nx=40, ny=24)
+    net.i_v[:] = 0.0
+    V, _, _, _, st = run_gpu(B, net, net.meta["h"], 10, 1)
+    assert np.all(V == 1.0) and st.total_sweeps == 0
+
+
+def test_bounds_are_upper_bounds(B):
+    """kappa >= ||M^-1 D||_inf and q >= ||M^-1 C/h||_inf (oracle, exact)."""
+    net = pgsynth.config0(nx=40, ny=30)
+    h = net.meta["h"]
+    _, _, _, _, st = run_gpu(B, net, h, 2, 0)
+    kx = bounds.scaled_minv_inf_norm(net, h)
+    qx = bounds.step_gain(net, h)
+    assert kx <= st.kappa <= kx * 1.01
+    assert qx <= st.q <= qx + 0.01
+
+
+def test_resume_equals_one_run(B):
+    """get/set state: 20 + 20 steps from a saved state equal 40 steps at once."""
+    net = pgsynth.config0(nx=30, ny=26)
+    h = net.meta["h"]
+    V1, _, _, _, _ = run_gpu(B, net, h, 40, 0)
+    with B.Grid(net) as g:
+        B.pg_transient(g.handle, h, 20)
+        v = np.zeros(net.n_nodes)
+        step = B.pg_get_state(g.handle, v)
+        assert step == 20
+    with B.Grid(net) as g2:
+        B.pg_set_state(g2.handle, v, step=20)   # extrapolation restarts from V(s-1)
+        V2 = np.zeros((20, net.n_nodes))
+        B.pg_transient(g2.handle, h, 20, v_all=V2)
+    np.testing.assert_allclose(V2, V1[20:], rtol=0, atol=TOL_V)
+
+
+def test_step_lockstep_and_solve(B):
+    net = pgsynth.config0(nx=21, ny=18)
+    h = net.meta["h"]
+    Vo, _ = transient.transient(net, h, 5)
+    with B.Grid(net) as g:
+        out = torch.empty(net.n_nodes, dtype=torch.float64, device="cuda")
+        for s in range(1, 6):
+            B.pg_step(g.handle, h, out)
+            torch.cuda.synchronize()
+            assert np.max(np.abs(out.cpu().numpy() - Vo[s])) <= TOL_V
+        # pg_solve: M x = b against a direct solve
+        from oracle.matrices import nodal_matrices
+        M = nodal_matrices(net).system_matrix(h)
+        b = np.random.default_rng(0).uniform(-1e-3, 1e-3, net.n_nodes)
+        x_ref = transient.DirectSolver(M).solve(b)
+        bt = torch.tensor(b, device="cuda")
+        xt = torch.empty_like(bt)
+        B.pg_solve(g.handle, h, bt, xt, 1e-9)
+        torch.cuda.synchronize()
+        assert np.max(np.abs(xt.cpu().numpy() - x_ref)) <= 1e-9
+
+
+def test_update_sources_new_scenario(B):
+    net = pgsynth.config0(nx=26, ny=22)
+    h = net.meta["h"]
+    net2 = pgsynth.config0(nx=26, ny=22, seed=11)
+    net2.i_a = net.i_a; net2.i_b = net.i_b; net2.i_ptr = net.i_ptr   # same load sites, new waveforms
+    scen = pgsynth.Netlist(**{**net.__dict__, "i_t": net2.i_t, "i_v": net2.i_v})
+    Vo, _ = transient.transient(scen, h, 25)
+    with B.Grid(net) as g:
+        B.pg_transient(g.handle, h, 10)
+        B.pg_update_sources(g.handle, net2.i_t, net2.i_v)
+        B.pg_reset(g.handle)
+        V = np.zeros((25, net.n_nodes))
+        B.pg_transient(g.handle, h, 25, v_all=V)
+    assert np.max(np.abs(V - Vo[1:])) <= TOL_V
+
+
+def test_not_converged_and_timeout_are_reported(B):
+    net = pgsynth.config0(nx=30, ny=30)
+    h = net.meta["h"]
+    with B.Grid(net, max_sweeps=2) as g:
+        rc, st = B.pg_transient_status(g.handle, h, 50)
+        assert B.STATUS[rc] == "PG_ERR_NOT_CONVERGED"
+        assert st.failed_step >= 1
+    # a block that never arrives at the first barrier: the others give up after the limit
+    with B.Grid(net, debug_flags=B.PG_DEBUG_SKIP_ARRIVAL, barrier_timeout_s=0.05) as g:
+        rc, st = B.pg_transient_status(g.handle, h, 5)
+        assert B.STATUS[rc] == "PG_ERR_TIMEOUT"
+    # the context is still usable afterwards
+    check_against_oracle(B, pgsynth.config0(nx=12, ny=12), h, 5, 0)
