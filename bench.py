@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--nsteps", type=int, default=1000, help="BE steps per transient")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--case", action="store_true",
+                    help="profiling case: set up the grid, run one transient of --nsteps steps, exit")
     return ap.parse_args()
 
 
@@ -228,6 +230,11 @@ def main():
     B.pg_set_stream(grid.handle, stream.cuda_stream)
     vmin = torch.empty(nsteps, dtype=torch.float64, device="cuda")
     vnode = torch.empty(nsteps, dtype=torch.int32, device="cuda")
+    if args.case:                                      # launches: kappa solve, q solve, this transient
+        st = B.pg_transient(grid.handle, h, nsteps)
+        print(json.dumps({"case": WORKLOAD, "nsteps": nsteps, **st.as_dict()}), flush=True)
+        grid.close()
+        return
     st0 = B.pg_transient(grid.handle, h, 1)           # per-h setup (coefficients, omega, kappa, q)
     setup_s = time.time() - t0
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
