@@ -216,6 +216,32 @@ pg_status pg_step(pg_grid* g, double h, double* v_out, pg_run_stats* stats);
 pg_status pg_solve(pg_grid* g, double h, const double* b, double* x, double tol,
                    pg_run_stats* stats);
 
+/*
+ * pg_solve without device allocations.  The paper has no counterpart: this
+ * serves callers that cannot call cudaMalloc when they solve, e.g. processes
+ * whose device memory is reserved up front by another allocator or capped,
+ * or steady-state loops that must not allocate.  Same arguments, result and
+ * errors as pg_solve, with these differences:
+ *   - All scratch (permuted right-hand side, iterate, residuals, corrections,
+ *     barrier and reduction words, statistics) lives in one file-scope device
+ *     array of 32 MiB inside the library; every GPU that loads the library
+ *     holds it until the process exits.  Grids whose scratch would not fit
+ *     (about 830k padded nodes in FP64, 930k in mixed precision) are rejected
+ *     with PG_ERR_INVALID_ARG and a message naming the limit.
+ *   - The coefficients for h must already be assembled (one earlier pg_solve
+ *     or pg_transient with the same h); otherwise PG_ERR_INVALID_ARG.  The
+ *     call itself allocates no device memory and calls no allocating routine.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array and it keeps the last call's contents;
+ *     the call clears what must start at zero.  Calls that overlap on the GPU
+ *     (other streams, other threads, other grids) race on it: serialise them.
+ * b and x are device pointers in the caller's node numbering.
+ */
+pg_status pg_solve_noalloc(pg_grid* g, double h, const double* b, double* x, double tol,
+                           pg_run_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -72,7 +72,7 @@ class PGError(RuntimeError):
 _LIB = None
 EXPORTS = ["pg_default_options", "pg_create_grid", "pg_destroy", "pg_status_str", "pg_last_error",
            "pg_set_stream", "pg_grid_info", "pg_set_state", "pg_get_state", "pg_reset",
-           "pg_update_sources", "pg_transient", "pg_step", "pg_solve"]
+           "pg_update_sources", "pg_transient", "pg_step", "pg_solve", "pg_solve_noalloc"]
 
 
 def lib(path: Optional[str] = None) -> C.CDLL:
@@ -99,8 +99,9 @@ def lib(path: Optional[str] = None) -> C.CDLL:
     L.pg_transient.argtypes = [vp, C.c_double, C.c_int32, C.POINTER(pg_output), C.POINTER(pg_run_stats)]
     L.pg_step.argtypes = [vp, C.c_double, vp, C.POINTER(pg_run_stats)]
     L.pg_solve.argtypes = [vp, C.c_double, vp, vp, C.c_double, C.POINTER(pg_run_stats)]
+    L.pg_solve_noalloc.argtypes = [vp, C.c_double, vp, vp, C.c_double, C.POINTER(pg_run_stats)]
     for name in ("pg_create_grid", "pg_set_stream", "pg_grid_info", "pg_set_state", "pg_get_state",
-                 "pg_reset", "pg_update_sources", "pg_transient", "pg_step", "pg_solve"):
+                 "pg_reset", "pg_update_sources", "pg_transient", "pg_step", "pg_solve", "pg_solve_noalloc"):
         getattr(L, name).restype = C.c_int
     if path is None:
         _LIB = L
@@ -226,6 +227,14 @@ def pg_step(h, step_h: float, v_out=None) -> pg_run_stats:
 def pg_solve(h, step_h: float, b, x, tol: float) -> pg_run_stats:
     st = pg_run_stats()
     _check(lib().pg_solve(h, float(step_h), _ptr(b), _ptr(x), float(tol), C.byref(st)), "pg_solve")
+    return st
+
+
+def pg_solve_noalloc(h, step_h: float, b, x, tol: float) -> pg_run_stats:
+    """pg_solve without device allocations (fixed 32 MiB scratch inside the library)."""
+    st = pg_run_stats()
+    _check(lib().pg_solve_noalloc(h, float(step_h), _ptr(b), _ptr(x), float(tol), C.byref(st)),
+           "pg_solve_noalloc")
     return st
 
 
