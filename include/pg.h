@@ -96,7 +96,7 @@ typedef struct pg_options {
     double tol;               /* target max-abs voltage error of every step against the exact
                                  backward-Euler trajectory, V (0 -> 1e-6) */
     double step_tol;          /* per-step solve target, V; 0 -> derived from tol: RC grids use
-                                 0.5 (1 - q) tol, grids with inductors use 1e-4 tol */
+                                 0.5 tol / kacc (see pg_run_stats), grids with inductors 1e-4 tol */
     int32_t max_sweeps;       /* cap on relaxation sweeps per step (0 -> 20000) */
     int32_t warm_start;       /* 0: V(s-1) as in Algorithm 1; 1: linear extrapolation (default) */
     double inner_reduction;   /* PG_PREC_MIXED: residual reduction asked of one FP32 inner solve
@@ -182,7 +182,7 @@ typedef struct pg_run_stats {
     int32_t max_outer_step;     /* most defect-correction passes any step needed */
     int64_t total_outer;
     double max_step_bound;      /* largest certified per-step error bound, V */
-    double err_bound;           /* bound on the accumulated error (RC: sum rule with q), V */
+    double err_bound;           /* bound on the accumulated error, kacc * max_step_bound, V (RC) */
     int64_t failed_step;        /* step index of a failure, -1 if none */
     double omega;               /* SOR factor used */
     double rho_jacobi;          /* estimated Jacobi spectral radius (lower bound) */
@@ -190,6 +190,8 @@ typedef struct pg_run_stats {
     double q;                   /* upper bound of ||M^-1 C/h||_inf (RC error gain per step) */
     double step_tol;            /* per-step target actually used, V */
     double device_ms;           /* device time of the persistent launch(es), ms */
+    double kacc;                /* RC: upper bound of ||1 + (G + G0)^-1 (C/h) 1||_inf, the factor
+                                   turning per-step errors into the accumulated error; inf for RLC */
 } pg_run_stats;
 
 /*
@@ -215,6 +217,42 @@ pg_status pg_step(pg_grid* g, double h, double* v_out, pg_run_stats* stats);
  */
 pg_status pg_solve(pg_grid* g, double h, const double* b, double* x, double tol,
                    pg_run_stats* stats);
+
+/*
+ * Replace element values on the same topology (netlist order; any pointer may
+ * be NULL to keep those values).  The next call re-assembles the per-h
+ * coefficients.  Host or device memory per on_host.  Errors:
+ * PG_ERR_INVALID_ARG for a non-positive or non-finite value.
+ */
+pg_status pg_update_values(pg_grid* g, const double* r_g, const double* c_val, const double* l_val,
+                           int32_t on_host);
+
+/* Objective of pg_adjoint. */
+#define PG_OBJ_SOFTPLUS_DROP 0   /* J = sum_{s=1..nsteps} sum_i softplus(vref - v_{s,i} - margin)^2 */
+
+typedef struct pg_objective {
+    int32_t kind;     /* PG_OBJ_SOFTPLUS_DROP */
+    double vref;      /* reference voltage, V (the supply) */
+    double margin;    /* tolerated drop before the penalty grows, V */
+} pg_objective;
+
+/*
+ * Gradient of a worst-IR-drop objective over an RC transient (no counterpart in
+ * the paper; it differentiates the backward-Euler recurrence the paper solves,
+ * Eq. 2).  Runs nsteps steps from the DC operating point with a checkpoint every
+ * ckpt_every steps (0 -> 50), then the discrete adjoint backwards:
+ *     M lambda_s = dJ/dv_s + (C/h) lambda_{s+1},  lambda_{nsteps+1} = 0,
+ * each solve by the same relaxation kernel (relative residual 1e-9), recomputing
+ * each segment's states from its checkpoint.  Outputs (netlist order, either may
+ * be NULL): dJ_dG[n_r] = -sum_s (lambda_a - lambda_b)(v_a - v_b) per resistor,
+ * dJ_dC[n_c] = -sum_s lambda_k (v_{s,k} - v_{s-1,k}) / h per capacitor, plus the
+ * DC point's own adjoint term when the DC point depends on the resistors.  *J
+ * (host) receives the objective.  Host or device outputs per on_host.  The grid's
+ * transient state is reset afterwards.  Errors: PG_ERR_UNSUPPORTED for grids with
+ * inductors; otherwise as pg_transient.
+ */
+pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* obj, int32_t ckpt_every,
+                     double* J, double* dJ_dG, double* dJ_dC, int32_t on_host, pg_run_stats* stats);
 
 /*
  * pg_solve without device allocations.  The paper has no counterpart: this

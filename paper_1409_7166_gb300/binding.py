@@ -51,12 +51,16 @@ class pg_output(C.Structure):
                 ("probes", C.c_void_p), ("probe_v", C.c_void_p)]
 
 
+class pg_objective(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("vref", C.c_double), ("margin", C.c_double)]
+
+
 class pg_run_stats(C.Structure):
     _fields_ = [("steps_done", C.c_int64), ("total_sweeps", C.c_int64), ("max_sweeps_step", C.c_int32),
                 ("max_outer_step", C.c_int32), ("total_outer", C.c_int64), ("max_step_bound", C.c_double),
                 ("err_bound", C.c_double), ("failed_step", C.c_int64), ("omega", C.c_double),
                 ("rho_jacobi", C.c_double), ("kappa", C.c_double), ("q", C.c_double),
-                ("step_tol", C.c_double), ("device_ms", C.c_double)]
+                ("step_tol", C.c_double), ("device_ms", C.c_double), ("kacc", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -72,7 +76,8 @@ class PGError(RuntimeError):
 _LIB = None
 EXPORTS = ["pg_default_options", "pg_create_grid", "pg_destroy", "pg_status_str", "pg_last_error",
            "pg_set_stream", "pg_grid_info", "pg_set_state", "pg_get_state", "pg_reset",
-           "pg_update_sources", "pg_transient", "pg_step", "pg_solve", "pg_solve_noalloc"]
+           "pg_update_sources", "pg_transient", "pg_step", "pg_solve", "pg_solve_noalloc",
+           "pg_update_values", "pg_adjoint"]
 
 
 def lib(path: Optional[str] = None) -> C.CDLL:
@@ -100,8 +105,12 @@ def lib(path: Optional[str] = None) -> C.CDLL:
     L.pg_step.argtypes = [vp, C.c_double, vp, C.POINTER(pg_run_stats)]
     L.pg_solve.argtypes = [vp, C.c_double, vp, vp, C.c_double, C.POINTER(pg_run_stats)]
     L.pg_solve_noalloc.argtypes = [vp, C.c_double, vp, vp, C.c_double, C.POINTER(pg_run_stats)]
+    L.pg_update_values.argtypes = [vp, vp, vp, vp, C.c_int32]
+    L.pg_adjoint.argtypes = [vp, C.c_double, C.c_int32, C.POINTER(pg_objective), C.c_int32, _f64p, vp, vp,
+                             C.c_int32, C.POINTER(pg_run_stats)]
     for name in ("pg_create_grid", "pg_set_stream", "pg_grid_info", "pg_set_state", "pg_get_state",
-                 "pg_reset", "pg_update_sources", "pg_transient", "pg_step", "pg_solve", "pg_solve_noalloc"):
+                 "pg_reset", "pg_update_sources", "pg_transient", "pg_step", "pg_solve", "pg_solve_noalloc",
+                 "pg_update_values", "pg_adjoint"):
         getattr(L, name).restype = C.c_int
     if path is None:
         _LIB = L
@@ -228,6 +237,22 @@ def pg_solve(h, step_h: float, b, x, tol: float) -> pg_run_stats:
     st = pg_run_stats()
     _check(lib().pg_solve(h, float(step_h), _ptr(b), _ptr(x), float(tol), C.byref(st)), "pg_solve")
     return st
+
+
+def pg_update_values(h, r_g=None, c_val=None, l_val=None):
+    _check(lib().pg_update_values(h, _ptr(r_g), _ptr(c_val), _ptr(l_val), _on_host(r_g, c_val, l_val)),
+           "pg_update_values")
+
+
+def pg_adjoint(h, step_h: float, nsteps: int, vref: float = 1.0, margin: float = 0.05, ckpt_every: int = 50,
+               dJ_dG=None, dJ_dC=None):
+    """Returns ``(J, stats)``; gradients land in ``dJ_dG`` / ``dJ_dC`` (netlist order)."""
+    obj = pg_objective(0, float(vref), float(margin))
+    J = C.c_double()
+    st = pg_run_stats()
+    _check(lib().pg_adjoint(h, float(step_h), int(nsteps), C.byref(obj), int(ckpt_every), C.byref(J),
+                            _ptr(dJ_dG), _ptr(dJ_dC), _on_host(dJ_dG, dJ_dC), C.byref(st)), "pg_adjoint")
+    return J.value, st
 
 
 def pg_solve_noalloc(h, step_h: float, b, x, tol: float) -> pg_run_stats:

@@ -37,7 +37,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs.append(o)
         if force or _stale(o, [s] + HEADERS):
             cmd = [NVCC, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
-                   "-cudart", "shared", "-c", s, "-o", o]
+                   "-cudart", "shared", *os.environ.get("PG_EXTRA_NVCC_FLAGS", "").split(), "-c", s, "-o", o]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

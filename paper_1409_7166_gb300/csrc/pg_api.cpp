@@ -25,6 +25,19 @@ namespace {
 
 constexpr int kSetupSweeps = 200000;
 
+// Device buffers owned by one call, freed when it returns.
+struct DeviceScratch {
+    std::vector<void*> p;
+    ~DeviceScratch() { for (void* q : p) cudaFree(q); }
+    template <typename T>
+    T* get(size_t n) {
+        void* q = nullptr;
+        if (cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) return nullptr;
+        p.push_back(q);
+        return static_cast<T*>(q);
+    }
+};
+
 pg_status cuda_fail(cudaError_t e, const char* what) {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
     return PG_ERR_CUDA;
@@ -225,6 +238,7 @@ namespace {
 // One persistent launch; reads back the status word and statistics.
 pg_status run(pg_grid* g, const RunParams& rp, double* stats, float* ms) {
     CK(cudaMemsetAsync(g->dc.bar_count, 0, sizeof(unsigned), g->stream));
+    CK(cudaMemsetAsync(g->dc.bar_gen, 0, sizeof(unsigned), g->stream));
     CK(cudaMemsetAsync(g->dc.err, 0, sizeof(int32_t), g->stream));
     CK(cudaMemsetAsync(g->dc.red, 0, kRedSlots * sizeof(unsigned long long), g->stream));
     CK(cudaEventRecord(g->ev0, g->stream));
@@ -307,6 +321,55 @@ pg_status estimate_rho(pg_grid* g, double* rho) {
     return PG_OK;
 }
 
+pg_status create_impl(const pg_netlist* nl, const pg_options* opt, std::unique_ptr<pg_grid>& out);
+pg_status prepare_h(pg_grid* g, double h);
+
+// The resistive (DC) network of the grid: capacitors open, inductors open (i_l = 0).
+pg_status ensure_dc_grid(pg_grid* g) {
+    if (g->dcgrid) return PG_OK;
+    pg_netlist d = g->nc.dc_view();
+    pg_options o = g->opt;
+    o.precision = PG_PREC_FP64;
+    o.omega = 0.0;
+    o.step_tol = 0.5 * g->opt.tol;
+    std::unique_ptr<pg_grid> sub;
+    pg_status s = create_impl(&d, &o, sub);
+    if (s == PG_ERR_FLOATING_NODE)
+        g_last_error = "the resistive network needs every sub-circuit tied to a source or ground by a resistor: " +
+                       g_last_error;
+    if (s) return s;
+    sub->stream = g->stream;
+    g->dcgrid = std::move(sub);
+    return PG_OK;
+}
+
+// kacc >= 1 + ||(G + G0)^-1 (C/h) 1||_inf from one relaxation solve on the DC network, with the
+// remainder bounded by that network's own kappa.
+pg_status accumulation_bound(pg_grid* g, double h, double* kacc) {
+    pg_status s = ensure_dc_grid(g);
+    if (s) return s;
+    pg_grid* d = g->dcgrid.get();
+    d->stream = g->stream;
+    if ((s = prepare_h(d, 1.0))) return s;
+    std::vector<double> rhs(d->P.n_pad, 0.0);
+    for (int i = 0; i < d->P.n_pad; ++i)
+        if (d->P.orig[i] >= 0) rhs[i] = g->P.cap[d->P.orig[i]] / h;
+    double* rd = nullptr;
+    CK(cudaMalloc(&rd, rhs.size() * sizeof(double)));
+    if (cudaMemcpy(rd, rhs.data(), rhs.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(rd);
+        return PG_ERR_CUDA;
+    }
+    double R = 0.0;
+    s = solve_internal(d, rd, 1e-3 / d->kappa, &R);
+    cudaFree(rd);
+    if (s) return s;
+    const double zmax = host_max(d, d->d_x, d->P.n, &s);
+    if (s) return s;
+    *kacc = 1.0 + zmax + d->kappa * R;
+    return PG_OK;
+}
+
 // Per-h setup: coefficients, omega, and the stopping-rule constants kappa, q.
 pg_status prepare_h(pg_grid* g, double h) {
     if (g->h == h) return PG_OK;
@@ -343,10 +406,20 @@ pg_status prepare_h(pg_grid* g, double h) {
         g->q = 0.0;
     }
     g->omega = save_omega;
+    // Accumulation of per-step errors (RC).  With T = M^-1 C/h >= 0 the error of step s is
+    // e_s = T e_{s-1} + eta_s, so |e_s| <= max_k |eta_k| * sum_j T^j 1 = max|eta| (I - T)^-1 1, and
+    // (I - T)^-1 1 = 1 + (G + G0)^-1 (C/h) 1 because M = C/h + (G + G0).  kacc bounds its max with
+    // one solve on the resistive (DC) network; it never exceeds 1 / (1 - q).
+    g->kacc = INFINITY;
+    if (g->P.n_l == 0) {
+        if (cmax == 0.0) g->kacc = 1.0;
+        else if ((s = accumulation_bound(g, h, &g->kacc))) { g->h = -1.0; return s; }
+        if (g->q < 1.0) g->kacc = std::min(g->kacc, 1.0 / (1.0 - g->q));
+    }
     const double tol = g->opt.tol;
     if (g->opt.step_tol > 0.0) g->step_tol = g->opt.step_tol;
-    else if (g->P.n_l > 0 || !(g->q < 1.0)) g->step_tol = 1e-4 * tol;
-    else g->step_tol = 0.5 * (1.0 - g->q) * tol;
+    else if (std::isfinite(g->kacc)) g->step_tol = 0.5 * tol / g->kacc;
+    else g->step_tol = 1e-4 * tol;
     const double slack = 1e-13;   // rounding allowance on max|r|/D (V)
     g->target = g->step_tol / g->kappa - slack;
     if (!(g->target > 0.0)) {
@@ -391,42 +464,28 @@ pg_status set_state_device(pg_grid* g, const double* src, double fill, const dou
     return PG_OK;
 }
 
-pg_status create_impl(const pg_netlist* nl, const pg_options* opt, std::unique_ptr<pg_grid>& out);
-
 // DC operating point at t = 0 (Section IV-B, first step): capacitors open, i_l(0) = 0.
 pg_status dc_init(pg_grid* g) {
     if (g->dc_trivial) return set_state_device(g, nullptr, g->dc_vdd, nullptr, 0);
-    if (!g->dcgrid) {
-        pg_netlist d = g->nc.dc_view();
-        pg_options o = g->opt;
-        o.precision = PG_PREC_FP64;
-        o.omega = 0.0;
-        o.step_tol = 0.0;
-        std::unique_ptr<pg_grid> sub;
-        pg_status s = create_impl(&d, &o, sub);
-        if (s == PG_ERR_FLOATING_NODE)
-            g_last_error = "DC operating point needs every sub-circuit tied to a source or ground by a resistor: " +
-                           g_last_error;
-        if (s) return s;
-        sub->stream = g->stream;
-        g->dcgrid = std::move(sub);
-    }
+    pg_status s = ensure_dc_grid(g);
+    if (s) return s;
     pg_grid* d = g->dcgrid.get();
     d->stream = g->stream;
     double vmean = 0.0;
     for (double x : g->nc.vdd) vmean += x;
     vmean = g->nc.vdd.empty() ? 0.0 : vmean / g->nc.vdd.size();
-    pg_status s;
     // The DC network has no C and no L, so its coefficients do not depend on h (any h > 0
-    // assembles them); its solve target follows the main grid's per-step target.
-    d->opt.step_tol = g->step_tol > 0.0 ? g->step_tol : 0.5 * g->opt.tol;
+    // assembles them).  Its solve error enters the transient like one more step error, so it
+    // gets the main grid's per-step target.
     if ((s = prepare_h(d, 1.0))) return s;
+    const double target = (g->step_tol > 0.0 ? g->step_tol : 0.5 * g->opt.tol) / d->kappa - 1e-13;
     if ((s = set_state_device(d, nullptr, vmean, nullptr, -1))) return s;
     RunParams rp = base_params(d);
     rp.mode = kModeTransient;
     rp.nsteps = 1;
     rp.step0 = -1;   // one step landing on t = 0
     rp.have_prev = 0;
+    rp.target = target;
     rp.solve_out = d->d_x;
     double stats[kStatCount];
     if ((s = run(d, rp, stats, nullptr))) return s;
@@ -475,7 +534,7 @@ pg_status fill_stats(pg_grid* g, const double* st, float ms, pg_run_stats* out) 
     out->total_outer = (int64_t)st[kStatOuter];
     out->max_outer_step = (int32_t)st[kStatMaxOuter];
     out->max_step_bound = g->kappa * (st[kStatMaxBound] + 1e-13);
-    out->err_bound = (g->P.n_l == 0 && g->q < 1.0) ? out->max_step_bound / (1.0 - g->q) : NAN;
+    out->err_bound = std::isfinite(g->kacc) ? out->max_step_bound * g->kacc : NAN;
     out->failed_step = (int64_t)st[kStatFailedStep];
     out->omega = g->omega;
     out->rho_jacobi = g->rho;
@@ -483,6 +542,7 @@ pg_status fill_stats(pg_grid* g, const double* st, float ms, pg_run_stats* out) 
     out->q = g->q;
     out->step_tol = g->step_tol;
     out->device_ms = ms;
+    out->kacc = g->kacc;
     return PG_OK;
 }
 
@@ -629,6 +689,36 @@ pg_status pg_update_sources(pg_grid* g, const double* i_t, const double* i_v, in
     return PG_OK;
 }
 
+pg_status pg_update_values(pg_grid* g, const double* r_g, const double* c_val, const double* l_val, int32_t on_host) {
+    if (!g) return PG_ERR_INVALID_ARG;
+    NetCopy& nc = g->nc;
+    auto pull = [&](const double* src, std::vector<double>& dst) -> pg_status {
+        if (!src || dst.empty()) return PG_OK;
+        if (on_host) std::memcpy(dst.data(), src, dst.size() * sizeof(double));
+        else CK(cudaMemcpy(dst.data(), src, dst.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        return PG_OK;
+    };
+    NetCopy trial = nc;
+    pg_status s;
+    if ((s = pull(r_g, trial.r_g)) || (s = pull(c_val, trial.c_val)) || (s = pull(l_val, trial.l_val))) return s;
+    pg_netlist view{};
+    view.n_nodes = trial.n; view.n_sources = trial.p; view.vdd = trial.vdd.data();
+    view.n_r = (int64_t)trial.r_g.size(); view.r_a = trial.r_a.data(); view.r_b = trial.r_b.data(); view.r_g = trial.r_g.data();
+    view.n_c = (int64_t)trial.c_val.size(); view.c_a = trial.c_a.data(); view.c_b = trial.c_b.data(); view.c_val = trial.c_val.data();
+    view.n_l = (int64_t)trial.l_val.size(); view.l_a = trial.l_a.data(); view.l_b = trial.l_b.data(); view.l_val = trial.l_val.data();
+    std::string why;
+    Packed backup = g->P;
+    if ((s = refill_values(&view, &g->P, &why))) {
+        g->P = std::move(backup);
+        g_last_error = why;
+        return s;
+    }
+    nc = std::move(trial);
+    g->h = -1.0;            // re-assemble the per-h coefficients on the next call
+    g->dcgrid.reset();      // the resistive network changed too
+    return PG_OK;
+}
+
 pg_status pg_transient(pg_grid* g, double h, int32_t nsteps, const pg_output* out, pg_run_stats* stats) {
     if (!g || nsteps < 0) return PG_ERR_INVALID_ARG;
     pg_status s = prepare_h(g, h);
@@ -714,6 +804,225 @@ pg_status pg_step(pg_grid* g, double h, double* v_out, pg_run_stats* stats) {
     pg_output o{};
     o.v_all = v_out;
     return pg_transient(g, h, 1, v_out ? &o : nullptr, stats);
+}
+
+pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* obj, int32_t ckpt_every,
+                     double* J, double* dJ_dG, double* dJ_dC, int32_t on_host, pg_run_stats* stats) {
+    if (!g || nsteps < 1 || !obj || ckpt_every < 0) return PG_ERR_INVALID_ARG;
+    if (obj->kind != PG_OBJ_SOFTPLUS_DROP) { g_last_error = "unknown objective"; return PG_ERR_INVALID_ARG; }
+    if (g->P.n_l > 0) { g_last_error = "the adjoint covers RC grids (no inductors)"; return PG_ERR_UNSUPPORTED; }
+    const int ck = ckpt_every > 0 ? ckpt_every : 50;
+    pg_status s = prepare_h(g, h);
+    if (s) return s;
+    const Packed& P = g->P;
+    const int np = P.n_pad;
+    const int nseg = (nsteps + ck - 1) / ck;
+    DeviceScratch sc;   // released on every exit path
+    double* ck_v = sc.get<double>((size_t)nseg * np);
+    double* ck_vp = sc.get<double>((size_t)nseg * np);
+    double* part = sc.get<double>((size_t)nsteps * g->blocks);
+    double* vseg = sc.get<double>((size_t)(ck + 1) * np);
+    double* lam = sc.get<double>(np);
+    double* lam_next = sc.get<double>(np);
+    double* rhs = sc.get<double>(np);
+    double* acc_slot = sc.get<double>(P.n_ell);
+    double* acc_lv = sc.get<double>(np);
+    double* acc_l = sc.get<double>(np);
+    double* acc_dv = sc.get<double>(np);
+    unsigned long long* scale = sc.get<unsigned long long>(1);
+    if (!ck_v || !ck_vp || !part || !vseg || !lam || !lam_next || !rhs || !acc_slot || !acc_lv || !acc_l ||
+        !acc_dv || !scale)
+        return PG_ERR_OOM;
+    std::vector<int> ck_have(nseg, 0);
+    auto advance = [&](int64_t done) {
+        for (int64_t k = 0; k < done; ++k) { const int vF = 3 - g->vL - g->vP; g->vP = g->vL; g->vL = vF; }
+        g->step += done;
+        if (done > 0) g->have_prev = true;
+    };
+    double st[kStatCount];
+    float ms_total = 0.f, ms = 0.f;
+    int64_t sweeps = 0, outer = 0;
+    double worst = 0.0;
+    auto account = [&]() {
+        ms_total += ms; sweeps += (int64_t)st[kStatSweeps]; outer += (int64_t)st[kStatOuter];
+        worst = std::max(worst, st[kStatMaxBound]);
+    };
+
+    // forward pass from the DC point, keeping (v_s, v_{s-1}) at every segment start
+    g->has_state = false;
+    if ((s = dc_init(g))) return s;
+    for (int k = 0; k < nseg; ++k) {
+        const int s0 = k * ck, len = std::min(ck, nsteps - s0);
+        CK(cudaMemcpyAsync(ck_v + (size_t)k * np, g->ds.v[g->vL], np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+        CK(cudaMemcpyAsync(ck_vp + (size_t)k * np, g->ds.v[g->vP], np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+        ck_have[k] = g->have_prev;
+        RunParams rp = base_params(g);
+        rp.mode = kModeTransient;
+        rp.nsteps = len;
+        rp.step0 = g->step;
+        rp.have_prev = g->have_prev;
+        rp.obj_partials = part + (size_t)s0 * g->blocks;
+        rp.obj_vref = obj->vref;
+        rp.obj_margin = obj->margin;
+        s = run(g, rp, st, &ms);
+        account();
+        advance((int64_t)st[kStatSteps]);
+        if (s) { g->has_state = false; return s; }
+    }
+    {
+        // J: fixed-order compensated sum of the per-step, per-block partial sums
+        std::vector<double> hp((size_t)nsteps * g->blocks);
+        CK(cudaMemcpy(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        double sum = 0.0, comp = 0.0;
+        for (double x : hp) {
+            const double t = sum + x;
+            comp += std::fabs(sum) >= std::fabs(x) ? (sum - t) + x : (x - t) + sum;
+            sum = t;
+        }
+        if (J) *J = sum + comp;
+    }
+
+    // backward pass, segment by segment, recomputing each segment's states
+    CK(cudaMemsetAsync(lam_next, 0, np * sizeof(double), g->stream));
+    CK(cudaMemsetAsync(acc_slot, 0, std::max<int64_t>(P.n_ell, 1) * sizeof(double), g->stream));
+    CK(cudaMemsetAsync(acc_lv, 0, np * sizeof(double), g->stream));
+    CK(cudaMemsetAsync(acc_l, 0, np * sizeof(double), g->stream));
+    CK(cudaMemsetAsync(acc_dv, 0, np * sizeof(double), g->stream));
+    const int kb = std::max(1, std::min(g->n_sm * 4, (P.n_slices + 7) / 8));
+    for (int k = nseg - 1; k >= 0; --k) {
+        const int s0 = k * ck, len = std::min(ck, nsteps - s0);
+        g->vL = 0; g->vP = 1;
+        CK(cudaMemcpyAsync(g->ds.v[0], ck_v + (size_t)k * np, np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+        CK(cudaMemcpyAsync(g->ds.v[1], ck_vp + (size_t)k * np, np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+        CK(cudaMemcpyAsync(vseg, ck_v + (size_t)k * np, np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+        g->have_prev = ck_have[k] != 0;
+        g->step = s0;
+        RunParams rp = base_params(g);
+        rp.mode = kModeTransient;
+        rp.nsteps = len;
+        rp.step0 = s0;
+        rp.have_prev = g->have_prev;
+        rp.v_perm_all = vseg + np;            // rows 1..len: v_{s0+1} .. v_{s0+len}
+        if ((s = run(g, rp, st, &ms))) { g->has_state = false; return s; }
+        account();
+        for (int t = len; t >= 1; --t) {
+            const double* v_s = vseg + (size_t)t * np;
+            const double* v_p = vseg + (size_t)(t - 1) * np;
+            CK(cudaMemsetAsync(scale, 0, sizeof(unsigned long long), g->stream));
+            CK(launch_adjoint_rhs(g->dg, v_s, lam_next, rhs, obj->vref, obj->margin, scale, kb, g->stream));
+            RunParams sp = base_params(g);
+            sp.mode = kModeSolve;
+            sp.nsteps = 1;
+            sp.step0 = 0;
+            sp.have_prev = 0;
+            sp.warm_extrap = 0;
+            sp.x0 = lam_next;
+            sp.target = 1e-9;                 // relative: max|r|/D <= 1e-9 max|rhs|/D
+            sp.target_scale = scale;
+            sp.max_sweeps = std::max(g->opt.max_sweeps, kSetupSweeps);
+            g->ds.rhs = rhs;
+            s = run(g, sp, st, &ms);
+            g->ds.rhs = nullptr;
+            if (s) { g->has_state = false; return s; }
+            account();
+            const int vF = 3 - g->vL - g->vP;
+            CK(cudaMemcpyAsync(lam, g->ds.v[vF], np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+            CK(launch_adjoint_grad(g->dg, lam, v_s, v_p, acc_slot, acc_lv, acc_l, acc_dv, kb, g->stream));
+            std::swap(lam, lam_next);
+        }
+    }
+    g->has_state = false;
+
+    // map the slot and node sums to element gradients (host)
+    std::vector<double> h_slot(std::max<int64_t>(P.n_ell, 1)), h_lv(np), h_l(np), h_dv(np);
+    CK(cudaMemcpy(h_slot.data(), acc_slot, h_slot.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(h_lv.data(), acc_lv, np * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(h_l.data(), acc_l, np * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(h_dv.data(), acc_dv, np * sizeof(double), cudaMemcpyDeviceToHost));
+    const NetCopy& nc = g->nc;
+    auto slot_of = [&](int32_t lo, int32_t hi) -> int64_t {
+        const int sl = lo / kSlice, q = lo % kSlice;
+        for (int k = 0; k < P.slice_w[sl]; ++k) {
+            const int64_t e = P.slice_off[sl] + (int64_t)k * kSlice + q;
+            if (P.ell_col[e] == hi && P.ell_adj[e] >= 0) return e;
+        }
+        return -1;
+    };
+    std::vector<double> gG(nc.r_g.size(), 0.0), gC(nc.c_val.size(), 0.0);
+    for (size_t e = 0; e < nc.r_g.size(); ++e) {
+        const int32_t a = nc.r_a[e], b = nc.r_b[e];
+        if (a >= 0 && b >= 0) {
+            const int32_t i = P.perm[a], j = P.perm[b];
+            const int64_t sl = slot_of(std::min(i, j), std::max(i, j));
+            gG[e] = sl >= 0 ? -h_slot[sl] : 0.0;
+        } else if (a >= 0 || b >= 0) {
+            const int32_t i = P.perm[a >= 0 ? a : b], o = a >= 0 ? b : a;
+            const double V = o == PG_GROUND ? 0.0 : nc.vdd[-2 - o];
+            gG[e] = -(h_lv[i] - V * h_l[i]);
+        }
+    }
+    for (size_t e = 0; e < nc.c_val.size(); ++e) {
+        const int32_t a = nc.c_a[e], b = nc.c_b[e];
+        if (a >= 0 || b >= 0) gC[e] = -h_dv[P.perm[a >= 0 ? a : b]] / h;
+    }
+    // the DC point depends on the resistors unless it is the trivial v = Vdd
+    if (!g->dc_trivial) {
+        if ((s = ensure_dc_grid(g))) return s;
+        pg_grid* d = g->dcgrid.get();
+        d->stream = g->stream;
+        if ((s = prepare_h(d, 1.0))) return s;
+        // mu solves G mu = (C/h) lambda_1, in the DC network's own numbering
+        std::vector<double> lam1(np), rd(d->P.n_pad, 0.0), v0p(np);
+        CK(cudaMemcpy(lam1.data(), lam_next, np * sizeof(double), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(v0p.data(), ck_v, np * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < d->P.n_pad; ++i) {
+            const int o = d->P.orig[i];
+            if (o >= 0) rd[i] = P.cap[o] / h * lam1[P.perm[o]];
+        }
+        double rmax = 0.0;
+        for (int i = 0; i < d->P.n_pad; ++i)
+            if (d->P.orig[i] >= 0) rmax = std::max(rmax, std::fabs(rd[i]) / 1.0);
+        double* rdd = sc.get<double>(rd.size());
+        if (!rdd) return PG_ERR_OOM;
+        CK(cudaMemcpy(rdd, rd.data(), rd.size() * sizeof(double), cudaMemcpyHostToDevice));
+        double R = 0.0;
+        if (rmax > 0.0) {
+            // relative residual 1e-9 of the scaled right-hand side
+            double dmin = INFINITY;
+            std::vector<double> Dh(d->P.n_pad);
+            CK(cudaMemcpy(Dh.data(), d->dg.D64, Dh.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            double smax = 0.0;
+            for (int i = 0; i < d->P.n_pad; ++i)
+                if (d->P.orig[i] >= 0) { smax = std::max(smax, std::fabs(rd[i]) / Dh[i]); dmin = std::min(dmin, Dh[i]); }
+            if ((s = solve_internal(d, rdd, 1e-9 * smax, &R))) return s;
+            std::vector<double> mu(P.n);
+            CK(cudaMemcpy(mu.data(), d->d_x, P.n * sizeof(double), cudaMemcpyDeviceToHost));
+            std::vector<double> v0(P.n);
+            for (int i = 0; i < np; ++i)
+                if (P.orig[i] >= 0) v0[P.orig[i]] = v0p[i];
+            auto tvv = [&](int32_t t) { return t >= 0 ? v0[t] : (t == PG_GROUND ? 0.0 : nc.vdd[-2 - t]); };
+            auto tmu = [&](int32_t t) { return t >= 0 ? mu[t] : 0.0; };
+            for (size_t e = 0; e < nc.r_g.size(); ++e)
+                gG[e] -= (tmu(nc.r_a[e]) - tmu(nc.r_b[e])) * (tvv(nc.r_a[e]) - tvv(nc.r_b[e]));
+        }
+    }
+    auto emit = [&](double* dst, const std::vector<double>& src) -> pg_status {
+        if (!dst || src.empty()) return PG_OK;
+        if (on_host) std::memcpy(dst, src.data(), src.size() * sizeof(double));
+        else CK(cudaMemcpy(dst, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice));
+        return PG_OK;
+    };
+    if ((s = emit(dJ_dG, gG)) || (s = emit(dJ_dC, gC))) return s;
+    if (stats) {
+        double z[kStatCount] = {0};
+        z[kStatSteps] = nsteps;
+        z[kStatSweeps] = (double)sweeps;
+        z[kStatOuter] = (double)outer;
+        z[kStatMaxBound] = worst;
+        z[kStatFailedStep] = -1;
+        fill_stats(g, z, ms_total, stats);
+    }
+    return PG_OK;
 }
 
 pg_status pg_solve(pg_grid* g, double h, const double* b, double* x, double tol, pg_run_stats* stats) {

@@ -350,4 +350,50 @@ pg_status build_packed(const pg_netlist* nl, Packed* P, std::string* why) {
     return PG_OK;
 }
 
+pg_status refill_values(const pg_netlist* nl, Packed* P, std::string* why) {
+    auto fail = [&](const std::string& m) { if (why) *why = m; return PG_ERR_INVALID_ARG; };
+    const int32_t n = P->n;
+    std::fill(P->adj_g.begin(), P->adj_g.end(), 0.0);
+    std::fill(P->adj_il.begin(), P->adj_il.end(), 0.0);
+    P->g_gnd.assign(n, 0.0); P->il_gnd.assign(n, 0.0); P->cap.assign(n, 0.0);
+    P->inj_g.assign(n, 0.0); P->inj_il.assign(n, 0.0);
+    auto tv = [&](int32_t t) { return t == PG_GROUND ? 0.0 : nl->vdd[-2 - t]; };
+    auto entry = [&](int32_t i, int32_t j) -> int64_t {
+        const auto b = P->adj_nbr.begin() + P->adj_ptr[i], e = P->adj_nbr.begin() + P->adj_ptr[i + 1];
+        const auto it = std::lower_bound(b, e, j);
+        return (it != e && *it == j) ? (int64_t)(it - P->adj_nbr.begin()) : -1;
+    };
+    for (int64_t e = 0; e < nl->n_r; ++e) {
+        const int32_t a = nl->r_a[e], b = nl->r_b[e];
+        const double g = nl->r_g[e];
+        if (!finite_pos(g)) return fail("resistor conductance must be > 0");
+        if (a >= 0 && b >= 0) {
+            P->adj_g[entry(a, b)] += g;
+            P->adj_g[entry(b, a)] += g;
+        } else if (a >= 0 || b >= 0) {
+            const int32_t i = a >= 0 ? a : b, o = a >= 0 ? b : a;
+            P->g_gnd[i] += g; P->inj_g[i] += g * tv(o);
+        }
+    }
+    for (int64_t e = 0; e < nl->n_l; ++e) {
+        const int32_t a = nl->l_a[e], b = nl->l_b[e];
+        if (!finite_pos(nl->l_val[e])) return fail("inductance must be > 0");
+        const double il = 1.0 / nl->l_val[e];
+        P->ind_invL[e] = il;
+        if (a >= 0 && b >= 0) {
+            P->adj_il[entry(a, b)] += il;
+            P->adj_il[entry(b, a)] += il;
+        } else if (a >= 0 || b >= 0) {
+            const int32_t i = a >= 0 ? a : b, o = a >= 0 ? b : a;
+            P->il_gnd[i] += il; P->inj_il[i] += il * tv(o);
+        }
+    }
+    for (int64_t e = 0; e < nl->n_c; ++e) {
+        if (!finite_pos(nl->c_val[e])) return fail("capacitance must be > 0");
+        const int32_t a = nl->c_a[e], b = nl->c_b[e];
+        if (a >= 0 || b >= 0) P->cap[a >= 0 ? a : b] += nl->c_val[e];
+    }
+    return PG_OK;
+}
+
 }  // namespace pg

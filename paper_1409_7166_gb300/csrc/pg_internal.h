@@ -63,6 +63,9 @@ struct Packed {
 };
 
 pg_status build_packed(const pg_netlist* nl, Packed* out, std::string* why);
+// Refill the value-dependent parts of a packed grid (merged weights, grounded
+// parts, capacitances, 1/L) from a netlist with the same topology.
+pg_status refill_values(const pg_netlist* nl, Packed* P, std::string* why);
 
 // ---------------------------------------------------------------- device side
 
@@ -151,6 +154,13 @@ struct RunParams {
     const int32_t* probes_perm;
     double* probe_v;
     double* solve_out;        // kModeSolve: x in caller numbering
+    // kModeSolve extras
+    const double* x0;                              // initial guess (permuted) or null (x = 0)
+    const unsigned long long* target_scale;        // if set, target *= this double (device)
+    // transient extras
+    double* v_perm_all;       // [nsteps x n_pad] voltages in permuted order (adjoint recompute)
+    double* obj_partials;     // [nsteps x nblocks] per-block sums of softplus(vref - v - margin)^2
+    double obj_vref, obj_margin;
 };
 
 }  // namespace pg
@@ -166,4 +176,9 @@ cudaError_t launch_power_step(const DevGrid& g, const double* x, double* y, cons
                               double* acc, unsigned long long* ymax, int blocks, cudaStream_t stream);
 cudaError_t launch_permute_in(const int32_t* orig, const double* src, double fill, double* dst, int n_pad,
                               int n_sm, cudaStream_t stream);
+cudaError_t launch_adjoint_rhs(const DevGrid& g, const double* v, const double* lam_next, double* rhs, double vref,
+                               double margin, unsigned long long* scale_slot, int blocks, cudaStream_t stream);
+cudaError_t launch_adjoint_grad(const DevGrid& g, const double* lam, const double* v, const double* v_prev,
+                                double* acc_slot, double* acc_lv, double* acc_l, double* acc_dv, int blocks,
+                                cudaStream_t stream);
 }  // namespace pg

@@ -23,6 +23,17 @@
 
 #include "pg_internal.h"
 
+// Minimum resident blocks per SM requested from ptxas for the persistent
+// kernel (register budget = 65536 / (256 * PG_MIN_BLOCKS)).
+#ifndef PG_MIN_BLOCKS
+#define PG_MIN_BLOCKS 2
+#endif
+// Slots of the SOR sweep issued together (loads in flight per lane).
+#ifndef PG_SWEEP_UNROLL
+#define PG_SWEEP_UNROLL 4
+#endif
+constexpr int kSweepUnroll = PG_SWEEP_UNROLL;
+
 namespace pg {
 
 namespace {
@@ -67,23 +78,12 @@ __device__ __forceinline__ void st4(double* p, const double (&x)[4]) {
     reinterpret_cast<double2*>(p)[1] = make_double2(x[2], x[3]);
 }
 
+// softplus(u) = log(1 + e^u), evaluated without overflow: max(u, 0) + log1p(e^-|u|)
+__device__ __forceinline__ double softplus_d(double u) { return fmax(u, 0.0) + log1p(exp(-fabs(u))); }
+__device__ __forceinline__ double sigmoid_d(double u) { return 0.5 * (1.0 + tanh(0.5 * u)); }
+
 // max that lets a NaN win, so a diverged iterate is never mistaken for convergence
 __device__ __forceinline__ double nanmax(double a, double b) { return (a > b || a != a) ? a : b; }
-
-// Block-wide max of non-negative values, merged into *slot with one atomic per block.
-__device__ __forceinline__ void block_max_into(double v, unsigned long long* slot) {
-    __shared__ double sm[32];
-    for (int o = 16; o; o >>= 1) v = nanmax(v, __shfl_xor_sync(kFull, v, o));
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) sm[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        v = (l < (int)(blockDim.x >> 5)) ? sm[l] : 0.0;
-        for (int o = 16; o; o >>= 1) v = nanmax(v, __shfl_xor_sync(kFull, v, o));
-        if (l == 0 && v != 0.0) atomicMax(slot, (unsigned long long)__double_as_longlong(v));
-    }
-    __syncthreads();
-}
 
 // Order-preserving map of a double to an unsigned key (for min reductions).
 __device__ __forceinline__ unsigned long long order_key(double x) {
@@ -95,38 +95,57 @@ __device__ __forceinline__ double key_value(unsigned long long k) {
     return __longlong_as_double((long long)b);
 }
 
-// Device-wide barrier with a time limit.  .ok is false (for the whole block)
-// when this or any other block recorded an error.  .val receives the value of
-// `read_slot` (a max-reduction slot filled before the barrier), read once by
-// thread 0 after the wait and broadcast, so every block sees the same number.
+// Device-wide barrier with a time limit, fused with the block's max-reduction.
+//
+// Every block merges `v` (its threads' partial maxima) into the reduction slot
+// `slot` with one atomic, then arrives.  The generation word is cleared by the
+// host before each launch, so barrier number k (counted from 0 in every block)
+// completes when the generation reaches k + 1: no load is needed before
+// arriving.  Arrival is an acq_rel RMW and the wait an acquire load, both at
+// device scope, which publishes the block's writes (ordered before the
+// arrival by __syncthreads) to every block that passes the barrier.  .ok is
+// false for the whole block when an error was recorded (this block's wait
+// timed out, or another block's did); .val is the reduced value, read once
+// by thread 0 after the wait and broadcast.
 struct BarrierResult {
     bool ok;
     double val;
 };
 
-__device__ __forceinline__ BarrierResult grid_barrier(const DevCtl& c, unsigned nblocks, long long timeout_ns,
-                                                      bool skip, const unsigned long long* read_slot) {
+__device__ __forceinline__ BarrierResult grid_barrier(const DevCtl& c, unsigned nblocks, unsigned target_gen,
+                                                      long long timeout_ns, bool skip, double v,
+                                                      unsigned long long* slot) {
+    __shared__ double s_part[32];
     __shared__ int s_ok;
     __shared__ double s_val;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (slot) {
+        for (int o = 16; o; o >>= 1) v = nanmax(v, __shfl_xor_sync(kFull, v, o));
+        if (l == 0) s_part[w] = v;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(*c.bar_gen);
         cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(*c.bar_count);
         cuda::atomic_ref<int, cuda::thread_scope_device> err(*c.err);
+        if (slot) {
+            double m = s_part[0];
+            for (int q = 1; q < (int)(blockDim.x >> 5); ++q) m = nanmax(m, s_part[q]);
+            if (m != 0.0) atomicMax(slot, (unsigned long long)__double_as_longlong(m));
+        }
         int ok = 1;
-        {
-            const unsigned g0 = gen.load(cuda::memory_order_relaxed);
-            __threadfence();
-            // test hook: this block waits without being counted, so the barrier can never open
-            const unsigned arrived = skip ? 0u : cnt.fetch_add(1u, cuda::memory_order_acq_rel);
-            if (!skip && arrived == nblocks - 1) {
-                cnt.store(0u, cuda::memory_order_relaxed);
-                gen.fetch_add(1u, cuda::memory_order_release);
-            } else {
-                const long long t0 = global_ns();
-                unsigned ns = 32;
-                while (gen.load(cuda::memory_order_acquire) == g0) {
-                    if (err.load(cuda::memory_order_relaxed) != 0) { ok = 0; break; }
+        // test hook: a skipping block waits without being counted, so the barrier never opens
+        const unsigned arrived = skip ? 0u : cnt.fetch_add(1u, cuda::memory_order_acq_rel);
+        if (!skip && arrived == nblocks - 1) {
+            cnt.store(0u, cuda::memory_order_relaxed);
+            gen.store(target_gen, cuda::memory_order_release);
+        } else {
+            long long t0 = 0;
+            unsigned ns = 0;
+            for (int it = 0; gen.load(cuda::memory_order_acquire) < target_gen; ++it) {
+                if (err.load(cuda::memory_order_relaxed) != 0) { ok = 0; break; }
+                if (it == 64) t0 = global_ns();
+                if (it > 64) {
                     if (global_ns() - t0 > timeout_ns) {
                         int z = 0;
                         err.compare_exchange_strong(z, (int)PG_ERR_TIMEOUT);
@@ -134,21 +153,18 @@ __device__ __forceinline__ BarrierResult grid_barrier(const DevCtl& c, unsigned 
                         break;
                     }
                     __nanosleep(ns);
-                    if (ns < 256) ns <<= 1;
+                    ns = ns < 128 ? ns + 16 : 128;
                 }
             }
-            __threadfence();
-            if (ok && err.load(cuda::memory_order_acquire) != 0) ok = 0;
         }
         s_ok = ok;
-        if (read_slot) {
-            cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> r(
-                *const_cast<unsigned long long*>(read_slot));
-            s_val = __longlong_as_double((long long)r.load(cuda::memory_order_acquire));
+        if (slot) {
+            cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> r(*slot);
+            s_val = __longlong_as_double((long long)r.load(cuda::memory_order_relaxed));
         }
     }
     __syncthreads();
-    return BarrierResult{s_ok != 0, s_val};
+    return BarrierResult{s_ok != 0, slot ? s_val : 0.0};
 }
 
 // Value of current source e at time t (piecewise linear, held outside the breakpoints).
@@ -181,34 +197,102 @@ __device__ __forceinline__ double term_volt(const DevGrid& g, const double* v, i
     return t >= 0 ? v[t] : (t == PG_GROUND ? 0.0 : g.vdd[-2 - t]);
 }
 
-// Columns of the 4 nodes of this lane in slot k of slice s.
-__device__ __forceinline__ void slot_cols(const DevGrid& g, bool dia, int dbase, int64_t e, int i0, int k,
-                                          int (&c)[4]) {
-    if (dia) {
-        const int o = __ldg(g.dia_off + dbase + k);
-        c[0] = i0 + o; c[1] = i0 + 1 + o; c[2] = i0 + 2 + o; c[3] = i0 + 3 + o;
-    } else {
-        ldg4(g.ell_col + e, c);
+// ---- slice descriptors
+//
+// A warp owns a contiguous run of slices of every colour (the same run in
+// every pass).  Their descriptors and diagonal column offsets are copied once
+// per launch into the warp's part of shared memory, so a sweep reads no
+// metadata from global memory: per slice only the weights, the node vectors
+// and the neighbour values.
+constexpr int kWarpsPerBlock = 8;
+constexpr int kCacheSlices = 32;    // descriptors cached per warp
+constexpr int kCachePool = 384;     // diagonal offsets cached per warp
+
+struct SliceDesc {
+    long long off;   // element offset of the slice's slot 0
+    int K;           // slots per node
+    int dpos;        // >= 0: offsets at pool[dpos]; -1: explicit columns; <= -2: offsets at dia_off[-2 - dpos]
+};
+
+struct WarpCache {
+    SliceDesc desc[kCacheSlices];
+    int pool[kCachePool];
+    int base[kMaxColours + 1];   // index of the warp's first slice of colour c in its list
+    int lo[kMaxColours];         // first slice of colour c owned by the warp
+    int cnt[kMaxColours];        // slices of colour c owned by the warp
+};
+
+__device__ __forceinline__ SliceDesc global_desc(const DevGrid& g, int s) {
+    SliceDesc d;
+    d.off = __ldg(g.slice_off + s);
+    d.K = __ldg(g.slice_w + s);
+    const int d0 = __ldg(g.slice_doff + s);
+    d.dpos = __ldg(g.slice_doff + s + 1) > d0 ? -2 - d0 : -1;
+    return d;
+}
+
+// Fill the calling warp's cache (once per launch).  Every lane must call it.
+__device__ void fill_warp_cache(const DevGrid& g, WarpCache& wc, int gwarp, int nwarps) {
+    const int lane = threadIdx.x & 31;
+    int j = 0;
+    for (int c = 0; c < g.ncol; ++c) {
+        const int c0 = __ldg(g.colour_slice + c), c1 = __ldg(g.colour_slice + c + 1);
+        const int S = c1 - c0;
+        const int R = (S + nwarps - 1) / nwarps;
+        const int lo = min(c0 + gwarp * R, c1), hi = min(lo + R, c1);
+        if (lane == 0) { wc.base[c] = j; wc.lo[c] = lo; wc.cnt[c] = hi - lo; }
+        for (int t = lane; t < hi - lo; t += 32)
+            if (j + t < kCacheSlices) wc.desc[j + t] = global_desc(g, lo + t);
+        j += hi - lo;
     }
+    if (lane == 0) wc.base[g.ncol] = j;
+    __syncwarp();
+    if (lane == 0) {
+        int pos = 0;
+        for (int k = 0; k < min(j, kCacheSlices); ++k) {
+            SliceDesc& d = wc.desc[k];
+            if (d.dpos <= -2) {
+                if (pos + d.K <= kCachePool) {
+                    const int src = -2 - d.dpos;
+                    for (int q = 0; q < d.K; ++q) wc.pool[pos + q] = __ldg(g.dia_off + src + q);
+                    d.dpos = pos;
+                    pos += d.K;
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Descriptor of the t-th slice (slice id s) of colour c in this warp's run.
+__device__ __forceinline__ SliceDesc warp_desc(const DevGrid& g, const WarpCache& wc, int c, int t, int s) {
+    const int j = wc.base[c] + t;
+    return j < kCacheSlices ? wc.desc[j] : global_desc(g, s);
 }
 
 // sigma_j = sum_k w[k][j] * x(col[k][j]) for the lane's 4 nodes, accumulated in Acc.
-template <typename Acc, typename Wt, typename Load>
-__device__ __forceinline__ void sell_row(const DevGrid& g, const Wt* w, int s, int lane, Load xload,
-                                         Acc (&sig)[4]) {
-    const int64_t base = __ldg(g.slice_off + s) + lane * kVec;
-    const int K = __ldg(g.slice_w + s);
-    const int d0 = __ldg(g.slice_doff + s);
-    const bool dia = __ldg(g.slice_doff + s + 1) > d0;
+// UNROLL trades registers for loads in flight: the hot FP32 sweep unrolls, the
+// once-per-pass FP64 rows do not (they would set the register budget of the whole
+// persistent kernel).
+template <int UNROLL, typename Acc, typename Wt, typename Load>
+__device__ __forceinline__ void sell_row(const DevGrid& g, const WarpCache* wc, const SliceDesc& d, const Wt* w,
+                                         int s, int lane, Load xload, Acc (&sig)[4]) {
+    const long long base = d.off + lane * kVec;
     const int i0 = s * kSlice + lane * kVec;
+    const int* offs = d.dpos >= 0 ? wc->pool + d.dpos : (d.dpos <= -2 ? g.dia_off + (-2 - d.dpos) : nullptr);
     sig[0] = sig[1] = sig[2] = sig[3] = Acc(0);
-#pragma unroll 2
-    for (int k = 0; k < K; ++k) {
-        const int64_t e = base + (int64_t)k * kSlice;
+#pragma unroll UNROLL
+    for (int k = 0; k < d.K; ++k) {
+        const long long e = base + (long long)k * kSlice;
         Wt wv[4];
         ldg4(w + e, wv);
         int c[4];
-        slot_cols(g, dia, d0, e, i0, k, c);
+        if (offs) {
+            const int o = offs[k];
+            c[0] = i0 + o; c[1] = i0 + 1 + o; c[2] = i0 + 2 + o; c[3] = i0 + 3 + o;
+        } else {
+            ldg4(g.ell_col + e, c);
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) sig[j] = fma((Acc)wv[j], xload(c[j]), sig[j]);
     }
@@ -218,8 +302,9 @@ __device__ __forceinline__ void sell_row(const DevGrid& g, const Wt* w, int s, i
 
 // Start of a step: RHS assembly (Eq. 2 / Eq. 10), warm start, FP64 residual.
 template <bool MIXED>
-__device__ __forceinline__ double phase_rhs(const DevGrid& g, const DevState& st, const RunParams& rp, int s, int lane,
-                            int vL, int vP, int vF, bool extrap, double t, int dsel) {
+__device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* wc, const SliceDesc& sd,
+                                            const DevState& st, const RunParams& rp, int s, int lane, int vL, int vP,
+                                            int vF, bool extrap, double t, int dsel) {
     const int i0 = s * kSlice + lane * kVec;
     const double* vl = vbuf(st, vL);
     const double* vp = vbuf(st, vP);
@@ -228,7 +313,8 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const DevState& st
     ldg4(g.invD64 + i0, iD);
     if (rp.mode == kModeSolve) {
         ldg4(st.rhs + i0, b);
-        vw[0] = vw[1] = vw[2] = vw[3] = 0.0;
+        if (rp.x0) ldg4(rp.x0 + i0, vw);
+        else vw[0] = vw[1] = vw[2] = vw[3] = 0.0;
     } else {
         double a[4], ch[4], cj[4];
         ld4(vl + i0, a);
@@ -262,11 +348,12 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const DevState& st
     }
     double sig[4];
     if (rp.mode == kModeSolve) {
-        sig[0] = sig[1] = sig[2] = sig[3] = 0.0;
+        if (rp.x0) sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return __ldg(rp.x0 + c); }, sig);
+        else sig[0] = sig[1] = sig[2] = sig[3] = 0.0;
     } else if (extrap) {
-        sell_row<double>(g, g.w64, s, lane, [&](int c) { return 2.0 * vl[c] - vp[c]; }, sig);
+        sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return 2.0 * vl[c] - vp[c]; }, sig);
     } else {
-        sell_row<double>(g, g.w64, s, lane, [&](int c) { return vl[c]; }, sig);
+        sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return vl[c]; }, sig);
     }
     double r[4], mon = 0.0;
 #pragma unroll
@@ -290,14 +377,14 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const DevState& st
 
 // One colour's SOR half-sweep on M delta = r (Eq. 16-17): returns max |unrelaxed update|.
 template <typename T>
-__device__ __forceinline__ double sweep_slice(const DevGrid& g, const T* w, const T* invD, const T* r, T* d, int s, int lane,
-                              T omega) {
+__device__ __forceinline__ double sweep_slice(const DevGrid& g, const WarpCache* wc, const SliceDesc& sd, const T* w,
+                                              const T* invD, const T* r, T* d, int s, int lane, T omega) {
     const int i0 = s * kSlice + lane * kVec;
     T dv[4], rv[4], iD[4], sig[4];
     ld4(d + i0, dv);
     ld4(r + i0, rv);
     ldg4(invD + i0, iD);
-    sell_row<T>(g, w, s, lane, [&](int c) { return d[c]; }, sig);
+    sell_row<kSweepUnroll, T>(g, wc, sd, w, s, lane, [&](int c) { return d[c]; }, sig);
     double mon = 0.0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -309,10 +396,171 @@ __device__ __forceinline__ double sweep_slice(const DevGrid& g, const T* w, cons
     return mon;
 }
 
+// ---- TMA-fed sweep (FP32 path)
+//
+// The streaming operands of a slice (its K weight slots, its own corrections,
+// residuals and 1/D: K + 3 contiguous 512-byte runs) are fetched by the
+// Tensor Memory Accelerator with cp.async.bulk into a per-warp shared-memory
+// stage, completion tracked by an mbarrier (transaction bytes).  Two stages
+// per warp: slice t+1 is in flight while slice t is computed, so the warp no
+// longer waits on its own streaming loads; only the neighbour gathers remain
+// ordinary (L1-cached) loads.  Slices with more than kTmaK slots or explicit
+// columns take the direct path.
+constexpr int kTmaK = 8;
+constexpr int kStageElems = (kTmaK + 3) * kSlice;
+
+__host__ __device__ constexpr int tma_stage_bytes(int elem_size) { return kStageElems * elem_size; }
+// per warp: two stages and two mbarriers (padded to keep stages 128-byte aligned)
+__host__ __device__ constexpr int tma_warp_bytes(int elem_size) { return 2 * tma_stage_bytes(elem_size) + 128; }
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// Generic-proxy writes (other blocks' and this warp's stores of the previous
+// phases, ordered by the device barrier) become visible to the bulk copies.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Bounded wait on a stage's mbarrier phase; false after the time limit.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long timeout_ns) {
+    long long t0 = 0;
+    for (int it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (it == 256) t0 = global_ns();
+        if (it > 256 && global_ns() - t0 > timeout_ns) return false;
+    }
+}
+
+struct TmaWarp {
+    unsigned char* stage[2];
+    unsigned long long* bar;   // [2]
+    unsigned parity;           // bit b: phase parity to wait for on stage b
+};
+
+template <typename T>
+__device__ __forceinline__ void tma_issue(const SliceDesc& sd, int s, const T* w, const T* d, const T* r,
+                                          const T* invD, T* buf, unsigned long long* bar) {
+    const unsigned wb = (unsigned)(sd.K * kSlice * sizeof(T));
+    const unsigned vb = (unsigned)(kSlice * sizeof(T));
+    mbar_expect_tx(bar, wb + 3 * vb);
+    bulk_g2s(buf, w + sd.off, wb, bar);
+    bulk_g2s(buf + kTmaK * kSlice, d + (long long)s * kSlice, vb, bar);
+    bulk_g2s(buf + (kTmaK + 1) * kSlice, r + (long long)s * kSlice, vb, bar);
+    bulk_g2s(buf + (kTmaK + 2) * kSlice, invD + (long long)s * kSlice, vb, bar);
+}
+
+// One slice of the SOR half-sweep with its streaming operands already in shared memory.
+template <typename T>
+__device__ __forceinline__ double sweep_slice_staged(const DevGrid& g, const WarpCache* wc, const SliceDesc& sd,
+                                                     const T* buf, T* d, int s, int lane, T omega) {
+    const int i0 = s * kSlice + lane * kVec;
+    T dv[4], rv[4], iD[4], sig[4];
+    ld4(buf + kTmaK * kSlice + lane * kVec, dv);
+    ld4(buf + (kTmaK + 1) * kSlice + lane * kVec, rv);
+    ld4(buf + (kTmaK + 2) * kSlice + lane * kVec, iD);
+    const int* offs = sd.dpos >= 0 ? wc->pool + sd.dpos : g.dia_off + (-2 - sd.dpos);
+    sig[0] = sig[1] = sig[2] = sig[3] = T(0);
+#pragma unroll kSweepUnroll
+    for (int k = 0; k < sd.K; ++k) {
+        T wv[4];
+        ld4(buf + k * kSlice + lane * kVec, wv);
+        const int o = offs[k];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sig[j] = fma(wv[j], d[i0 + j + o], sig[j]);
+    }
+    double mon = 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const T upd = (rv[j] + sig[j]) * iD[j] - dv[j];
+        dv[j] = fma(omega, upd, dv[j]);
+        mon = nanmax(mon, (double)fabs(upd));
+    }
+    st4(d + i0, dv);
+    return mon;
+}
+
+// The warp's run of colour-c slices, double-buffered through the TMA.  Returns
+// the max unrelaxed update, or NaN (after recording PG_ERR_TIMEOUT and letting
+// its copies land) when a copy does not complete within the time limit.
+template <typename T>
+__device__ double sweep_colour_tma(const DevGrid& g, const WarpCache* wc, TmaWarp& tw, int c, const T* w,
+                                   const T* invD, const T* r, T* d, int lane, T omega, int* err,
+                                   long long timeout_ns) {
+    const int cnt = wc->cnt[c], lo = wc->lo[c];
+    if (cnt == 0) return 0.0;
+    auto staged = [&](const SliceDesc& sd) { return sd.dpos != -1 && sd.K <= kTmaK; };
+    SliceDesc cur = warp_desc(g, *wc, c, 0, lo);
+    bool cur_t = staged(cur);
+    if (lane == 0) {
+        fence_proxy_async_global();
+        if (cur_t) tma_issue<T>(cur, lo, w, d, r, invD, (T*)tw.stage[0], tw.bar + 0);
+    }
+    double mon = 0.0;
+    unsigned pending = cur_t ? 1u : 0u;   // bit b: stage b has a copy in flight
+    for (int t = 0; t < cnt; ++t) {
+        const int sb = t & 1;
+        SliceDesc nxt{};
+        bool nxt_t = false;
+        if (t + 1 < cnt) {
+            nxt = warp_desc(g, *wc, c, t + 1, lo + t + 1);
+            nxt_t = staged(nxt);
+            if (nxt_t && lane == 0)
+                tma_issue<T>(nxt, lo + t + 1, w, d, r, invD, (T*)(sb ? tw.stage[0] : tw.stage[1]), tw.bar + (sb ^ 1));
+            if (nxt_t) pending |= 1u << (sb ^ 1);
+        }
+        if (cur_t) {
+            const bool ok = mbar_wait(tw.bar + sb, (tw.parity >> sb) & 1u, timeout_ns);
+            if (!ok) {
+                if (lane == 0) atomicCAS(err, 0, (int)PG_ERR_TIMEOUT);
+                // let every copy still in flight land before the stages are abandoned
+                for (int b = 0; b < 2; ++b)
+                    if ((pending >> b) & 1u) mbar_wait(tw.bar + b, (tw.parity >> b) & 1u, timeout_ns);
+                __syncwarp();
+                return __longlong_as_double(0x7ff8000000000000ll);
+            }
+            tw.parity ^= 1u << sb;
+            pending &= ~(1u << sb);
+            mon = nanmax(mon, sweep_slice_staged<T>(g, wc, cur, (const T*)(sb ? tw.stage[1] : tw.stage[0]), d, lo + t,
+                                                    lane, omega));
+        } else {
+            mon = nanmax(mon, sweep_slice<T>(g, wc, cur, w, invD, r, d, lo + t, lane, omega));
+        }
+        __syncwarp();   // stage sb is read by every lane before it is refilled
+        cur = nxt;
+        cur_t = nxt_t;
+    }
+    return mon;
+}
+
 // Outer defect-correction pass: v += delta, r -= M delta (FP64), refresh the FP32 residual.
 template <typename T>
-__device__ __forceinline__ double outer_slice(const DevGrid& g, const DevState& st, const T* d, T* dnext, float* r32, int s,
-                              int lane, double* v) {
+__device__ __forceinline__ double outer_slice(const DevGrid& g, const WarpCache* wc, const SliceDesc& sd,
+                                              const DevState& st, const T* d, T* dnext, float* r32, int s, int lane,
+                                              double* v) {
     const int i0 = s * kSlice + lane * kVec;
     T dv[4];
     ld4(d + i0, dv);
@@ -321,7 +569,7 @@ __device__ __forceinline__ double outer_slice(const DevGrid& g, const DevState& 
     ldg4(g.invD64 + i0, iD);
     ld4(st.r64 + i0, r);
     ld4(v + i0, vv);
-    sell_row<double>(g, g.w64, s, lane, [&](int c) { return (double)d[c]; }, sig);
+    sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return (double)d[c]; }, sig);
     double mon = 0.0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -346,7 +594,7 @@ __device__ __forceinline__ double outer_slice(const DevGrid& g, const DevState& 
 // ---------------------------------------------------------------- the persistent kernel
 
 template <bool MIXED>
-__global__ void __launch_bounds__(256) persistent_kernel(DevGrid g, DevState st, DevCtl ctl, RunParams rp) {
+__global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid g, DevState st, DevCtl ctl, RunParams rp) {
     using T = typename std::conditional<MIXED, float, double>::type;
     const unsigned nblocks = gridDim.x;
     const int lane = threadIdx.x & 31;
@@ -356,17 +604,36 @@ __global__ void __launch_bounds__(256) persistent_kernel(DevGrid g, DevState st,
     const int nthreads = (int)(gridDim.x * blockDim.x);
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     const T omega = (T)rp.omega;
+    __shared__ WarpCache s_cache[kWarpsPerBlock];
+    WarpCache* wc = &s_cache[threadIdx.x >> 5];
+    fill_warp_cache(g, *wc, gwarp, nwarps);
+    // TMA stages (mixed precision only; the launch passes the dynamic shared memory)
+    extern __shared__ __align__(128) unsigned char s_dyn[];
+    TmaWarp tw{};
+    if (MIXED) {
+        unsigned char* base = s_dyn + (threadIdx.x >> 5) * tma_warp_bytes(sizeof(float));
+        tw.stage[0] = base;
+        tw.stage[1] = base + tma_stage_bytes(sizeof(float));
+        tw.bar = reinterpret_cast<unsigned long long*>(base + 2 * tma_stage_bytes(sizeof(float)));
+        tw.parity = 0;
+        if (lane == 0) {
+            mbar_init(tw.bar + 0, 1);
+            mbar_init(tw.bar + 1, 1);
+            fence_proxy_async_smem();
+        }
+        __syncwarp();
+    }
 
     // Reduction slots rotate over 4 barrier-delimited phases: phase k merges into
     // slot k%4 and, at its start, clears slot (k+2)%4, whose last readers all
     // passed barrier k-1 (the host clears all four before the launch).
     int phase = 0;
     bool first_bar = true;
-    auto barrier = [&](bool want_val) -> BarrierResult {
+    auto barrier = [&](bool want_val, double v) -> BarrierResult {
         const bool skip = first_bar && (rp.debug_flags & PG_DEBUG_SKIP_ARRIVAL) && blockIdx.x == 0;
         first_bar = false;
-        const BarrierResult r =
-            grid_barrier(ctl, nblocks, rp.timeout_ns, skip, want_val ? ctl.red + (phase & 3) : nullptr);
+        const BarrierResult r = grid_barrier(ctl, nblocks, (unsigned)(phase + 1), rp.timeout_ns, skip, v,
+                                             want_val ? ctl.red + (phase & 3) : nullptr);
         ++phase;
         if (lead) ctl.red[(phase + 2) & 3] = 0ull;
         return r;
@@ -419,9 +686,9 @@ __global__ void __launch_bounds__(256) persistent_kernel(DevGrid g, DevState st,
         }
     };
 
+    const double target = rp.target_scale ? rp.target * __longlong_as_double((long long)*rp.target_scale) : rp.target;
     int vL = rp.cur, vP = rp.prev, vF = 3 - rp.cur - rp.prev;
     bool have_prev = rp.have_prev != 0;
-    const int nsl = g.n_slices;
 
     for (int sl = 0; sl < rp.nsteps; ++sl) {
         const long long sabs = rp.step0 + sl + 1;
@@ -432,40 +699,50 @@ __global__ void __launch_bounds__(256) persistent_kernel(DevGrid g, DevState st,
 
         // ---- phase A: RHS + warm start + residual, all colours
         double mon = 0.0;
-        for (int s = gwarp; s < nsl; s += nwarps)
-            mon = nanmax(mon, phase_rhs<MIXED>(g, st, rp, s, lane, vL, vP, vF, extrap, t, dsel));
-        block_max_into(mon, ctl.red + (phase & 3));
-        BarrierResult br = barrier(true);
+        for (int c = 0; c < g.ncol; ++c)
+            for (int tt = 0; tt < wc->cnt[c]; ++tt) {
+                const int s = wc->lo[c] + tt;
+                mon = nanmax(mon, phase_rhs<MIXED>(g, wc, warp_desc(g, *wc, c, tt, s), st, rp, s, lane, vL, vP, vF,
+                                                   extrap, t, dsel));
+            }
+        BarrierResult br = barrier(true, mon);
         if (!br.ok) { publish(-1); return; }
         double R = br.val;
 
         int sweeps = 0, outer = 0;
         bool ok = true;
-        while (!(R <= rp.target)) {
+        while (!(R <= target)) {
             if (!(R == R) || isinf(R) || outer >= rp.max_outer || sweeps >= rp.max_sweeps) { ok = false; break; }
             // inner relaxation on the correction
-            const double inner_tgt = MIXED ? fmax(0.5 * rp.target, rp.inner_reduction * R) : 0.5 * rp.target;
+            const double inner_tgt = MIXED ? fmax(0.5 * target, rp.inner_reduction * R) : 0.5 * target;
             const T* rr = MIXED ? (const T*)st.r32 : (const T*)st.r64;
             T* dd = dbuf<T>(st, dsel);
             const T* ww = MIXED ? (const T*)g.w32 : (const T*)g.w64;
             const T* iD = MIXED ? (const T*)g.invD32 : (const T*)g.invD64;
             double est_mark = INFINITY;   // monitor value at the last stagnation check
+            bool est_nan = false;         // a non-finite update (diverged, or a failed copy)
             int inner = 0;
             while (true) {
                 double est = 0.0;
                 for (int c = 0; c < g.ncol; ++c) {
-                    const int s0 = __ldg(g.colour_slice + c), s1 = __ldg(g.colour_slice + c + 1);
                     double m = 0.0;
-                    for (int s = s0 + gwarp; s < s1; s += nwarps)
-                        m = nanmax(m, sweep_slice<T>(g, ww, iD, rr, dd, s, lane, omega));
-                    block_max_into(m, ctl.red + (phase & 3));
-                    const BarrierResult be = barrier(true);
+                    if (MIXED) {
+                        m = sweep_colour_tma<T>(g, wc, tw, c, ww, iD, rr, dd, lane, omega, ctl.err, rp.timeout_ns);
+                    } else {
+                        for (int tt = 0; tt < wc->cnt[c]; ++tt) {
+                            const int s = wc->lo[c] + tt;
+                            m = nanmax(m, sweep_slice<T>(g, wc, warp_desc(g, *wc, c, tt, s), ww, iD, rr, dd, s, lane,
+                                                         omega));
+                        }
+                    }
+                    const BarrierResult be = barrier(true, m);
                     if (!be.ok) { publish(-1); return; }
                     est = nanmax(est, be.val);
                 }
                 ++sweeps;
                 ++inner;
-                if (est <= inner_tgt || !(est == est) || sweeps >= rp.max_sweeps) break;
+                if (!(est == est)) { est_nan = true; break; }
+                if (est <= inner_tgt || sweeps >= rp.max_sweeps) break;
                 // The inner solve stalls at its precision floor (about eps * ||M^-1 D|| of the
                 // correction); hand over to the FP64 outer pass when 16 sweeps gain < 10 %.
                 if ((inner & 15) == 0) {
@@ -473,13 +750,17 @@ __global__ void __launch_bounds__(256) persistent_kernel(DevGrid g, DevState st,
                     est_mark = est;
                 }
             }
+            if (est_nan) { ok = false; break; }
             // outer pass
             double m = 0.0;
             T* dn = dbuf<T>(st, dsel ^ 1);
-            for (int s = gwarp; s < nsl; s += nwarps)
-                m = nanmax(m, outer_slice<T>(g, st, dd, dn, MIXED ? st.r32 : nullptr, s, lane, vbuf(st, vF)));
-            block_max_into(m, ctl.red + (phase & 3));
-            br = barrier(true);
+            for (int c = 0; c < g.ncol; ++c)
+                for (int tt = 0; tt < wc->cnt[c]; ++tt) {
+                    const int s = wc->lo[c] + tt;
+                    m = nanmax(m, outer_slice<T>(g, wc, warp_desc(g, *wc, c, tt, s), st, dd, dn,
+                                                 MIXED ? st.r32 : nullptr, s, lane, vbuf(st, vF)));
+                }
+            br = barrier(true, m);
             if (!br.ok) { publish(-1); return; }
             R = br.val;
             dsel ^= 1;
@@ -500,10 +781,16 @@ __global__ void __launch_bounds__(256) persistent_kernel(DevGrid g, DevState st,
         }
         unsigned long long bk = ~0ull;
         int ba = 0x7fffffff;
+        double objsum = 0.0;
         for (int i = gtid; i < g.n_pad; i += nthreads) {
+            if (rp.v_perm_all) rp.v_perm_all[(long long)sl * g.n_pad + i] = vnew[i];
             const int o = __ldg(g.orig + i);
             if (o < 0) continue;
             const double x = vnew[i];
+            if (rp.obj_partials) {
+                const double sp = softplus_d(rp.obj_vref - x - rp.obj_margin);
+                objsum += sp * sp;
+            }
             if (rp.v_all) rp.v_all[(long long)sl * g.n_real + o] = x;
             if (rp.solve_out) rp.solve_out[o] = x;
             if (rp.vmin) {
@@ -532,6 +819,19 @@ __global__ void __launch_bounds__(256) persistent_kernel(DevGrid g, DevState st,
                 ctl.blk_arg[(sl & 1) * nblocks + blockIdx.x] = ba;
             }
         }
+        if (rp.obj_partials) {
+            // fixed-order block sum (deterministic, so finite differences of J are meaningful)
+            __shared__ double s_obj[kWarpsPerBlock];
+            for (int o = 16; o; o >>= 1) objsum += __shfl_down_sync(kFull, objsum, o);
+            if (lane == 0) s_obj[threadIdx.x >> 5] = objsum;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double t2 = 0.0;
+                for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t2 += s_obj[q];
+                rp.obj_partials[(long long)sl * nblocks + blockIdx.x] = t2;
+            }
+            __syncthreads();
+        }
         tot_sweeps += sweeps; tot_outer += outer;
         max_sw = max(max_sw, sweeps); max_out = max(max_out, outer);
         max_bound_R = fmax(max_bound_R, R);
@@ -540,7 +840,7 @@ __global__ void __launch_bounds__(256) persistent_kernel(DevGrid g, DevState st,
         // rotate: the new state becomes the latest
         vP = vL; vL = vF; vF = 3 - vL - vP;
         have_prev = true;
-        if (!barrier(false).ok) { publish(-1); return; }
+        if (!barrier(false, 0.0).ok) { publish(-1); return; }
     }
     if (rp.nsteps > 0) finalize_vmin(rp.nsteps - 1);
     publish(-1);
@@ -563,7 +863,7 @@ __global__ void __launch_bounds__(256) power_step_kernel(DevGrid g, const double
         ld4(x + i0, xv);
         ldg4(g.D64 + i0, D);
         ldg4(g.invD64 + i0, iD);
-        sell_row<double>(g, g.w64, s, lane, [&](int c) { return x[c] * sc; }, sig);
+        sell_row<1, double>(g, nullptr, global_desc(g, s), g.w64, s, lane, [&](int c) { return x[c] * sc; }, sig);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const double xs = xv[j] * sc;
@@ -597,23 +897,107 @@ __global__ void permute_in_kernel(const int32_t* __restrict__ orig, const double
     }
 }
 
+// ---------------------------------------------------------------- adjoint (not in the paper)
+
+// rhs = dJ/dv_s + (C/h) lambda_{s+1} with dJ/dv = -2 softplus(u) sigmoid(u), u = vref - v - margin;
+// also max |rhs| / D into *scale_slot (sets the relative solve target).
+__global__ void __launch_bounds__(256) adjoint_rhs_kernel(DevGrid g, const double* __restrict__ v,
+                                                         const double* __restrict__ lam_next,
+                                                         double* __restrict__ rhs, double vref, double margin,
+                                                         unsigned long long* scale_slot) {
+    double m = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n_pad; i += gridDim.x * blockDim.x) {
+        double r = 0.0;
+        if (__ldg(g.orig + i) >= 0) {
+            const double u = vref - v[i] - margin;
+            r = -2.0 * softplus_d(u) * sigmoid_d(u) + __ldg(g.ch + i) * lam_next[i];
+            m = fmax(m, fabs(r) * __ldg(g.invD64 + i));
+        }
+        rhs[i] = r;
+    }
+    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(scale_slot, (unsigned long long)__double_as_longlong(m));
+}
+
+// Gradient sums of one step (FP64): per neighbour slot with col > node (each edge once)
+// acc_slot += (lam_i - lam_j)(v_i - v_j); per node acc_lv += lam v, acc_l += lam,
+// acc_dv += lam (v - v_prev).
+__global__ void __launch_bounds__(256) adjoint_grad_kernel(DevGrid g, const double* __restrict__ lam,
+                                                          const double* __restrict__ v,
+                                                          const double* __restrict__ v_prev,
+                                                          double* __restrict__ acc_slot, double* __restrict__ acc_lv,
+                                                          double* __restrict__ acc_l, double* __restrict__ acc_dv) {
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int s = gwarp; s < g.n_slices; s += nwarps) {
+        const SliceDesc d = global_desc(g, s);
+        const int i0 = s * kSlice + lane * kVec;
+        double li[4], vi[4], vp[4];
+        ld4(lam + i0, li);
+        ld4(v + i0, vi);
+        ld4(v_prev + i0, vp);
+        for (int j = 0; j < 4; ++j) {
+            acc_lv[i0 + j] += li[j] * vi[j];
+            acc_l[i0 + j] += li[j];
+            acc_dv[i0 + j] += li[j] * (vi[j] - vp[j]);
+        }
+        for (int k = 0; k < d.K; ++k) {
+            const long long e = d.off + (long long)k * kSlice + lane * kVec;
+            int c[4];
+            if (d.dpos != -1) {
+                const int o = __ldg(g.dia_off + (-2 - d.dpos) + k);
+                if (o <= 0) continue;                       // the neighbour with the larger index owns it
+                c[0] = i0 + o; c[1] = i0 + 1 + o; c[2] = i0 + 2 + o; c[3] = i0 + 3 + o;
+            } else {
+                ldg4(g.ell_col + e, c);
+            }
+            for (int j = 0; j < 4; ++j)
+                if (c[j] > i0 + j) acc_slot[e + j] += (li[j] - lam[c[j]]) * (vi[j] - v[c[j]]);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- host-side launch helpers
+
+// Dynamic shared memory of the persistent kernel: the TMA stages of the FP32 sweep.
+static size_t persistent_smem(bool mixed) {
+    return mixed ? (size_t)kWarpsPerBlock * tma_warp_bytes(sizeof(float)) : 0;
+}
 
 cudaError_t launch_persistent(bool mixed, const DevGrid& g, const DevState& st, const DevCtl& ctl,
                               const RunParams& rp, int blocks, int threads, cudaStream_t stream) {
     void* args[] = {(void*)&g, (void*)&st, (void*)&ctl, (void*)&rp};
     const void* fn = mixed ? (const void*)persistent_kernel<true> : (const void*)persistent_kernel<false>;
-    return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, stream);
+    return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, persistent_smem(mixed), stream);
 }
 
 cudaError_t persistent_occupancy(bool mixed, int threads, int* blocks_per_sm) {
     const void* fn = mixed ? (const void*)persistent_kernel<true> : (const void*)persistent_kernel<false>;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, 0);
+    const size_t smem = persistent_smem(mixed);
+    if (smem > 0) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);
 }
 
 cudaError_t launch_power_step(const DevGrid& g, const double* x, double* y, const unsigned long long* xmax_prev,
                               double* acc, unsigned long long* ymax, int blocks, cudaStream_t stream) {
     power_step_kernel<<<blocks, 256, 0, stream>>>(g, x, y, xmax_prev, acc, ymax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_rhs(const DevGrid& g, const double* v, const double* lam_next, double* rhs, double vref,
+                               double margin, unsigned long long* scale_slot, int blocks, cudaStream_t stream) {
+    adjoint_rhs_kernel<<<blocks, 256, 0, stream>>>(g, v, lam_next, rhs, vref, margin, scale_slot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_grad(const DevGrid& g, const double* lam, const double* v, const double* v_prev,
+                                double* acc_slot, double* acc_lv, double* acc_l, double* acc_dv, int blocks,
+                                cudaStream_t stream) {
+    adjoint_grad_kernel<<<blocks, 256, 0, stream>>>(g, lam, v, v_prev, acc_slot, acc_lv, acc_l, acc_dv);
     return cudaGetLastError();
 }
 

@@ -166,6 +166,7 @@ extern "C" pg_status pg_solve_noalloc(pg_grid* g, double h, const double* b, dou
         stats->q = g->q;
         stats->step_tol = tol;
         stats->device_ms = ms;
+        stats->kacc = 1.0;
     }
     if (err == PG_ERR_TIMEOUT) return fail(PG_ERR_TIMEOUT, "device barrier timed out");
     if (err == PG_ERR_NOT_CONVERGED) return fail(PG_ERR_NOT_CONVERGED, "relaxation did not converge");

@@ -286,11 +286,9 @@ def config2(seed: int = 2, nx: int = 512, ny: int = 512, nl: int = 2) -> Netlist
     return net
 
 
-def config3(seed: int = 3, n_grids: int = 256, side_lo: int = 64, side_hi: int = 512) -> Netlist:
-    """256 independent RC grids of uneven size (side U{64..512}, 1-2 layers),
-    each drawn like config 0 from its own child seed; 2-layer grids get vias
-    U[5,20] S with pads on the top layer and caps/loads on the bottom layer.
-    h = 10 ps, 500 steps, FP32 sweeps with FP64 refinement."""
+def config3_parts(seed: int = 3, n_grids: int = 256, side_lo: int = 64, side_hi: int = 512):
+    """The independent grids of :func:`config3`, each as its own netlist with node
+    ids starting at 0, plus the node offset at which it sits in the batch."""
     root = np.random.SeedSequence(seed)
     top = np.random.Generator(np.random.PCG64(root))
     sides = top.integers(side_lo, side_hi + 1, size=n_grids)
@@ -302,13 +300,29 @@ def config3(seed: int = 3, n_grids: int = 256, side_lo: int = 64, side_hi: int =
         spec = LatticeSpec(nx=s, ny=s, nl=nlk, g_layer=("uniform", 0.5, 2.0),
                            g_via=("uniform", 5.0, 20.0), pad_pitch=10,
                            cap_layers=(0,), cap=("uniform", 10e-15, 100e-15), load_frac=0.2)
-        parts.append(lattice_netlist(spec, np.random.Generator(np.random.PCG64(children[k])),
-                                     node_offset=off))
-        off += parts[-1].n_nodes
-    net = concat_netlists(parts, name=f"batched_{n_grids}_rc_grids")
+        part = lattice_netlist(spec, np.random.Generator(np.random.PCG64(children[k])))
+        parts.append((off, part))
+        off += part.n_nodes
+    return parts
+
+
+def config3(seed: int = 3, n_grids: int = 256, side_lo: int = 64, side_hi: int = 512) -> Netlist:
+    """256 independent RC grids of uneven size (side U{64..512}, 1-2 layers),
+    each drawn like config 0 from its own child seed; 2-layer grids get vias
+    U[5,20] S with pads on the top layer and caps/loads on the bottom layer.
+    h = 10 ps, 500 steps, FP32 sweeps with FP64 refinement."""
+    parts = config3_parts(seed, n_grids, side_lo, side_hi)
+    shifted = []
+    for off, p in parts:
+        sh = lambda t: np.where(t >= 0, t + off, t).astype(np.int32)
+        shifted.append(Netlist(**{**p.__dict__, "r_a": sh(p.r_a), "r_b": sh(p.r_b), "c_a": sh(p.c_a),
+                                  "c_b": sh(p.c_b), "l_a": sh(p.l_a), "l_b": sh(p.l_b),
+                                  "i_a": sh(p.i_a), "i_b": sh(p.i_b)}))
+    net = concat_netlists(shifted, name=f"batched_{n_grids}_rc_grids")
     net.meta = dict(h=10e-12, nsteps=500, precision="mixed",
-                    grid_sizes=[p.n_nodes for p in parts],
-                    grid_shapes=[p.lattice for p in parts])
+                    grid_sizes=[p.n_nodes for _, p in parts],
+                    grid_shapes=[p.lattice for _, p in parts],
+                    grid_offsets=[off for off, _ in parts])
     return net
 
 

@@ -147,8 +147,11 @@ def test_bounds_are_upper_bounds(B):
     _, _, _, _, st = run_gpu(B, net, h, 2, 0)
     kx = bounds.scaled_minv_inf_norm(net, h)
     qx = bounds.step_gain(net, h)
+    ax = bounds.accumulation_gain(net, h)
     assert kx <= st.kappa <= kx * 1.01
     assert qx <= st.q <= qx + 0.01
+    assert ax <= st.kacc <= ax + 0.01
+    assert st.kacc <= 1.0 / (1.0 - st.q)
 
 
 def test_resume_equals_one_run(B):

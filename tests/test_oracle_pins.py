@@ -51,6 +51,31 @@ def test_single_node_bounds_closed_form():
     assert bounds.step_gain(net, h) == pytest.approx((C / h) / (C / h + g0), rel=1e-14)
 
 
+def test_accumulation_gain_bounds_error_propagation():
+    """Per-step errors eta_k with |eta_k| <= 1 propagate through e_s = T e_{s-1} + eta_s,
+    T = M^-1 C/h; the accumulation gain bounds |e_s| for every sign pattern, is
+    attained by eta = 1, and never exceeds 1/(1-q)."""
+    net = pgsynth.config1(nx=9, ny=7)
+    h = net.meta["h"]
+    mats = matrices.nodal_matrices(net)
+    M = mats.system_matrix(h).toarray()
+    T = np.linalg.solve(M, np.diag(mats.C.diagonal() / h))
+    K = bounds.accumulation_gain(net, h)
+    q = bounds.step_gain(net, h)
+    assert K <= 1.0 / (1.0 - q) + 1e-9
+    rng = np.random.default_rng(2)
+    for trial in range(5):
+        e = np.zeros(net.n_nodes)
+        worst = 0.0
+        for s in range(3000):
+            eta = np.ones(net.n_nodes) if trial == 0 else rng.choice([-1.0, 1.0], net.n_nodes)
+            e = T @ e + eta
+            worst = max(worst, np.max(np.abs(e)))
+        assert worst <= K * (1 + 1e-9)
+        if trial == 0:
+            assert worst == pytest.approx(K, rel=1e-6)     # the all-ones pattern attains it
+
+
 def test_two_node_rc_hand_derived():
     """Pad(G0) - node0 - R(g) - node1 with C1 and a constant load I at node 1.
 
@@ -342,3 +367,42 @@ def test_generator_multilayer_counts():
     assert np.all(net.r_a[net.r_b < 0] >= 2 * nx * ny)  # pads on the top layer
     r = pgsynth.config2(nx=32, ny=32).counts()
     assert r["L"] == 32 * 32 + 4  # every via and every pad
+
+
+# ---------------------------------------------------------------- adjoint (not in the paper)
+
+def _adjoint_case():
+    net = pgsynth.config0(nx=7, ny=6)
+    # a resistor to ground and loads already on at t = 0 make the DC point depend on G
+    net.r_a = np.concatenate([net.r_a, np.array([20], np.int32)])
+    net.r_b = np.concatenate([net.r_b, np.array([GROUND], np.int32)])
+    net.r_g = np.concatenate([net.r_g, np.array([0.3])])
+    net.i_v = net.i_v.copy() * 40.0                 # drops of tens of mV
+    net.i_v[0::3] = 5e-3
+    return net
+
+
+def test_adjoint_matches_central_differences():
+    """The oracle's discrete adjoint against central finite differences of the
+    oracle's own forward objective (exact direct solves), for resistors (segments,
+    pads, a resistor to ground: DC-point term) and capacitors."""
+    from oracle import adjoint
+    net = _adjoint_case()
+    h, S = 10e-12, 25
+    J, dG, dC = adjoint.gradients(net, h, S)
+    assert J == pytest.approx(adjoint.objective(net, h, S), rel=1e-12)
+    rng = np.random.default_rng(4)
+    picks = [("r", int(k)) for k in rng.choice(len(net.r_g), 8, replace=False)]
+    picks += [("r", len(net.r_g) - 1), ("r", int(np.nonzero(net.r_b < -1)[0][0]))]
+    picks += [("c", int(k)) for k in rng.choice(len(net.c_val), 6, replace=False)]
+    for kind, k in picks:
+        arr = net.r_g if kind == "r" else net.c_val
+        d = 1e-4 * arr[k]
+        vals = []
+        for sgn in (+1, -1):
+            pert = arr.copy(); pert[k] += sgn * d
+            n2 = pgsynth.Netlist(**{**net.__dict__, ("r_g" if kind == "r" else "c_val"): pert})
+            vals.append(adjoint.objective(n2, h, S))
+        fd = (vals[0] - vals[1]) / (2 * d)
+        ad = dG[k] if kind == "r" else dC[k]
+        assert ad == pytest.approx(fd, rel=2e-5, abs=1e-9 * abs(J) / arr[k]), (kind, k)
