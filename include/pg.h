@@ -105,6 +105,11 @@ typedef struct pg_options {
     int32_t blocks_per_sm;    /* 0 -> as many as fit */
     double barrier_timeout_s; /* device barrier time limit (0 -> 2 s) */
     int32_t debug_flags;      /* PG_DEBUG_* test hooks; 0 in production */
+    int32_t lattice_sweeps;   /* PG_PREC_MIXED on a lattice netlist (lat_nx/ny/nl given, <= 3 layers,
+                                 branches only between lattice neighbours): k > 0 runs the inner solve
+                                 as shared-memory tiles with ghost zones, k exact red-black sweeps per
+                                 device barrier (k <= 7); 0 (default) keeps the neighbour-list sweep,
+                                 which measures faster on GB300 */
 } pg_options;
 
 /* Fill *opt with the defaults listed above. */

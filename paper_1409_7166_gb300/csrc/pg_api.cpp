@@ -107,6 +107,12 @@ pg_status alloc_device(pg_grid* g) {
     double* cinj = g->alloc<double>(np);
     float* w32 = g->mixed ? g->alloc<float>(P.n_ell) : nullptr;
     float* invD32 = g->mixed ? g->alloc<float>(np) : nullptr;
+    if (g->mixed && P.lattice && g->opt.lattice_sweeps > 0) {
+        float* lw[4];
+        for (auto& q : lw) if (!(q = g->alloc<float>(P.n))) return PG_ERR_OOM;
+        d.lat_nx = P.lat_nx; d.lat_ny = P.lat_ny; d.lat_nl = P.lat_nl;
+        d.lwE = lw[0]; d.lwN = lw[1]; d.lwU = lw[2]; d.liD = lw[3];
+    }
     if (!colour_slice || !slice_off || !slice_w || !slice_doff || !dia_off || !ell_col || !orig || !ld_ptr ||
         !ld_idx || !pwl_ptr || !pwl_t || !pwl_v || !ind_a || !ind_b || !ind_hl || !ind_ptr || !ind_idx || !vdd ||
         !w64 || !D64 || !invD64 || !ch || !cinj || (g->mixed && (!w32 || !invD32)))
@@ -203,6 +209,22 @@ pg_status assemble_h(pg_grid* g, double h) {
         (s = upload(g, const_cast<double*>(g->dg.ch), ch)) || (s = upload(g, const_cast<double*>(g->dg.cinj), cinj)) ||
         (s = upload(g, const_cast<double*>(g->dg.w64), w)) || (s = upload(g, const_cast<double*>(g->dg.ind_hl), hl)))
         return s;
+    if (g->dg.lwE) {
+        // lattice form of the FP32 inner solve: each branch weight once, caller order
+        std::vector<float> e(P.n, 0.f), nn(P.n, 0.f), u(P.n, 0.f), id(P.n, 0.f);
+        for (int o = 0; o < P.n; ++o) {
+            for (int64_t a = P.adj_ptr[o]; a < P.adj_ptr[o + 1]; ++a) {
+                const float w = (float)(P.adj_g[a] + h * P.adj_il[a]);
+                if (P.adj_dir[a] == 0) e[o] = w;
+                else if (P.adj_dir[a] == 1) nn[o] = w;
+                else if (P.adj_dir[a] == 2) u[o] = w;
+            }
+            id[o] = (float)iD[P.perm[o]];
+        }
+        if ((s = upload(g, const_cast<float*>(g->dg.lwE), e)) || (s = upload(g, const_cast<float*>(g->dg.lwN), nn)) ||
+            (s = upload(g, const_cast<float*>(g->dg.lwU), u)) || (s = upload(g, const_cast<float*>(g->dg.liD), id)))
+            return s;
+    }
     if (g->mixed) {
         std::vector<float> w32(P.n_ell), iD32(np);
         for (int64_t e = 0; e < P.n_ell; ++e) w32[e] = (float)w[e];
@@ -230,6 +252,7 @@ RunParams pg::base_params(const pg_grid* g) {
     rp.debug_flags = g->opt.debug_flags;
     rp.cur = g->vL; rp.prev = g->vP;
     rp.warm_extrap = g->opt.warm_start;
+    rp.lat_k = g->dg.lwE ? g->opt.lattice_sweeps : 0;
     return rp;
 }
 
@@ -328,10 +351,10 @@ pg_status prepare_h(pg_grid* g, double h);
 pg_status ensure_dc_grid(pg_grid* g) {
     if (g->dcgrid) return PG_OK;
     pg_netlist d = g->nc.dc_view();
-    pg_options o = g->opt;
-    o.precision = PG_PREC_FP64;
+    pg_options o = g->opt;          // same precision as the grid (FP64 sweeps are slow on GB300)
     o.omega = 0.0;
     o.step_tol = 0.5 * g->opt.tol;
+    d.lat_nx = g->nc.nx; d.lat_ny = g->nc.ny; d.lat_nl = g->nc.nl;
     std::unique_ptr<pg_grid> sub;
     pg_status s = create_impl(&d, &o, sub);
     if (s == PG_ERR_FLOATING_NODE)
@@ -508,6 +531,7 @@ pg_status create_impl(const pg_netlist* nl, const pg_options* opt, std::unique_p
     if (o.threads_per_block <= 0) o.threads_per_block = 256;
     if (o.threads_per_block != 256) { g_last_error = "threads_per_block must be 256"; return PG_ERR_INVALID_ARG; }
     if (o.barrier_timeout_s <= 0.0) o.barrier_timeout_s = 2.0;
+    if (o.lattice_sweeps > 7) { g_last_error = "lattice_sweeps must be <= 7"; return PG_ERR_INVALID_ARG; }
     g->threads = o.threads_per_block;
     g->mixed = o.precision == PG_PREC_MIXED;
     std::string why;

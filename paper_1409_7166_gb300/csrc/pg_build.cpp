@@ -177,6 +177,29 @@ pg_status build_packed(const pg_netlist* nl, Packed* P, std::string* why) {
     }
     { std::vector<int32_t>().swap(tn); std::vector<double>().swap(tg); std::vector<double>().swap(tl); }
 
+    // --- lattice form: every merged neighbour pair is a lattice neighbour pair
+    P->lattice = false;
+    P->adj_dir.assign(P->adj_nbr.size(), -1);
+    if (nl->lat_nx > 0 && nl->lat_ny > 0 && nl->lat_nl > 0 && nl->lat_nl <= 3 &&
+        (int64_t)nl->lat_nx * nl->lat_ny * nl->lat_nl == n) {
+        const int32_t nx = nl->lat_nx, ny = nl->lat_ny;
+        bool ok = true;
+        for (int i = 0; i < n && ok; ++i) {
+            for (int64_t k = P->adj_ptr[i]; k < P->adj_ptr[i + 1]; ++k) {
+                const int j = P->adj_nbr[k];
+                const int xi = i % nx, yi = (i / nx) % ny, li = i / (nx * ny);
+                const int xj = j % nx, yj = (j / nx) % ny, lj = j / (nx * ny);
+                const int dx = xj - xi, dy = yj - yi, dl = lj - li;
+                if (dx == 1 && dy == 0 && dl == 0) P->adj_dir[k] = 0;
+                else if (dx == 0 && dy == 1 && dl == 0) P->adj_dir[k] = 1;
+                else if (dx == 0 && dy == 0 && dl == 1) P->adj_dir[k] = 2;
+                else if (!((dx == -1 && dy == 0 && dl == 0) || (dx == 0 && dy == -1 && dl == 0) ||
+                           (dx == 0 && dy == 0 && dl == -1))) { ok = false; break; }
+            }
+        }
+        if (ok) { P->lattice = true; P->lat_nx = nx; P->lat_ny = ny; P->lat_nl = nl->lat_nl; }
+    }
+
     // --- colouring: BFS 2-colouring (red-black), else greedy multicolour
     std::vector<int32_t> colour(n, -1);
     bool bipartite = true;

@@ -56,6 +56,12 @@ struct Packed {
     std::vector<double> ind_invL;
     std::vector<int32_t> ind_ptr, ind_idx;    // per permuted node CSR of signed inductor ids
 
+    // lattice form (optional): nodes (x, y, l) with id (l*ny + y)*nx + x and every
+    // branch between lattice neighbours; adj_dir marks the +x / +y / +l entries
+    bool lattice = false;
+    int32_t lat_nx = 0, lat_ny = 0, lat_nl = 0;
+    std::vector<int8_t> adj_dir;   // 0: +x, 1: +y, 2: +l, -1: the reverse entries
+
     // components (connected sub-circuits, Fig. 1)
     int32_t n_comp = 0;
     std::vector<uint8_t> comp_has_r_anchor;
@@ -98,6 +104,12 @@ struct DevGrid {
     const int32_t* ind_ptr;
     const int32_t* ind_idx;
     const double* vdd;
+    // lattice form of the FP32 inner solve (caller order), or null
+    int32_t lat_nx, lat_ny, lat_nl;
+    const float* lwE;        // weight to (x+1, y, l); 0 on the last column
+    const float* lwN;        // weight to (x, y+1, l)
+    const float* lwU;        // weight to (x, y, l+1)
+    const float* liD;        // 1 / D
 };
 
 enum Mode : int32_t { kModeTransient = 0, kModeSolve = 1 };
@@ -161,6 +173,7 @@ struct RunParams {
     double* v_perm_all;       // [nsteps x n_pad] voltages in permuted order (adjoint recompute)
     double* obj_partials;     // [nsteps x nblocks] per-block sums of softplus(vref - v - margin)^2
     double obj_vref, obj_margin;
+    int32_t lat_k;            // > 0: lattice inner solve, lat_k exact red-black sweeps per round
 };
 
 }  // namespace pg

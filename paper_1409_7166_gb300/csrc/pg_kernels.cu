@@ -84,6 +84,11 @@ __device__ __forceinline__ double sigmoid_d(double u) { return 0.5 * (1.0 + tanh
 
 // max that lets a NaN win, so a diverged iterate is never mistaken for convergence
 __device__ __forceinline__ double nanmax(double a, double b) { return (a > b || a != a) ? a : b; }
+// FP32 version for the FP32 sweeps: GB300's FP64 pipe is a small fraction of its FP32
+// rate, so even a per-node double compare would cost a large share of a sweep.
+__device__ __forceinline__ float nanmaxf(float a, float b) { return (a > b || a != a) ? a : b; }
+template <typename T>
+__device__ __forceinline__ T nanmax_t(T a, T b) { return (a > b || a != a) ? a : b; }
 
 // Order-preserving map of a double to an unsigned key (for min reductions).
 __device__ __forceinline__ unsigned long long order_key(double x) {
@@ -363,7 +368,15 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* w
     }
     st4(vbuf(st, vF) + i0, vw);
     st4(st.r64 + i0, r);
-    if (MIXED) {
+    if (MIXED && rp.lat_k > 0) {
+        // the lattice inner solve keeps its FP32 residual and correction in caller order
+        float* dz = dbuf<float>(st, dsel);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int o = __ldg(g.orig + i0 + j);
+            if (o >= 0) { st.r32[o] = (float)r[j]; dz[o] = 0.f; }
+        }
+    } else if (MIXED) {
         float r32[4] = {(float)r[0], (float)r[1], (float)r[2], (float)r[3]};
         float z[4] = {0.f, 0.f, 0.f, 0.f};
         st4(st.r32 + i0, r32);
@@ -385,15 +398,15 @@ __device__ __forceinline__ double sweep_slice(const DevGrid& g, const WarpCache*
     ld4(r + i0, rv);
     ldg4(invD + i0, iD);
     sell_row<kSweepUnroll, T>(g, wc, sd, w, s, lane, [&](int c) { return d[c]; }, sig);
-    double mon = 0.0;
+    T mon = T(0);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const T upd = (rv[j] + sig[j]) * iD[j] - dv[j];
         dv[j] = fma(omega, upd, dv[j]);
-        mon = nanmax(mon, (double)fabs(upd));
+        mon = nanmax_t<T>(mon, fabs(upd));
     }
     st4(d + i0, dv);
-    return mon;
+    return (double)mon;
 }
 
 // ---- TMA-fed sweep (FP32 path)
@@ -492,15 +505,15 @@ __device__ __forceinline__ double sweep_slice_staged(const DevGrid& g, const War
 #pragma unroll
         for (int j = 0; j < 4; ++j) sig[j] = fma(wv[j], d[i0 + j + o], sig[j]);
     }
-    double mon = 0.0;
+    T mon = T(0);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const T upd = (rv[j] + sig[j]) * iD[j] - dv[j];
         dv[j] = fma(omega, upd, dv[j]);
-        mon = nanmax(mon, (double)fabs(upd));
+        mon = nanmax_t<T>(mon, fabs(upd));
     }
     st4(d + i0, dv);
-    return mon;
+    return (double)mon;
 }
 
 // The warp's run of colour-c slices, double-buffered through the TMA.  Returns
@@ -556,20 +569,178 @@ __device__ double sweep_colour_tma(const DevGrid& g, const WarpCache* wc, TmaWar
     return mon;
 }
 
+// ---- lattice inner solve (FP32, ghost zones)
+//
+// For a lattice grid (nodes (x, y, l), branches only between lattice
+// neighbours) the inner relaxation runs on 32 x 32-column regions of all
+// layers held in shared memory.  A region is its tile of (32 - 2H)^2 columns
+// plus a ghost zone of H = 2k columns on each side; k exact red-black SOR
+// sweeps (2k half-sweeps, colour = parity of x + y + l) are applied to the
+// whole region, the outermost ring never being updated.  After half-sweep j
+// every node at distance >= j from the region's edge holds the exact
+// red-black value, so after 2k half-sweeps the tile interior equals k global
+// red-black sweeps (Eq. 16-17).  Tiles read the previous round's corrections
+// and write the next buffer, so a round needs one device barrier for k sweeps,
+// and every branch weight is stored once (E, N, U per node).
+constexpr int kLatR = 32;                          // region side (columns)
+constexpr int kLatMaxL = 3;                        // layers held per region
+constexpr int kLatPlane = kLatR * kLatR;
+
+__host__ __device__ constexpr int lattice_smem_bytes() { return 6 * kLatMaxL * kLatPlane * (int)sizeof(float); }
+
+// Asynchronous global -> shared copies (no registers held while in flight);
+// src_bytes = 0 fills the destination with zeros.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, unsigned src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, unsigned src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// One round over all tiles of the lattice; returns the max unrelaxed update of
+// the last sweep over tile interiors.  NL (the layer count) is a template
+// parameter so the layer loop unrolls and the vertical neighbours need no
+// run-time tests.
+template <int NL>
+__device__ double lattice_round_nl(const DevGrid& g, const float* __restrict__ dold, float* __restrict__ dnew,
+                                   const float* __restrict__ r, float omega, int k, unsigned char* smem) {
+    const int nx = g.lat_nx, ny = g.lat_ny;
+    const int H = 2 * k, T = kLatR - 2 * H;
+    const int tiles_x = (nx + T - 1) / T, tiles_y = (ny + T - 1) / T, ntiles = tiles_x * tiles_y;
+    float* sd = reinterpret_cast<float*>(smem);
+    float* sr = sd + kLatMaxL * kLatPlane;
+    float* si = sr + kLatMaxL * kLatPlane;
+    float* se = si + kLatMaxL * kLatPlane;
+    float* sn = se + kLatMaxL * kLatPlane;
+    float* su = sn + kLatMaxL * kLatPlane;
+    const int rx = threadIdx.x & (kLatR - 1);
+    const int ry0 = threadIdx.x >> 5;                 // rows ry0, ry0 + 8, ry0 + 16, ry0 + 24
+    const long long plane = (long long)nx * ny;
+    // 16-byte copies need every region row to start on a 4-float boundary
+    const bool vec16 = (nx & 3) == 0 && (H & 3) == 0 && (T & 3) == 0;
+    float mon = 0.f;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int x0 = (tile % tiles_x) * T - H, y0 = (tile / tiles_x) * T - H;
+        const int x = x0 + rx;
+        auto src_of = [&](int arr) -> const float* {   // by value: no local array
+            return arr == 0 ? dold : arr == 1 ? r : arr == 2 ? g.liD : arr == 3 ? g.lwE : arr == 4 ? g.lwN : g.lwU;
+        };
+        if (vec16) {
+            // one 16-byte chunk per thread per (array, layer) plane: 32 rows x 8 chunks = 256
+            const int ry = threadIdx.x >> 3, cx = threadIdx.x & 7;
+            const int xx = x0 + 4 * cx, yy = y0 + ry;
+            const bool in = yy >= 0 && yy < ny && xx >= 0 && xx < nx;   // nx, x0 multiples of 4
+            const long long off = in ? (long long)yy * nx + xx : 0;
+            const int sa = ry * kLatR + 4 * cx;
+#pragma unroll
+            for (int arr = 0; arr < 6; ++arr)
+#pragma unroll
+                for (int l = 0; l < NL; ++l)
+                    cp_async16(sd + arr * kLatMaxL * kLatPlane + l * kLatPlane + sa,
+                               src_of(arr) + (in ? l * plane + off : 0), in ? 16u : 0u);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int ry = ry0 + 8 * q, yy = y0 + ry;
+                const bool in = yy >= 0 && yy < ny && x >= 0 && x < nx;
+                const long long off = in ? (long long)yy * nx + x : 0;
+                const int sa = ry * kLatR + rx;
+#pragma unroll
+                for (int arr = 0; arr < 6; ++arr)
+#pragma unroll
+                    for (int l = 0; l < NL; ++l)
+                        cp_async4(sd + arr * kLatMaxL * kLatPlane + l * kLatPlane + sa,
+                                  src_of(arr) + (in ? l * plane + off : 0), in ? 4u : 0u);
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        // per-row predicates (identical for every half-sweep of the tile)
+        bool act[4], inner[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int ry = ry0 + 8 * q, y = y0 + ry;
+            const int edge = min(min(rx, ry), min(kLatR - 1 - rx, kLatR - 1 - ry));
+            act[q] = edge > 0 && x >= 0 && x < nx && y >= 0 && y < ny;
+            inner[q] = act[q] && edge >= H;
+        }
+        for (int hs = 0; hs < 2 * k; ++hs) {
+            const bool last = hs >= 2 * k - 2;
+            const int par = (x + y0 + ry0 + hs) & 1;      // rows ry0 + 8q share the parity of y
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+#pragma unroll
+                for (int l = 0; l < NL; ++l) {
+                    if (((l & 1) != par) || !act[q]) continue;
+                    const int a = l * kLatPlane + (ry0 + 8 * q) * kLatR + rx;
+                    float sig = se[a] * sd[a + 1] + se[a - 1] * sd[a - 1] + sn[a] * sd[a + kLatR] +
+                                sn[a - kLatR] * sd[a - kLatR];
+                    if (l + 1 < NL) sig += su[a] * sd[a + kLatPlane];
+                    if (l > 0) sig += su[a - kLatPlane] * sd[a - kLatPlane];
+                    const float dv = sd[a];
+                    const float upd = (sr[a] + sig) * si[a] - dv;
+                    sd[a] = fmaf(omega, upd, dv);
+                    if (last && inner[q]) mon = nanmaxf(mon, fabsf(upd));
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (!inner[q]) continue;
+            const long long b = (long long)(y0 + ry0 + 8 * q) * nx + x;
+#pragma unroll
+            for (int l = 0; l < NL; ++l) dnew[b + l * plane] = sd[l * kLatPlane + (ry0 + 8 * q) * kLatR + rx];
+        }
+        __syncthreads();   // the next tile overwrites the region
+    }
+    return (double)mon;
+}
+
+__device__ __forceinline__ double lattice_round(const DevGrid& g, const float* dold, float* dnew, const float* r,
+                                                float omega, int k, unsigned char* smem) {
+    switch (g.lat_nl) {
+        case 1: return lattice_round_nl<1>(g, dold, dnew, r, omega, k, smem);
+        case 2: return lattice_round_nl<2>(g, dold, dnew, r, omega, k, smem);
+        default: return lattice_round_nl<3>(g, dold, dnew, r, omega, k, smem);
+    }
+}
+
 // Outer defect-correction pass: v += delta, r -= M delta (FP64), refresh the FP32 residual.
 template <typename T>
 __device__ __forceinline__ double outer_slice(const DevGrid& g, const WarpCache* wc, const SliceDesc& sd,
                                               const DevState& st, const T* d, T* dnext, float* r32, int s, int lane,
-                                              double* v) {
+                                              double* v, bool lat) {
     const int i0 = s * kSlice + lane * kVec;
     T dv[4];
-    ld4(d + i0, dv);
+    if (lat) {
+        // correction in caller order (lattice inner solve); padding has none
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int o = __ldg(g.orig + i0 + j);
+            dv[j] = o >= 0 ? d[o] : T(0);
+        }
+    } else {
+        ld4(d + i0, dv);
+    }
     double D[4], iD[4], r[4], vv[4], sig[4];
     ldg4(g.D64 + i0, D);
     ldg4(g.invD64 + i0, iD);
     ld4(st.r64 + i0, r);
     ld4(v + i0, vv);
-    sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return (double)d[c]; }, sig);
+    if (lat) {
+        sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) {
+            const int o = __ldg(g.orig + c);
+            return o >= 0 ? (double)d[o] : 0.0;
+        }, sig);
+    } else {
+        sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return (double)d[c]; }, sig);
+    }
     double mon = 0.0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -580,11 +751,19 @@ __device__ __forceinline__ double outer_slice(const DevGrid& g, const WarpCache*
     }
     st4(st.r64 + i0, r);
     st4(v + i0, vv);
-    T z[4] = {T(0), T(0), T(0), T(0)};
-    st4(dnext + i0, z);
-    if (r32) {
-        float f[4] = {(float)r[0], (float)r[1], (float)r[2], (float)r[3]};
-        st4(r32 + i0, f);
+    if (lat) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int o = __ldg(g.orig + i0 + j);
+            if (o >= 0) { dnext[o] = T(0); r32[o] = (float)r[j]; }
+        }
+    } else {
+        T z[4] = {T(0), T(0), T(0), T(0)};
+        st4(dnext + i0, z);
+        if (r32) {
+            float f[4] = {(float)r[0], (float)r[1], (float)r[2], (float)r[3]};
+            st4(r32 + i0, f);
+        }
     }
     return mon;
 }
@@ -616,7 +795,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
         tw.stage[1] = base + tma_stage_bytes(sizeof(float));
         tw.bar = reinterpret_cast<unsigned long long*>(base + 2 * tma_stage_bytes(sizeof(float)));
         tw.parity = 0;
-        if (lane == 0) {
+        if (lane == 0 && rp.lat_k == 0) {      // the lattice solve reuses this memory instead
             mbar_init(tw.bar + 0, 1);
             mbar_init(tw.bar + 1, 1);
             fence_proxy_async_smem();
@@ -722,7 +901,27 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
             double est_mark = INFINITY;   // monitor value at the last stagnation check
             bool est_nan = false;         // a non-finite update (diverged, or a failed copy)
             int inner = 0;
-            while (true) {
+            while (MIXED && rp.lat_k > 0) {
+                // lattice rounds: lat_k exact red-black sweeps per device barrier
+                const float* dold = dbuf<float>(st, dsel);
+                float* dnew = dbuf<float>(st, dsel ^ 1);
+                const double m = lattice_round(g, dold, dnew, st.r32, (float)omega, rp.lat_k, s_dyn);
+                const BarrierResult be = barrier(true, m);
+                if (!be.ok) { publish(-1); return; }
+                const double est = be.val;
+                dsel ^= 1;
+                dd = (T*)dbuf<float>(st, dsel);
+                const int before = inner;
+                sweeps += rp.lat_k;
+                inner += rp.lat_k;
+                if (!(est == est)) { est_nan = true; break; }
+                if (est <= inner_tgt || sweeps >= rp.max_sweeps) break;
+                if ((inner >> 4) != (before >> 4)) {
+                    if (est > 0.9 * est_mark) break;
+                    est_mark = est;
+                }
+            }
+            while (!(MIXED && rp.lat_k > 0)) {
                 double est = 0.0;
                 for (int c = 0; c < g.ncol; ++c) {
                     double m = 0.0;
@@ -758,7 +957,8 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
                 for (int tt = 0; tt < wc->cnt[c]; ++tt) {
                     const int s = wc->lo[c] + tt;
                     m = nanmax(m, outer_slice<T>(g, wc, warp_desc(g, *wc, c, tt, s), st, dd, dn,
-                                                 MIXED ? st.r32 : nullptr, s, lane, vbuf(st, vF)));
+                                                 MIXED ? st.r32 : nullptr, s, lane, vbuf(st, vF),
+                                                 MIXED && rp.lat_k > 0));
                 }
             br = barrier(true, m);
             if (!br.ok) { publish(-1); return; }
@@ -960,7 +1160,10 @@ __global__ void __launch_bounds__(256) adjoint_grad_kernel(DevGrid g, const doub
 
 // ---------------------------------------------------------------- host-side launch helpers
 
-// Dynamic shared memory of the persistent kernel: the TMA stages of the FP32 sweep.
+// Dynamic shared memory of the persistent kernel: the TMA stages of the FP32 sweep, or
+// (same bytes) the region of the lattice inner solve.
+static_assert(lattice_smem_bytes() <= kWarpsPerBlock * tma_warp_bytes(sizeof(float)),
+              "the lattice region must fit in the TMA stage memory");
 static size_t persistent_smem(bool mixed) {
     return mixed ? (size_t)kWarpsPerBlock * tma_warp_bytes(sizeof(float)) : 0;
 }
