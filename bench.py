@@ -109,13 +109,18 @@ def algorithmic_bytes(st, n, mn, n_src, mixed: bool, nsteps: int, extrap: bool =
     """Bytes the method must move for the work recorded in ``st``.
 
     per node-sweep (FP32 sweep on the correction): 16 + 4 m/n  (delta r/w, r, 1/D, each weight once)
+    per node-sweep (FP32 column-block sweep):      20 + 4 m/n  (the block's two Thomas factors
+                                                                 replace 1/D)
     per node-sweep (FP64 sweep):                   32 + 8 m/n
     per node, outer FP64 pass:   52 + 8 m/n (mixed) or 56 + 8 m/n (FP64)
     per node, step start (RHS, warm start, residual): 56 + 8 m/n (+8 with extrapolation)
                                   + 56 B per PWL source (index + 3 breakpoints)
     per node, step end (read v once for the outputs): 8
     """
-    sweep_b = (16 + 4 * mn) if mixed else (32 + 8 * mn)
+    if mixed:
+        sweep_b = (20 + 4 * mn) if st.get("lattice_sweeps", 0) > 0 else (16 + 4 * mn)
+    else:
+        sweep_b = 32 + 8 * mn
     outer_b = (52 if mixed else 56) + 8 * mn
     start_b = 56 + (8 if extrap else 0) + 8 * mn
     return (st["total_sweeps"] * sweep_b * n + st["total_outer"] * outer_b * n
@@ -325,6 +330,10 @@ def main():
             "max_step_bound_V": max(s["max_step_bound"] for s in stats),
             "err_bound_V": max(s["err_bound"] for s in stats),
             "omega": stats[0]["omega"], "kappa": stats[0]["kappa"], "q": stats[0]["q"],
+            "kacc": stats[0]["kacc"],
+            "inner_solve": (f"lattice column-block red-black SOR, {stats[0]['lattice_sweeps']} sweeps per "
+                            "device barrier" if stats[0]["lattice_sweeps"] > 0 else
+                            "neighbour-list (SELL) red-black SOR"),
             "setup_s": setup_s,
             "roofline": roof,
             "cpu_baseline": cpu,

@@ -106,10 +106,11 @@ typedef struct pg_options {
     double barrier_timeout_s; /* device barrier time limit (0 -> 2 s) */
     int32_t debug_flags;      /* PG_DEBUG_* test hooks; 0 in production */
     int32_t lattice_sweeps;   /* PG_PREC_MIXED on a lattice netlist (lat_nx/ny/nl given, <= 3 layers,
-                                 branches only between lattice neighbours): k > 0 runs the inner solve
-                                 as shared-memory tiles with ghost zones, k exact red-black sweeps per
-                                 device barrier (k <= 7); 0 (default) keeps the neighbour-list sweep,
-                                 which measures faster on GB300 */
+                                 branches only between lattice neighbours): the inner solve becomes
+                                 column-block red-black SOR (each (x, y) column's layers solved exactly)
+                                 on shared-memory tiles with ghost zones, k exact block sweeps per device
+                                 barrier.  k > 0 (<= 7): that k; 0 (default): k = 2 for 2-3 layers,
+                                 off for 1 layer; < 0: off (neighbour-list point SOR) */
 } pg_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -197,6 +198,8 @@ typedef struct pg_run_stats {
     double device_ms;           /* device time of the persistent launch(es), ms */
     double kacc;                /* RC: upper bound of ||1 + (G + G0)^-1 (C/h) 1||_inf, the factor
                                    turning per-step errors into the accumulated error; inf for RLC */
+    int32_t lattice_sweeps;     /* inner solve: 0 = neighbour-list point SOR, k > 0 = lattice
+                                   column-block SOR with k sweeps per device barrier */
 } pg_run_stats;
 
 /*

@@ -60,7 +60,8 @@ class pg_run_stats(C.Structure):
                 ("max_outer_step", C.c_int32), ("total_outer", C.c_int64), ("max_step_bound", C.c_double),
                 ("err_bound", C.c_double), ("failed_step", C.c_int64), ("omega", C.c_double),
                 ("rho_jacobi", C.c_double), ("kappa", C.c_double), ("q", C.c_double),
-                ("step_tol", C.c_double), ("device_ms", C.c_double), ("kacc", C.c_double)]
+                ("step_tol", C.c_double), ("device_ms", C.c_double), ("kacc", C.c_double),
+                ("lattice_sweeps", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

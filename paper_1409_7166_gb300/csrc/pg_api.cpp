@@ -107,11 +107,16 @@ pg_status alloc_device(pg_grid* g) {
     double* cinj = g->alloc<double>(np);
     float* w32 = g->mixed ? g->alloc<float>(P.n_ell) : nullptr;
     float* invD32 = g->mixed ? g->alloc<float>(np) : nullptr;
-    if (g->mixed && P.lattice && g->opt.lattice_sweeps > 0) {
-        float* lw[4];
+    // lattice column-block inner solve: on by default for multi-layer lattices (the via
+    // couplings go into the blocks); single-layer grids measure faster on the SELL sweep
+    const int lat_k = g->opt.lattice_sweeps > 0 ? g->opt.lattice_sweeps
+                    : (g->opt.lattice_sweeps == 0 && P.lat_nl >= 2 ? 2 : 0);
+    if (g->mixed && P.lattice && lat_k > 0) {
+        g->lat_k = lat_k;
+        float* lw[5];
         for (auto& q : lw) if (!(q = g->alloc<float>(P.n))) return PG_ERR_OOM;
         d.lat_nx = P.lat_nx; d.lat_ny = P.lat_ny; d.lat_nl = P.lat_nl;
-        d.lwE = lw[0]; d.lwN = lw[1]; d.lwU = lw[2]; d.liD = lw[3];
+        d.lwE = lw[0]; d.lwN = lw[1]; d.lwU = lw[2]; d.lm = lw[3]; d.lip = lw[4];
     }
     if (!colour_slice || !slice_off || !slice_w || !slice_doff || !dia_off || !ell_col || !orig || !ld_ptr ||
         !ld_idx || !pwl_ptr || !pwl_t || !pwl_v || !ind_a || !ind_b || !ind_hl || !ind_ptr || !ind_idx || !vdd ||
@@ -211,18 +216,35 @@ pg_status assemble_h(pg_grid* g, double h) {
         return s;
     if (g->dg.lwE) {
         // lattice form of the FP32 inner solve: each branch weight once, caller order
-        std::vector<float> e(P.n, 0.f), nn(P.n, 0.f), u(P.n, 0.f), id(P.n, 0.f);
+        std::vector<float> e(P.n, 0.f), nn(P.n, 0.f), u(P.n, 0.f), mm(P.n, 0.f), ip(P.n, 0.f);
+        std::vector<double> u64(P.n, 0.0);
         for (int o = 0; o < P.n; ++o) {
             for (int64_t a = P.adj_ptr[o]; a < P.adj_ptr[o + 1]; ++a) {
-                const float w = (float)(P.adj_g[a] + h * P.adj_il[a]);
-                if (P.adj_dir[a] == 0) e[o] = w;
-                else if (P.adj_dir[a] == 1) nn[o] = w;
-                else if (P.adj_dir[a] == 2) u[o] = w;
+                const double w = P.adj_g[a] + h * P.adj_il[a];
+                if (P.adj_dir[a] == 0) e[o] = (float)w;
+                else if (P.adj_dir[a] == 1) nn[o] = (float)w;
+                else if (P.adj_dir[a] == 2) { u[o] = (float)w; u64[o] = w; }
             }
-            id[o] = (float)iD[P.perm[o]];
+        }
+        // Thomas factors of each column's block (diagonal D_l, off-diagonal -u_l between l and l+1)
+        const int64_t plane = (int64_t)P.lat_nx * P.lat_ny;
+        for (int64_t c = 0; c < plane; ++c) {
+            double dp_prev = 0.0;
+            for (int l = 0; l < P.lat_nl; ++l) {
+                const int64_t o = c + l * plane;
+                double dp = D[P.perm[o]];
+                if (l > 0) {
+                    const double m = u64[o - plane] / dp_prev;
+                    dp -= m * u64[o - plane];
+                    mm[o] = (float)m;
+                }
+                ip[o] = (float)(1.0 / dp);
+                dp_prev = dp;
+            }
         }
         if ((s = upload(g, const_cast<float*>(g->dg.lwE), e)) || (s = upload(g, const_cast<float*>(g->dg.lwN), nn)) ||
-            (s = upload(g, const_cast<float*>(g->dg.lwU), u)) || (s = upload(g, const_cast<float*>(g->dg.liD), id)))
+            (s = upload(g, const_cast<float*>(g->dg.lwU), u)) || (s = upload(g, const_cast<float*>(g->dg.lm), mm)) ||
+            (s = upload(g, const_cast<float*>(g->dg.lip), ip)))
             return s;
     }
     if (g->mixed) {
@@ -252,7 +274,7 @@ RunParams pg::base_params(const pg_grid* g) {
     rp.debug_flags = g->opt.debug_flags;
     rp.cur = g->vL; rp.prev = g->vP;
     rp.warm_extrap = g->opt.warm_start;
-    rp.lat_k = g->dg.lwE ? g->opt.lattice_sweeps : 0;
+    rp.lat_k = g->dg.lwE ? g->lat_k : 0;
     return rp;
 }
 
@@ -393,6 +415,35 @@ pg_status accumulation_bound(pg_grid* g, double h, double* kacc) {
     return PG_OK;
 }
 
+// Spectral radius of the column-block Jacobi operator of a lattice grid (the inner solve's
+// relaxation), by power iteration on (I + B^-1 W)/2; Rayleigh quotient, a lower bound.
+pg_status estimate_rho_lattice(pg_grid* g, double* rho) {
+    const int n = g->P.n, iters = 300;
+    DeviceScratch sc;
+    double* x = sc.get<double>(n);
+    double* y = sc.get<double>(n);
+    double* acc = sc.get<double>(2 * iters);
+    unsigned long long* mx = sc.get<unsigned long long>(iters);
+    if (!x || !y || !acc || !mx) return PG_ERR_OOM;
+    std::vector<double> ones(n, 1.0);
+    pg_status s;
+    if ((s = upload(g, x, ones))) return s;
+    CK(cudaMemsetAsync(acc, 0, 2 * iters * sizeof(double), g->stream));
+    CK(cudaMemsetAsync(mx, 0, iters * sizeof(unsigned long long), g->stream));
+    const int64_t cols = (int64_t)g->P.lat_nx * g->P.lat_ny;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(g->n_sm * 4, (cols + 255) / 256));
+    for (int k = 0; k < iters; ++k) {
+        CK(launch_lattice_power(g->dg, x, y, k ? mx + (k - 1) : nullptr, acc + 2 * k, mx + k, blocks, g->stream));
+        std::swap(x, y);
+    }
+    std::vector<double> a(2 * iters);
+    CK(cudaMemcpyAsync(a.data(), acc, a.size() * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    const double num = a[2 * (iters - 1)], den = a[2 * (iters - 1) + 1];
+    *rho = den > 0.0 ? std::min(std::max(num / den, 0.0), 1.0) : 0.0;
+    return PG_OK;
+}
+
 // Per-h setup: coefficients, omega, and the stopping-rule constants kappa, q.
 pg_status prepare_h(pg_grid* g, double h) {
     if (g->h == h) return PG_OK;
@@ -404,9 +455,11 @@ pg_status prepare_h(pg_grid* g, double h) {
         g->omega = g->opt.omega;
         g->rho = 0.0;
     } else {
-        if ((s = estimate_rho(g, &g->rho))) return s;
+        if ((s = g->dg.lwE ? estimate_rho_lattice(g, &g->rho) : estimate_rho(g, &g->rho))) return s;
         const double r = std::min(g->rho, 1.0 - 1e-12);
-        g->omega = g->P.ncol == 2 ? 2.0 / (1.0 + std::sqrt(1.0 - r * r)) : 1.0;
+        // red-black (2-cyclic, consistently ordered; the column blocks of the lattice solve
+        // are too): Young's optimum; other colourings use Gauss-Seidel
+        g->omega = (g->P.ncol == 2 || g->dg.lwE) ? 2.0 / (1.0 + std::sqrt(1.0 - r * r)) : 1.0;
     }
     // kappa >= ||M^-1 D||_inf: solve M x = D 1 to max|r|/D <= 1e-3, then bound the remainder.
     g->kappa = 1.0;
@@ -567,6 +620,7 @@ pg_status fill_stats(pg_grid* g, const double* st, float ms, pg_run_stats* out) 
     out->step_tol = g->step_tol;
     out->device_ms = ms;
     out->kacc = g->kacc;
+    out->lattice_sweeps = g->lat_k;
     return PG_OK;
 }
 

@@ -73,6 +73,7 @@ struct pg_grid {
     int n_sm = 0;
     int blocks = 1, threads = 256;
     bool mixed = false;
+    int lat_k = 0;                 // lattice inner solve: block sweeps per device barrier (0 = off)
     std::vector<void*> allocs;
     DevGrid dg{};
     DevState ds{};

@@ -109,7 +109,8 @@ struct DevGrid {
     const float* lwE;        // weight to (x+1, y, l); 0 on the last column
     const float* lwN;        // weight to (x, y+1, l)
     const float* lwU;        // weight to (x, y, l+1)
-    const float* liD;        // 1 / D
+    const float* lm;         // column block (via couplings): Thomas multiplier u_{l-1} / d'_{l-1} (0 for l = 0)
+    const float* lip;        // column block: inverse Thomas pivot 1 / d'_l
 };
 
 enum Mode : int32_t { kModeTransient = 0, kModeSolve = 1 };
@@ -187,6 +188,8 @@ cudaError_t launch_persistent(bool mixed, const DevGrid& g, const DevState& st, 
 cudaError_t persistent_occupancy(bool mixed, int threads, int* blocks_per_sm);
 cudaError_t launch_power_step(const DevGrid& g, const double* x, double* y, const unsigned long long* xmax_prev,
                               double* acc, unsigned long long* ymax, int blocks, cudaStream_t stream);
+cudaError_t launch_lattice_power(const DevGrid& g, const double* x, double* y, const unsigned long long* xmax_prev,
+                                 double* acc, unsigned long long* ymax, int blocks, cudaStream_t stream);
 cudaError_t launch_permute_in(const int32_t* orig, const double* src, double fill, double* dst, int n_pad,
                               int n_sm, cudaStream_t stream);
 cudaError_t launch_adjoint_rhs(const DevGrid& g, const double* v, const double* lam_next, double* rhs, double vref,

@@ -569,24 +569,35 @@ __device__ double sweep_colour_tma(const DevGrid& g, const WarpCache* wc, TmaWar
     return mon;
 }
 
-// ---- lattice inner solve (FP32, ghost zones)
+// ---- lattice inner solve (FP32, ghost zones, column blocks)
 //
 // For a lattice grid (nodes (x, y, l), branches only between lattice
-// neighbours) the inner relaxation runs on 32 x 32-column regions of all
-// layers held in shared memory.  A region is its tile of (32 - 2H)^2 columns
-// plus a ghost zone of H = 2k columns on each side; k exact red-black SOR
-// sweeps (2k half-sweeps, colour = parity of x + y + l) are applied to the
-// whole region, the outermost ring never being updated.  After half-sweep j
-// every node at distance >= j from the region's edge holds the exact
-// red-black value, so after 2k half-sweeps the tile interior equals k global
-// red-black sweeps (Eq. 16-17).  Tiles read the previous round's corrections
-// and write the next buffer, so a round needs one device barrier for k sweeps,
-// and every branch weight is stored once (E, N, U per node).
+// neighbours) the inner relaxation is block red-black SOR whose blocks are the
+// columns (x, y, all l): a column is coloured by the parity of x + y, and its
+// update solves the column's tridiagonal block exactly (Thomas factors
+// precomputed per h) against the in-plane neighbours of the other colour.
+// Gauss-Seidel / SOR over any block partition of an SPD matrix converges for
+// 0 < omega < 2 (Theorem 1's argument, with the Ostrowski-Reich theorem for
+// blocks), and taking the stiff via couplings into the blocks shrinks the
+// spectral radius that the in-plane sweep has to overcome.  With one layer a
+// block is a node and this is the point red-black SOR of Eq. 16-17.
+//
+// The relaxation runs on 32 x 32-column regions of all layers held in shared
+// memory: the region is its tile of (32 - 2H)^2 columns plus a ghost zone of
+// H = 2k columns, k exact sweeps (2k half-sweeps) are applied to the whole
+// region with its outermost ring fixed, and after half-sweep j every column at
+// distance >= j from the edge holds the exact value, so the tile interior
+// equals k global block sweeps.  Tiles read the previous round's corrections
+// and write the next buffer: one device barrier per k sweeps, every branch
+// weight stored once (E, N, U per node).
 constexpr int kLatR = 32;                          // region side (columns)
 constexpr int kLatMaxL = 3;                        // layers held per region
 constexpr int kLatPlane = kLatR * kLatR;
+constexpr int kLatArrays = 7;                      // delta, r, wE, wN, wU, Thomas m, 1/pivot
 
-__host__ __device__ constexpr int lattice_smem_bytes() { return 6 * kLatMaxL * kLatPlane * (int)sizeof(float); }
+__host__ __device__ constexpr int lattice_smem_bytes() {
+    return kLatArrays * kLatMaxL * kLatPlane * (int)sizeof(float);
+}
 
 // Asynchronous global -> shared copies (no registers held while in flight);
 // src_bytes = 0 fills the destination with zeros.
@@ -602,100 +613,111 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
-// One round over all tiles of the lattice; returns the max unrelaxed update of
-// the last sweep over tile interiors.  NL (the layer count) is a template
-// parameter so the layer loop unrolls and the vertical neighbours need no
-// run-time tests.
+// One round over all tiles; returns the max unrelaxed column update of the last
+// sweep over tile interiors.  NL (layers) is a template parameter: the column
+// solve unrolls completely.
 template <int NL>
 __device__ double lattice_round_nl(const DevGrid& g, const float* __restrict__ dold, float* __restrict__ dnew,
                                    const float* __restrict__ r, float omega, int k, unsigned char* smem) {
     const int nx = g.lat_nx, ny = g.lat_ny;
     const int H = 2 * k, T = kLatR - 2 * H;
     const int tiles_x = (nx + T - 1) / T, tiles_y = (ny + T - 1) / T, ntiles = tiles_x * tiles_y;
+    constexpr int A = kLatMaxL * kLatPlane;           // floats per array
     float* sd = reinterpret_cast<float*>(smem);
-    float* sr = sd + kLatMaxL * kLatPlane;
-    float* si = sr + kLatMaxL * kLatPlane;
-    float* se = si + kLatMaxL * kLatPlane;
-    float* sn = se + kLatMaxL * kLatPlane;
-    float* su = sn + kLatMaxL * kLatPlane;
-    const int rx = threadIdx.x & (kLatR - 1);
-    const int ry0 = threadIdx.x >> 5;                 // rows ry0, ry0 + 8, ry0 + 16, ry0 + 24
+    float* sr = sd + A;
+    float* se = sd + 2 * A;
+    float* sn = sd + 3 * A;
+    float* su = sd + 4 * A;
+    float* sm = sd + 5 * A;
+    float* sp = sd + 6 * A;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pair = lane & 15;                        // columns 2 pair, 2 pair + 1
+    const int rsub = lane >> 4;                        // half-warps take adjacent rows (no bank conflicts)
     const long long plane = (long long)nx * ny;
-    // 16-byte copies need every region row to start on a 4-float boundary
-    const bool vec16 = (nx & 3) == 0 && (H & 3) == 0 && (T & 3) == 0;
+    const bool vec16 = (nx & 3) == 0 && (H & 3) == 0 && (T & 3) == 0;   // 16-byte aligned region rows
     float mon = 0.f;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int x0 = (tile % tiles_x) * T - H, y0 = (tile / tiles_x) * T - H;
-        const int x = x0 + rx;
         auto src_of = [&](int arr) -> const float* {   // by value: no local array
-            return arr == 0 ? dold : arr == 1 ? r : arr == 2 ? g.liD : arr == 3 ? g.lwE : arr == 4 ? g.lwN : g.lwU;
+            return arr == 0 ? dold : arr == 1 ? r : arr == 2 ? g.lwE : arr == 3 ? g.lwN : arr == 4 ? g.lwU
+                 : arr == 5 ? g.lm : g.lip;
         };
         if (vec16) {
-            // one 16-byte chunk per thread per (array, layer) plane: 32 rows x 8 chunks = 256
-            const int ry = threadIdx.x >> 3, cx = threadIdx.x & 7;
+            const int ry = threadIdx.x >> 3, cx = threadIdx.x & 7;   // one 16-byte chunk per plane
             const int xx = x0 + 4 * cx, yy = y0 + ry;
-            const bool in = yy >= 0 && yy < ny && xx >= 0 && xx < nx;   // nx, x0 multiples of 4
+            const bool in = yy >= 0 && yy < ny && xx >= 0 && xx < nx;
             const long long off = in ? (long long)yy * nx + xx : 0;
             const int sa = ry * kLatR + 4 * cx;
 #pragma unroll
-            for (int arr = 0; arr < 6; ++arr)
+            for (int arr = 0; arr < kLatArrays; ++arr)
 #pragma unroll
                 for (int l = 0; l < NL; ++l)
-                    cp_async16(sd + arr * kLatMaxL * kLatPlane + l * kLatPlane + sa,
-                               src_of(arr) + (in ? l * plane + off : 0), in ? 16u : 0u);
+                    cp_async16(sd + arr * A + l * kLatPlane + sa, src_of(arr) + (in ? l * plane + off : 0),
+                               in ? 16u : 0u);
         } else {
+            const int rx = threadIdx.x & 31;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int ry = ry0 + 8 * q, yy = y0 + ry;
-                const bool in = yy >= 0 && yy < ny && x >= 0 && x < nx;
-                const long long off = in ? (long long)yy * nx + x : 0;
+                const int ry = (threadIdx.x >> 5) + 8 * q, yy = y0 + ry, xx = x0 + rx;
+                const bool in = yy >= 0 && yy < ny && xx >= 0 && xx < nx;
+                const long long off = in ? (long long)yy * nx + xx : 0;
                 const int sa = ry * kLatR + rx;
 #pragma unroll
-                for (int arr = 0; arr < 6; ++arr)
+                for (int arr = 0; arr < kLatArrays; ++arr)
 #pragma unroll
                     for (int l = 0; l < NL; ++l)
-                        cp_async4(sd + arr * kLatMaxL * kLatPlane + l * kLatPlane + sa,
-                                  src_of(arr) + (in ? l * plane + off : 0), in ? 4u : 0u);
+                        cp_async4(sd + arr * A + l * kLatPlane + sa, src_of(arr) + (in ? l * plane + off : 0),
+                                  in ? 4u : 0u);
             }
         }
         cp_async_wait_all();
         __syncthreads();
-        // per-row predicates (identical for every half-sweep of the tile)
-        bool act[4], inner[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int ry = ry0 + 8 * q, y = y0 + ry;
-            const int edge = min(min(rx, ry), min(kLatR - 1 - rx, kLatR - 1 - ry));
-            act[q] = edge > 0 && x >= 0 && x < nx && y >= 0 && y < ny;
-            inner[q] = act[q] && edge >= H;
-        }
         for (int hs = 0; hs < 2 * k; ++hs) {
             const bool last = hs >= 2 * k - 2;
-            const int par = (x + y0 + ry0 + hs) & 1;      // rows ry0 + 8q share the parity of y
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int j = 0; j < 2; ++j) {
+                const int ry = 2 * (warp + 8 * j) + rsub, y = y0 + ry;
+                const int rx = 2 * pair + ((hs + x0 + y) & 1);      // the column of this colour in the pair
+                const int x = x0 + rx;
+                const int edge = min(min(rx, ry), min(kLatR - 1 - rx, kLatR - 1 - ry));
+                if (edge == 0 || x < 0 || x >= nx || y < 0 || y >= ny) continue;
+                const int a0 = ry * kLatR + rx;
+                float f[NL], xs[NL];
 #pragma unroll
                 for (int l = 0; l < NL; ++l) {
-                    if (((l & 1) != par) || !act[q]) continue;
-                    const int a = l * kLatPlane + (ry0 + 8 * q) * kLatR + rx;
-                    float sig = se[a] * sd[a + 1] + se[a - 1] * sd[a - 1] + sn[a] * sd[a + kLatR] +
-                                sn[a - kLatR] * sd[a - kLatR];
-                    if (l + 1 < NL) sig += su[a] * sd[a + kLatPlane];
-                    if (l > 0) sig += su[a - kLatPlane] * sd[a - kLatPlane];
+                    const int a = a0 + l * kLatPlane;
+                    f[l] = sr[a] + se[a] * sd[a + 1] + se[a - 1] * sd[a - 1] + sn[a] * sd[a + kLatR] +
+                           sn[a - kLatR] * sd[a - kLatR];
+                }
+#pragma unroll
+                for (int l = 1; l < NL; ++l) f[l] = fmaf(sm[a0 + l * kLatPlane], f[l - 1], f[l]);
+                xs[NL - 1] = f[NL - 1] * sp[a0 + (NL - 1) * kLatPlane];
+#pragma unroll
+                for (int l = NL - 2; l >= 0; --l)
+                    xs[l] = fmaf(su[a0 + l * kLatPlane], xs[l + 1], f[l]) * sp[a0 + l * kLatPlane];
+                const bool interior = edge >= H;
+#pragma unroll
+                for (int l = 0; l < NL; ++l) {
+                    const int a = a0 + l * kLatPlane;
                     const float dv = sd[a];
-                    const float upd = (sr[a] + sig) * si[a] - dv;
+                    const float upd = xs[l] - dv;
                     sd[a] = fmaf(omega, upd, dv);
-                    if (last && inner[q]) mon = nanmaxf(mon, fabsf(upd));
+                    if (last && interior) mon = nanmaxf(mon, fabsf(upd));
                 }
             }
             __syncthreads();
         }
+        {
+            const int rx = threadIdx.x & 31;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (!inner[q]) continue;
-            const long long b = (long long)(y0 + ry0 + 8 * q) * nx + x;
+            for (int q = 0; q < 4; ++q) {
+                const int ry = (threadIdx.x >> 5) + 8 * q, y = y0 + ry, x = x0 + rx;
+                const int edge = min(min(rx, ry), min(kLatR - 1 - rx, kLatR - 1 - ry));
+                if (edge < H || x < 0 || x >= nx || y < 0 || y >= ny) continue;
+                const long long b = (long long)y * nx + x;
 #pragma unroll
-            for (int l = 0; l < NL; ++l) dnew[b + l * plane] = sd[l * kLatPlane + (ry0 + 8 * q) * kLatR + rx];
+                for (int l = 0; l < NL; ++l) dnew[b + l * plane] = sd[l * kLatPlane + ry * kLatR + rx];
+            }
         }
         __syncthreads();   // the next tile overwrites the region
     }
@@ -1086,6 +1108,69 @@ __global__ void __launch_bounds__(256) power_step_kernel(DevGrid g, const double
     }
 }
 
+// Power iteration for the column-block Jacobi operator B^-1 W (lattice form): one
+// thread per column, y = (x + B^-1 W x) / 2 with x scaled by 1 / xmax_prev; accumulates
+// x.(W x) and x.(B x), whose ratio is a Rayleigh quotient of W v = lambda B v.
+template <int NL>
+__global__ void __launch_bounds__(256) lattice_power_kernel(DevGrid g, const double* x, double* y,
+                                                           const unsigned long long* xmax_prev, double* acc,
+                                                           unsigned long long* ymax) {
+    const int nx = g.lat_nx, ny = g.lat_ny;
+    const long long plane = (long long)nx * ny;
+    const double sc = xmax_prev ? 1.0 / __longlong_as_double((long long)*xmax_prev) : 1.0;
+    double num = 0.0, den = 0.0, mx = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < plane;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int cx = (int)(c % nx), cy = (int)(c / nx);
+        double xv[NL], wx[NL], f[NL], dl[NL], u[NL];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            const long long o = c + l * plane;
+            xv[l] = x[o] * sc;
+            double s = 0.0;
+            if (cx + 1 < nx) s += (double)__ldg(g.lwE + o) * x[o + 1] * sc;
+            if (cx > 0) s += (double)__ldg(g.lwE + o - 1) * x[o - 1] * sc;
+            if (cy + 1 < ny) s += (double)__ldg(g.lwN + o) * x[o + nx] * sc;
+            if (cy > 0) s += (double)__ldg(g.lwN + o - nx) * x[o - nx] * sc;
+            wx[l] = s;
+            u[l] = (double)__ldg(g.lwU + o);
+            // block diagonal from the Thomas factors: d_l = d'_l + m_l u_{l-1}
+            dl[l] = 1.0 / (double)__ldg(g.lip + o) + (l > 0 ? (double)__ldg(g.lm + o) * u[l - 1] : 0.0);
+        }
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            double bx = dl[l] * xv[l];
+            if (l > 0) bx -= u[l - 1] * xv[l - 1];
+            if (l + 1 < NL) bx -= u[l] * xv[l + 1];
+            num += xv[l] * wx[l];
+            den += xv[l] * bx;
+            f[l] = wx[l];
+        }
+#pragma unroll
+        for (int l = 1; l < NL; ++l) f[l] += (double)__ldg(g.lm + c + l * plane) * f[l - 1];
+        double z[NL];
+        z[NL - 1] = f[NL - 1] * (double)__ldg(g.lip + c + (NL - 1) * plane);
+#pragma unroll
+        for (int l = NL - 2; l >= 0; --l) z[l] = (f[l] + u[l] * z[l + 1]) * (double)__ldg(g.lip + c + l * plane);
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            const double yv = 0.5 * (xv[l] + z[l]);
+            y[c + l * plane] = yv;
+            mx = fmax(mx, yv);
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        num += __shfl_xor_sync(kFull, num, o);
+        den += __shfl_xor_sync(kFull, den, o);
+        mx = fmax(mx, __shfl_xor_sync(kFull, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(acc + 0, num);
+        atomicAdd(acc + 1, den);
+        atomicMax(ymax, (unsigned long long)__double_as_longlong(mx));
+    }
+}
+
 // ---------------------------------------------------------------- state set-up
 
 // dst[i] = src[orig[i]] (caller numbering -> permuted), or `fill` when src is null; padding gets 0.
@@ -1201,6 +1286,16 @@ cudaError_t launch_adjoint_grad(const DevGrid& g, const double* lam, const doubl
                                 double* acc_slot, double* acc_lv, double* acc_l, double* acc_dv, int blocks,
                                 cudaStream_t stream) {
     adjoint_grad_kernel<<<blocks, 256, 0, stream>>>(g, lam, v, v_prev, acc_slot, acc_lv, acc_l, acc_dv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lattice_power(const DevGrid& g, const double* x, double* y, const unsigned long long* xmax_prev,
+                                 double* acc, unsigned long long* ymax, int blocks, cudaStream_t stream) {
+    switch (g.lat_nl) {
+        case 1: lattice_power_kernel<1><<<blocks, 256, 0, stream>>>(g, x, y, xmax_prev, acc, ymax); break;
+        case 2: lattice_power_kernel<2><<<blocks, 256, 0, stream>>>(g, x, y, xmax_prev, acc, ymax); break;
+        default: lattice_power_kernel<3><<<blocks, 256, 0, stream>>>(g, x, y, xmax_prev, acc, ymax); break;
+    }
     return cudaGetLastError();
 }
 

@@ -222,3 +222,16 @@ def test_not_converged_and_timeout_are_reported(B):
         assert B.STATUS[rc] == "PG_ERR_TIMEOUT"
     # the context is still usable afterwards
     check_against_oracle(B, pgsynth.config0(nx=12, ny=12), h, 5, 0)
+
+
+@pytest.mark.parametrize("shape,k", [((97, 61, 3), 2), ((96, 64, 3), 2), ((96, 64, 3), 1), ((64, 48, 1), 2),
+                                     ((40, 36, 2), 3)])
+def test_lattice_block_inner_solve(B, shape, k):
+    """The shared-memory column-block red-black inner solve (lattice grids, mixed
+    precision): odd sides use 4-byte region copies, multiples of 4 the 16-byte path;
+    1, 2 and 3 layers; k sweeps per device barrier."""
+    nx, ny, nl = shape
+    net = pgsynth.config1(nx=nx, ny=ny, nl=nl) if nl > 1 else pgsynth.config0(nx=nx, ny=ny)
+    with B.Grid(net, precision=1, lattice_sweeps=k) as g:
+        assert g.info["n_nodes"] == nx * ny * nl
+    check_against_oracle(B, net, net.meta["h"], 40, 1, lattice_sweeps=k)
