@@ -65,7 +65,12 @@ typedef enum pg_status {
  * times must be non-decreasing; the value is held constant before the first
  * and after the last breakpoint and is linear in between.
  * lat_nx/lat_ny/lat_nl: optional lattice shape (node (x,y,l) = (l*ny+y)*nx+x)
- * or 0; informational only.
+ * or 0.  n_lat / lat_desc: optional list of n_lat lattices (independent grids
+ * side by side), lat_desc[4k .. 4k+3] = (first node id, nx, ny, nl), node
+ * (x, y, l) of lattice k having id first + (l*ny + y)*nx + x.  When the lattices
+ * cover every node and every branch joins lattice neighbours, the mixed-precision
+ * inner solve can use the lattice form (see pg_options.lattice_sweeps); results
+ * do not depend on it.
  * pg_create_grid copies everything; the caller may free the arrays after it
  * returns.  All pointers are host pointers.
  */
@@ -80,6 +85,8 @@ typedef struct pg_netlist {
     const int64_t* i_ptr;              /* [n_i + 1] */
     const double* i_t; const double* i_v;
     int32_t lat_nx, lat_ny, lat_nl;
+    int32_t n_lat;
+    const int32_t* lat_desc;           /* [4 * n_lat] or NULL */
 } pg_netlist;
 
 typedef enum pg_precision {

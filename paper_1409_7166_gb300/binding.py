@@ -34,7 +34,8 @@ class pg_netlist(C.Structure):
                 ("n_l", C.c_int64), ("l_a", _i32p), ("l_b", _i32p), ("l_val", _f64p),
                 ("n_i", C.c_int64), ("i_a", _i32p), ("i_b", _i32p), ("i_ptr", _i64p),
                 ("i_t", _f64p), ("i_v", _f64p),
-                ("lat_nx", C.c_int32), ("lat_ny", C.c_int32), ("lat_nl", C.c_int32)]
+                ("lat_nx", C.c_int32), ("lat_ny", C.c_int32), ("lat_nl", C.c_int32),
+                ("n_lat", C.c_int32), ("lat_desc", _i32p)]
 
 
 class pg_options(C.Structure):
@@ -170,6 +171,10 @@ def pg_create_grid(net, opt: Optional[pg_options] = None):
     nl.i_ptr = arr(net.i_ptr, np.int64); nl.i_t = arr(net.i_t, np.float64); nl.i_v = arr(net.i_v, np.float64)
     lat = getattr(net, "lattice", None) or (0, 0, 0)
     nl.lat_nx, nl.lat_ny, nl.lat_nl = (int(x) for x in lat)
+    lats = getattr(net, "lattices", None)
+    if lats:
+        nl.n_lat = len(lats)
+        nl.lat_desc = arr(np.asarray(lats, dtype=np.int32).reshape(-1), np.int32)
     h = C.c_void_p()
     _check(lib().pg_create_grid(C.byref(nl), C.byref(opt) if opt is not None else None, C.byref(h)),
            "pg_create_grid")

@@ -110,13 +110,31 @@ pg_status alloc_device(pg_grid* g) {
     // lattice column-block inner solve: on by default for multi-layer lattices (the via
     // couplings go into the blocks); single-layer grids measure faster on the SELL sweep
     const int lat_k = g->opt.lattice_sweeps > 0 ? g->opt.lattice_sweeps
-                    : (g->opt.lattice_sweeps == 0 && P.lat_nl >= 2 ? 2 : 0);
+                    : (g->opt.lattice_sweeps == 0 && P.lat_maxnl >= 2 ? 2 : 0);
+    std::vector<int32_t> lat_tile0, lat_info;
+    std::vector<int64_t> lat_col0;
     if (g->mixed && P.lattice && lat_k > 0) {
         g->lat_k = lat_k;
         float* lw[5];
         for (auto& q : lw) if (!(q = g->alloc<float>(P.n))) return PG_ERR_OOM;
-        d.lat_nx = P.lat_nx; d.lat_ny = P.lat_ny; d.lat_nl = P.lat_nl;
         d.lwE = lw[0]; d.lwN = lw[1]; d.lwU = lw[2]; d.lm = lw[3]; d.lip = lw[4];
+        // tiles of (32 - 4k)^2 interior columns per lattice, and columns per lattice
+        const int nlat = (int)P.lats.size() / 4, T = 32 - 4 * lat_k;
+        lat_info = P.lats;
+        lat_tile0.assign(nlat + 1, 0);
+        lat_col0.assign(nlat + 1, 0);
+        for (int L = 0; L < nlat; ++L) {
+            const int nx = P.lats[4 * L + 1], ny = P.lats[4 * L + 2];
+            lat_tile0[L + 1] = lat_tile0[L] + ((nx + T - 1) / T) * ((ny + T - 1) / T);
+            lat_col0[L + 1] = lat_col0[L] + (int64_t)nx * ny;
+        }
+        int32_t* li = g->alloc<int32_t>(lat_info.size());
+        int32_t* lt = g->alloc<int32_t>(lat_tile0.size());
+        int64_t* lc = g->alloc<int64_t>(lat_col0.size());
+        int32_t* nlatv = g->alloc<int32_t>(np);
+        if (!li || !lt || !lc || !nlatv) return PG_ERR_OOM;
+        d.n_lats = nlat; d.lat_info = li; d.lat_tile0 = lt; d.lat_tiles = lat_tile0[nlat];
+        d.lat_col0 = lc; d.lat_cols = lat_col0[nlat]; d.node_lat = nlatv;
     }
     if (!colour_slice || !slice_off || !slice_w || !slice_doff || !dia_off || !ell_col || !orig || !ld_ptr ||
         !ld_idx || !pwl_ptr || !pwl_t || !pwl_v || !ind_a || !ind_b || !ind_hl || !ind_ptr || !ind_idx || !vdd ||
@@ -128,6 +146,12 @@ pg_status alloc_device(pg_grid* g) {
     d.ind_hl = ind_hl; d.ind_ptr = ind_ptr; d.ind_idx = ind_idx; d.vdd = vdd;
     d.w64 = w64; d.D64 = D64; d.invD64 = invD64; d.ch = ch; d.cinj = cinj; d.w32 = w32; d.invD32 = invD32;
     pg_status s;
+    if (d.lwE &&
+        ((s = upload(g, const_cast<int32_t*>(d.lat_info), lat_info)) ||
+         (s = upload(g, const_cast<int32_t*>(d.lat_tile0), lat_tile0)) ||
+         (s = upload(g, const_cast<int64_t*>(d.lat_col0), lat_col0)) ||
+         (s = upload(g, const_cast<int32_t*>(d.node_lat), P.node_lat))))
+        return s;
     if ((s = upload(g, colour_slice, cs)) || (s = upload(g, slice_off, P.slice_off)) ||
         (s = upload(g, slice_w, P.slice_w)) || (s = upload(g, slice_doff, P.slice_doff)) ||
         (s = upload(g, dia_off, P.dia_off)) || (s = upload(g, ell_col, P.ell_col)) || (s = upload(g, orig, P.orig)) ||
@@ -182,6 +206,7 @@ pg_status alloc_device(pg_grid* g) {
     c.blk_arg = g->alloc<int32_t>(2 * g->blocks);
     c.stats = g->alloc<double>(kStatCount);
     if (!c.bar_count || !c.bar_gen || !c.err || !c.red || !c.blk_min || !c.blk_arg || !c.stats) return PG_ERR_OOM;
+    if (d.lwE && !(c.lat_R = g->alloc<unsigned long long>(2 * (size_t)d.n_lats))) return PG_ERR_OOM;
     CK(cudaMemsetAsync(c.bar_gen, 0, sizeof(unsigned), g->stream));
     CK(cudaEventCreate(&g->ev0));
     CK(cudaEventCreate(&g->ev1));
@@ -227,11 +252,12 @@ pg_status assemble_h(pg_grid* g, double h) {
             }
         }
         // Thomas factors of each column's block (diagonal D_l, off-diagonal -u_l between l and l+1)
-        const int64_t plane = (int64_t)P.lat_nx * P.lat_ny;
-        for (int64_t c = 0; c < plane; ++c) {
+        for (size_t L = 0; L < P.lats.size() / 4; ++L) {
+          const int64_t off = P.lats[4 * L], plane = (int64_t)P.lats[4 * L + 1] * P.lats[4 * L + 2];
+          for (int64_t c = 0; c < plane; ++c) {
             double dp_prev = 0.0;
-            for (int l = 0; l < P.lat_nl; ++l) {
-                const int64_t o = c + l * plane;
+            for (int l = 0; l < P.lats[4 * L + 3]; ++l) {
+                const int64_t o = off + c + l * plane;
                 double dp = D[P.perm[o]];
                 if (l > 0) {
                     const double m = u64[o - plane] / dp_prev;
@@ -241,6 +267,7 @@ pg_status assemble_h(pg_grid* g, double h) {
                 ip[o] = (float)(1.0 / dp);
                 dp_prev = dp;
             }
+          }
         }
         if ((s = upload(g, const_cast<float*>(g->dg.lwE), e)) || (s = upload(g, const_cast<float*>(g->dg.lwN), nn)) ||
             (s = upload(g, const_cast<float*>(g->dg.lwU), u)) || (s = upload(g, const_cast<float*>(g->dg.lm), mm)) ||
@@ -286,6 +313,8 @@ pg_status run(pg_grid* g, const RunParams& rp, double* stats, float* ms) {
     CK(cudaMemsetAsync(g->dc.bar_gen, 0, sizeof(unsigned), g->stream));
     CK(cudaMemsetAsync(g->dc.err, 0, sizeof(int32_t), g->stream));
     CK(cudaMemsetAsync(g->dc.red, 0, kRedSlots * sizeof(unsigned long long), g->stream));
+    if (g->dc.lat_R)
+        CK(cudaMemsetAsync(g->dc.lat_R, 0, 2 * (size_t)g->dg.n_lats * sizeof(unsigned long long), g->stream));
     CK(cudaEventRecord(g->ev0, g->stream));
     CK(launch_persistent(g->mixed, g->dg, g->ds, g->dc, rp, g->blocks, g->threads, g->stream));
     CK(cudaEventRecord(g->ev1, g->stream));
@@ -377,6 +406,8 @@ pg_status ensure_dc_grid(pg_grid* g) {
     o.omega = 0.0;
     o.step_tol = 0.5 * g->opt.tol;
     d.lat_nx = g->nc.nx; d.lat_ny = g->nc.ny; d.lat_nl = g->nc.nl;
+    d.n_lat = (int32_t)(g->nc.lat_desc.size() / 4);
+    d.lat_desc = g->nc.lat_desc.empty() ? nullptr : g->nc.lat_desc.data();
     std::unique_ptr<pg_grid> sub;
     pg_status s = create_impl(&d, &o, sub);
     if (s == PG_ERR_FLOATING_NODE)
@@ -430,7 +461,7 @@ pg_status estimate_rho_lattice(pg_grid* g, double* rho) {
     if ((s = upload(g, x, ones))) return s;
     CK(cudaMemsetAsync(acc, 0, 2 * iters * sizeof(double), g->stream));
     CK(cudaMemsetAsync(mx, 0, iters * sizeof(unsigned long long), g->stream));
-    const int64_t cols = (int64_t)g->P.lat_nx * g->P.lat_ny;
+    const int64_t cols = g->dg.lat_cols;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(g->n_sm * 4, (cols + 255) / 256));
     for (int k = 0; k < iters; ++k) {
         CK(launch_lattice_power(g->dg, x, y, k ? mx + (k - 1) : nullptr, acc + 2 * k, mx + k, blocks, g->stream));

@@ -177,28 +177,53 @@ pg_status build_packed(const pg_netlist* nl, Packed* P, std::string* why) {
     }
     { std::vector<int32_t>().swap(tn); std::vector<double>().swap(tg); std::vector<double>().swap(tl); }
 
-    // --- lattice form: every merged neighbour pair is a lattice neighbour pair
+    // --- lattice form: lattices cover every node and every merged neighbour pair is a
+    //     lattice neighbour pair inside one lattice
     P->lattice = false;
     P->adj_dir.assign(P->adj_nbr.size(), -1);
-    if (nl->lat_nx > 0 && nl->lat_ny > 0 && nl->lat_nl > 0 && nl->lat_nl <= 3 &&
-        (int64_t)nl->lat_nx * nl->lat_ny * nl->lat_nl == n) {
-        const int32_t nx = nl->lat_nx, ny = nl->lat_ny;
-        bool ok = true;
-        for (int i = 0; i < n && ok; ++i) {
-            for (int64_t k = P->adj_ptr[i]; k < P->adj_ptr[i + 1]; ++k) {
-                const int j = P->adj_nbr[k];
-                const int xi = i % nx, yi = (i / nx) % ny, li = i / (nx * ny);
-                const int xj = j % nx, yj = (j / nx) % ny, lj = j / (nx * ny);
-                const int dx = xj - xi, dy = yj - yi, dl = lj - li;
-                if (dx == 1 && dy == 0 && dl == 0) P->adj_dir[k] = 0;
-                else if (dx == 0 && dy == 1 && dl == 0) P->adj_dir[k] = 1;
-                else if (dx == 0 && dy == 0 && dl == 1) P->adj_dir[k] = 2;
-                else if (!((dx == -1 && dy == 0 && dl == 0) || (dx == 0 && dy == -1 && dl == 0) ||
-                           (dx == 0 && dy == 0 && dl == -1))) { ok = false; break; }
+    P->lats.clear();
+    P->lat_maxnl = 0;
+    if (nl->n_lat > 0 && nl->lat_desc) {
+        P->lats.assign(nl->lat_desc, nl->lat_desc + 4 * nl->n_lat);
+    } else if (nl->lat_nx > 0 && nl->lat_ny > 0 && nl->lat_nl > 0) {
+        P->lats = {0, nl->lat_nx, nl->lat_ny, nl->lat_nl};
+    }
+    std::vector<int32_t> lat_of;   // caller id -> lattice
+    bool ok = !P->lats.empty();
+    if (ok) {
+        lat_of.assign(n, -1);
+        int64_t expect = 0;
+        for (size_t k = 0; k < P->lats.size() / 4 && ok; ++k) {
+            const int64_t off = P->lats[4 * k], nx = P->lats[4 * k + 1], ny = P->lats[4 * k + 2],
+                          nz = P->lats[4 * k + 3];
+            ok = off == expect && nx > 0 && ny > 0 && nz > 0 && nz <= 3 && off + nx * ny * nz <= n;
+            if (ok) {
+                for (int64_t q = off; q < off + nx * ny * nz; ++q) lat_of[q] = (int32_t)k;
+                expect = off + nx * ny * nz;
+                P->lat_maxnl = std::max<int32_t>(P->lat_maxnl, (int32_t)nz);
             }
         }
-        if (ok) { P->lattice = true; P->lat_nx = nx; P->lat_ny = ny; P->lat_nl = nl->lat_nl; }
+        ok = ok && expect == n;
     }
+    for (int i = 0; i < n && ok; ++i) {
+        const int L = lat_of[i];
+        const int off = P->lats[4 * L], nx = P->lats[4 * L + 1], ny = P->lats[4 * L + 2];
+        const int li = i - off;
+        const int xi = li % nx, yi = (li / nx) % ny, zi = li / (nx * ny);
+        for (int64_t k = P->adj_ptr[i]; k < P->adj_ptr[i + 1] && ok; ++k) {
+            const int j = P->adj_nbr[k];
+            if (lat_of[j] != L) { ok = false; break; }
+            const int lj = j - off;
+            const int dx = lj % nx - xi, dy = (lj / nx) % ny - yi, dz = lj / (nx * ny) - zi;
+            if (dx == 1 && dy == 0 && dz == 0) P->adj_dir[k] = 0;
+            else if (dx == 0 && dy == 1 && dz == 0) P->adj_dir[k] = 1;
+            else if (dx == 0 && dy == 0 && dz == 1) P->adj_dir[k] = 2;
+            else if (!((dx == -1 && dy == 0 && dz == 0) || (dx == 0 && dy == -1 && dz == 0) ||
+                       (dx == 0 && dy == 0 && dz == -1))) ok = false;
+        }
+    }
+    if (!ok) { P->lats.clear(); P->lat_maxnl = 0; }
+    P->lattice = ok;
 
     // --- colouring: BFS 2-colouring (red-black), else greedy multicolour
     std::vector<int32_t> colour(n, -1);
@@ -256,6 +281,11 @@ pg_status build_packed(const pg_netlist* nl, Packed* P, std::string* why) {
         std::vector<int32_t> fillc(P->colour_start, P->colour_start + ncol);
         for (int i = 0; i < n; ++i) { int k = fillc[colour[i]]++; P->perm[i] = k; P->orig[k] = i; }
     }
+
+    P->node_lat.assign(np, -1);
+    if (P->lattice)
+        for (int q = 0; q < np; ++q)
+            if (P->orig[q] >= 0) P->node_lat[q] = lat_of[P->orig[q]];
 
     // --- SELL slices, diagonal-offset form where the slice's columns are constant offsets
     const int32_t nsl = np / kSlice;

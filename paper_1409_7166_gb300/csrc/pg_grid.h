@@ -18,6 +18,7 @@ struct NetCopy {
     std::vector<double> r_g, c_val, l_val, i_t, i_v;
     std::vector<int64_t> i_ptr;
     int32_t nx = 0, ny = 0, nl = 0;
+    std::vector<int32_t> lat_desc;
 
     void from(const pg_netlist* nl_) {
         n = nl_->n_nodes; p = nl_->n_sources;
@@ -34,6 +35,7 @@ struct NetCopy {
             i_ptr.assign(1, 0);
         }
         nx = nl_->lat_nx; ny = nl_->lat_ny; nl = nl_->lat_nl;
+        if (nl_->n_lat > 0 && nl_->lat_desc) lat_desc.assign(nl_->lat_desc, nl_->lat_desc + 4 * nl_->n_lat);
     }
     // The DC network at t = 0: capacitors open, inductors carrying i_l(0) = 0 (open).
     pg_netlist dc_view() const {

@@ -59,8 +59,10 @@ struct Packed {
     // lattice form (optional): nodes (x, y, l) with id (l*ny + y)*nx + x and every
     // branch between lattice neighbours; adj_dir marks the +x / +y / +l entries
     bool lattice = false;
-    int32_t lat_nx = 0, lat_ny = 0, lat_nl = 0;
+    std::vector<int32_t> lats;     // 4 per lattice: first node id, nx, ny, nl
+    int32_t lat_maxnl = 0;
     std::vector<int8_t> adj_dir;   // 0: +x, 1: +y, 2: +l, -1: the reverse entries
+    std::vector<int32_t> node_lat; // permuted node -> lattice (-1 for padding)
 
     // components (connected sub-circuits, Fig. 1)
     int32_t n_comp = 0;
@@ -105,7 +107,13 @@ struct DevGrid {
     const int32_t* ind_idx;
     const double* vdd;
     // lattice form of the FP32 inner solve (caller order), or null
-    int32_t lat_nx, lat_ny, lat_nl;
+    int32_t n_lats;          // independent lattices, 4 ints each in lat_info: first id, nx, ny, nl
+    const int32_t* lat_info;
+    const int32_t* lat_tile0;   // [n_lats + 1] first tile of each lattice (for the round's tile size)
+    int32_t lat_tiles;
+    const int64_t* lat_col0;    // [n_lats + 1] first column (x, y) of each lattice
+    int64_t lat_cols;
+    const int32_t* node_lat;    // [n_pad] lattice of each permuted node, -1 for padding
     const float* lwE;        // weight to (x+1, y, l); 0 on the last column
     const float* lwN;        // weight to (x, y+1, l)
     const float* lwU;        // weight to (x, y, l+1)
@@ -133,6 +141,7 @@ struct DevCtl {
     unsigned long long* blk_min;    // [2 * nblocks] per-block min keys (double bits, ordered)
     int32_t* blk_arg;               // [2 * nblocks]
     double* stats;                  // device statistics, see kStat*
+    unsigned long long* lat_R;      // [2 * n_lats] per-lattice max |r| / D of the latest FP64 pass
 };
 
 enum Stat : int {

@@ -90,6 +90,31 @@ __device__ __forceinline__ float nanmaxf(float a, float b) { return (a > b || a 
 template <typename T>
 __device__ __forceinline__ T nanmax_t(T a, T b) { return (a > b || a != a) ? a : b; }
 
+// Per-lattice maxima of val over the lane's 4 nodes (warp-collective): one atomic
+// per warp when the slice lies in one lattice (the common case), else per node.
+__device__ __forceinline__ void lattice_max(const DevGrid& g, unsigned long long* latR, int i0,
+                                            const double (&val)[4]) {
+    int L[4];
+    bool same = true;
+    const int L0 = __shfl_sync(0xffffffffu, __ldg(g.node_lat + i0), 0);
+    double m = 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        L[j] = __ldg(g.node_lat + i0 + j);
+        same = same && (L[j] == L0 || L[j] < 0);
+        if (L[j] >= 0) m = nanmax(m, val[j]);
+    }
+    if (__all_sync(0xffffffffu, same)) {
+        for (int o = 16; o; o >>= 1) m = nanmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0 && L0 >= 0 && m != 0.0)
+            atomicMax(latR + L0, (unsigned long long)__double_as_longlong(m));
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (L[j] >= 0 && val[j] != 0.0) atomicMax(latR + L[j], (unsigned long long)__double_as_longlong(val[j]));
+    }
+}
+
 // Order-preserving map of a double to an unsigned key (for min reductions).
 __device__ __forceinline__ unsigned long long order_key(double x) {
     unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -309,7 +334,7 @@ __device__ __forceinline__ void sell_row(const DevGrid& g, const WarpCache* wc, 
 template <bool MIXED>
 __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* wc, const SliceDesc& sd,
                                             const DevState& st, const RunParams& rp, int s, int lane, int vL, int vP,
-                                            int vF, bool extrap, double t, int dsel) {
+                                            int vF, bool extrap, double t, int dsel, unsigned long long* latR) {
     const int i0 = s * kSlice + lane * kVec;
     const double* vl = vbuf(st, vL);
     const double* vp = vbuf(st, vP);
@@ -360,12 +385,14 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* w
     } else {
         sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return vl[c]; }, sig);
     }
-    double r[4], mon = 0.0;
+    double r[4], sc[4], mon = 0.0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         r[j] = b[j] + sig[j] - D[j] * vw[j];
-        mon = nanmax(mon, fabs(r[j]) * iD[j]);
+        sc[j] = fabs(r[j]) * iD[j];
+        mon = nanmax(mon, sc[j]);
     }
+    if (latR) lattice_max(g, latR, i0, sc);
     st4(vbuf(st, vF) + i0, vw);
     st4(st.r64 + i0, r);
     if (MIXED && rp.lat_k > 0) {
@@ -613,15 +640,15 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
-// One round over all tiles; returns the max unrelaxed column update of the last
-// sweep over tile interiors.  NL (layers) is a template parameter: the column
-// solve unrolls completely.
+// One tile (region of lattice L): load, 2k half-sweeps, store the interior.
+// Returns the max unrelaxed column update of the last sweep over the interior.
+// NL (layers) is a template parameter: the column solve unrolls completely.
 template <int NL>
-__device__ double lattice_round_nl(const DevGrid& g, const float* __restrict__ dold, float* __restrict__ dnew,
-                                   const float* __restrict__ r, float omega, int k, unsigned char* smem) {
-    const int nx = g.lat_nx, ny = g.lat_ny;
+__device__ float lattice_tile(const DevGrid& g, int off, int nx, int ny, int tile, const float* __restrict__ dold,
+                              float* __restrict__ dnew, const float* __restrict__ r, float omega, int k,
+                              unsigned char* smem) {
     const int H = 2 * k, T = kLatR - 2 * H;
-    const int tiles_x = (nx + T - 1) / T, tiles_y = (ny + T - 1) / T, ntiles = tiles_x * tiles_y;
+    const int tiles_x = (nx + T - 1) / T;
     constexpr int A = kLatMaxL * kLatPlane;           // floats per array
     float* sd = reinterpret_cast<float*>(smem);
     float* sr = sd + A;
@@ -634,110 +661,140 @@ __device__ double lattice_round_nl(const DevGrid& g, const float* __restrict__ d
     const int pair = lane & 15;                        // columns 2 pair, 2 pair + 1
     const int rsub = lane >> 4;                        // half-warps take adjacent rows (no bank conflicts)
     const long long plane = (long long)nx * ny;
-    const bool vec16 = (nx & 3) == 0 && (H & 3) == 0 && (T & 3) == 0;   // 16-byte aligned region rows
-    float mon = 0.f;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int x0 = (tile % tiles_x) * T - H, y0 = (tile / tiles_x) * T - H;
-        auto src_of = [&](int arr) -> const float* {   // by value: no local array
-            return arr == 0 ? dold : arr == 1 ? r : arr == 2 ? g.lwE : arr == 3 ? g.lwN : arr == 4 ? g.lwU
-                 : arr == 5 ? g.lm : g.lip;
-        };
-        if (vec16) {
-            const int ry = threadIdx.x >> 3, cx = threadIdx.x & 7;   // one 16-byte chunk per plane
-            const int xx = x0 + 4 * cx, yy = y0 + ry;
+    const bool vec16 = (nx & 3) == 0 && (off & 3) == 0 && (H & 3) == 0 && (T & 3) == 0;   // aligned rows
+    const int x0 = (tile % tiles_x) * T - H, y0 = (tile / tiles_x) * T - H;
+    auto src_of = [&](int arr) -> const float* {       // by value: no local array
+        return arr == 0 ? dold : arr == 1 ? r : arr == 2 ? g.lwE : arr == 3 ? g.lwN : arr == 4 ? g.lwU
+             : arr == 5 ? g.lm : g.lip;
+    };
+    if (vec16) {
+        const int ry = threadIdx.x >> 3, cx = threadIdx.x & 7;   // one 16-byte chunk per plane
+        const int xx = x0 + 4 * cx, yy = y0 + ry;
+        const bool in = yy >= 0 && yy < ny && xx >= 0 && xx < nx;
+        const long long o = in ? off + (long long)yy * nx + xx : 0;
+        const int sa = ry * kLatR + 4 * cx;
+#pragma unroll
+        for (int arr = 0; arr < kLatArrays; ++arr)
+#pragma unroll
+            for (int l = 0; l < NL; ++l)
+                cp_async16(sd + arr * A + l * kLatPlane + sa, src_of(arr) + (in ? o + l * plane : 0), in ? 16u : 0u);
+    } else {
+        const int rx = threadIdx.x & 31;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int ry = (threadIdx.x >> 5) + 8 * q, yy = y0 + ry, xx = x0 + rx;
             const bool in = yy >= 0 && yy < ny && xx >= 0 && xx < nx;
-            const long long off = in ? (long long)yy * nx + xx : 0;
-            const int sa = ry * kLatR + 4 * cx;
+            const long long o = in ? off + (long long)yy * nx + xx : 0;
+            const int sa = ry * kLatR + rx;
 #pragma unroll
             for (int arr = 0; arr < kLatArrays; ++arr)
 #pragma unroll
                 for (int l = 0; l < NL; ++l)
-                    cp_async16(sd + arr * A + l * kLatPlane + sa, src_of(arr) + (in ? l * plane + off : 0),
-                               in ? 16u : 0u);
-        } else {
-            const int rx = threadIdx.x & 31;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int ry = (threadIdx.x >> 5) + 8 * q, yy = y0 + ry, xx = x0 + rx;
-                const bool in = yy >= 0 && yy < ny && xx >= 0 && xx < nx;
-                const long long off = in ? (long long)yy * nx + xx : 0;
-                const int sa = ry * kLatR + rx;
-#pragma unroll
-                for (int arr = 0; arr < kLatArrays; ++arr)
-#pragma unroll
-                    for (int l = 0; l < NL; ++l)
-                        cp_async4(sd + arr * A + l * kLatPlane + sa, src_of(arr) + (in ? l * plane + off : 0),
-                                  in ? 4u : 0u);
-            }
+                    cp_async4(sd + arr * A + l * kLatPlane + sa, src_of(arr) + (in ? o + l * plane : 0), in ? 4u : 0u);
         }
-        cp_async_wait_all();
-        __syncthreads();
-        for (int hs = 0; hs < 2 * k; ++hs) {
-            const bool last = hs >= 2 * k - 2;
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int ry = 2 * (warp + 8 * j) + rsub, y = y0 + ry;
-                const int rx = 2 * pair + ((hs + x0 + y) & 1);      // the column of this colour in the pair
-                const int x = x0 + rx;
-                const int edge = min(min(rx, ry), min(kLatR - 1 - rx, kLatR - 1 - ry));
-                if (edge == 0 || x < 0 || x >= nx || y < 0 || y >= ny) continue;
-                const int a0 = ry * kLatR + rx;
-                float f[NL], xs[NL];
-#pragma unroll
-                for (int l = 0; l < NL; ++l) {
-                    const int a = a0 + l * kLatPlane;
-                    f[l] = sr[a] + se[a] * sd[a + 1] + se[a - 1] * sd[a - 1] + sn[a] * sd[a + kLatR] +
-                           sn[a - kLatR] * sd[a - kLatR];
-                }
-#pragma unroll
-                for (int l = 1; l < NL; ++l) f[l] = fmaf(sm[a0 + l * kLatPlane], f[l - 1], f[l]);
-                xs[NL - 1] = f[NL - 1] * sp[a0 + (NL - 1) * kLatPlane];
-#pragma unroll
-                for (int l = NL - 2; l >= 0; --l)
-                    xs[l] = fmaf(su[a0 + l * kLatPlane], xs[l + 1], f[l]) * sp[a0 + l * kLatPlane];
-                const bool interior = edge >= H;
-#pragma unroll
-                for (int l = 0; l < NL; ++l) {
-                    const int a = a0 + l * kLatPlane;
-                    const float dv = sd[a];
-                    const float upd = xs[l] - dv;
-                    sd[a] = fmaf(omega, upd, dv);
-                    if (last && interior) mon = nanmaxf(mon, fabsf(upd));
-                }
-            }
-            __syncthreads();
-        }
-        {
-            const int rx = threadIdx.x & 31;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int ry = (threadIdx.x >> 5) + 8 * q, y = y0 + ry, x = x0 + rx;
-                const int edge = min(min(rx, ry), min(kLatR - 1 - rx, kLatR - 1 - ry));
-                if (edge < H || x < 0 || x >= nx || y < 0 || y >= ny) continue;
-                const long long b = (long long)y * nx + x;
-#pragma unroll
-                for (int l = 0; l < NL; ++l) dnew[b + l * plane] = sd[l * kLatPlane + ry * kLatR + rx];
-            }
-        }
-        __syncthreads();   // the next tile overwrites the region
     }
-    return (double)mon;
+    cp_async_wait_all();
+    __syncthreads();
+    float mon = 0.f;
+    for (int hs = 0; hs < 2 * k; ++hs) {
+        const bool last = hs >= 2 * k - 2;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int ry = 2 * (warp + 8 * j) + rsub, y = y0 + ry;
+            const int rx = 2 * pair + ((hs + x0 + y) & 1);      // the column of this colour in the pair
+            const int x = x0 + rx;
+            const int edge = min(min(rx, ry), min(kLatR - 1 - rx, kLatR - 1 - ry));
+            if (edge == 0 || x < 0 || x >= nx || y < 0 || y >= ny) continue;
+            const int a0 = ry * kLatR + rx;
+            float f[NL], xs[NL];
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                const int a = a0 + l * kLatPlane;
+                f[l] = sr[a] + se[a] * sd[a + 1] + se[a - 1] * sd[a - 1] + sn[a] * sd[a + kLatR] +
+                       sn[a - kLatR] * sd[a - kLatR];
+            }
+#pragma unroll
+            for (int l = 1; l < NL; ++l) f[l] = fmaf(sm[a0 + l * kLatPlane], f[l - 1], f[l]);
+            xs[NL - 1] = f[NL - 1] * sp[a0 + (NL - 1) * kLatPlane];
+#pragma unroll
+            for (int l = NL - 2; l >= 0; --l)
+                xs[l] = fmaf(su[a0 + l * kLatPlane], xs[l + 1], f[l]) * sp[a0 + l * kLatPlane];
+            const bool interior = edge >= H;
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                const int a = a0 + l * kLatPlane;
+                const float dv = sd[a];
+                const float upd = xs[l] - dv;
+                sd[a] = fmaf(omega, upd, dv);
+                if (last && interior) mon = nanmaxf(mon, fabsf(upd));
+            }
+        }
+        __syncthreads();
+    }
+    {
+        const int rx = threadIdx.x & 31;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int ry = (threadIdx.x >> 5) + 8 * q, y = y0 + ry, x = x0 + rx;
+            const int edge = min(min(rx, ry), min(kLatR - 1 - rx, kLatR - 1 - ry));
+            if (edge < H || x < 0 || x >= nx || y < 0 || y >= ny) continue;
+            const long long b = off + (long long)y * nx + x;
+#pragma unroll
+            for (int l = 0; l < NL; ++l) dnew[b + l * plane] = sd[l * kLatPlane + ry * kLatR + rx];
+        }
+    }
+    __syncthreads();   // the next tile overwrites the region
+    return mon;
 }
 
-__device__ __forceinline__ double lattice_round(const DevGrid& g, const float* dold, float* dnew, const float* r,
-                                                float omega, int k, unsigned char* smem) {
-    switch (g.lat_nl) {
-        case 1: return lattice_round_nl<1>(g, dold, dnew, r, omega, k, smem);
-        case 2: return lattice_round_nl<2>(g, dold, dnew, r, omega, k, smem);
-        default: return lattice_round_nl<3>(g, dold, dnew, r, omega, k, smem);
+// One round over the tiles of every lattice whose residual (latest FP64 pass,
+// slots `latR`) is still above the step's target.  The lattices are independent
+// sub-circuits (Fig. 1), so a converged one keeps its solution: its correction
+// must stay zero in both buffers, which the start buffer is (zeroed by the FP64
+// pass) and which the first round of the inner solve (`first`) writes into the
+// other one; later rounds skip those tiles entirely.
+__device__ double lattice_round(const DevGrid& g, const float* dold, float* dnew, const float* r, float omega,
+                                int k, unsigned char* smem, const unsigned long long* latR, double target,
+                                bool first) {
+    float mon = 0.f;
+    for (int t = blockIdx.x; t < g.lat_tiles; t += gridDim.x) {
+        int lo = 0, hi = g.n_lats;                      // lattice with lat_tile0[L] <= t < lat_tile0[L+1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(g.lat_tile0 + mid) <= t) lo = mid; else hi = mid;
+        }
+        const int L = lo;
+        const int off = __ldg(g.lat_info + 4 * L), nx = __ldg(g.lat_info + 4 * L + 1),
+                  ny = __ldg(g.lat_info + 4 * L + 2), nl = __ldg(g.lat_info + 4 * L + 3);
+        const int tile = t - __ldg(g.lat_tile0 + L);
+        if (latR && __longlong_as_double((long long)latR[L]) <= target) {
+            // converged lattice (uniform across the block: no barrier divergence)
+            if (first) {
+                const int H = 2 * k, T = kLatR - 2 * H, tiles_x = (nx + T - 1) / T;
+                const int tx0 = (tile % tiles_x) * T, ty0 = (tile / tiles_x) * T;
+                const long long plane = (long long)nx * ny;
+                for (int q = threadIdx.x; q < T * T; q += blockDim.x) {
+                    const int x = tx0 + q % T, y = ty0 + q / T;
+                    if (x >= nx || y >= ny) continue;
+                    for (int l = 0; l < nl; ++l) dnew[off + l * plane + (long long)y * nx + x] = 0.f;
+                }
+            }
+            continue;
+        }
+        float m;
+        if (nl == 1) m = lattice_tile<1>(g, off, nx, ny, tile, dold, dnew, r, omega, k, smem);
+        else if (nl == 2) m = lattice_tile<2>(g, off, nx, ny, tile, dold, dnew, r, omega, k, smem);
+        else m = lattice_tile<3>(g, off, nx, ny, tile, dold, dnew, r, omega, k, smem);
+        mon = nanmaxf(mon, m);
     }
+    return (double)mon;
 }
 
 // Outer defect-correction pass: v += delta, r -= M delta (FP64), refresh the FP32 residual.
 template <typename T>
 __device__ __forceinline__ double outer_slice(const DevGrid& g, const WarpCache* wc, const SliceDesc& sd,
                                               const DevState& st, const T* d, T* dnext, float* r32, int s, int lane,
-                                              double* v, bool lat) {
+                                              double* v, bool lat, unsigned long long* latR) {
     const int i0 = s * kSlice + lane * kVec;
     T dv[4];
     if (lat) {
@@ -763,14 +820,16 @@ __device__ __forceinline__ double outer_slice(const DevGrid& g, const WarpCache*
     } else {
         sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return (double)d[c]; }, sig);
     }
-    double mon = 0.0;
+    double mon = 0.0, sc[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const double dj = (double)dv[j];
         r[j] = r[j] - (D[j] * dj - sig[j]);
         vv[j] += dj;
-        mon = nanmax(mon, fabs(r[j]) * iD[j]);
+        sc[j] = fabs(r[j]) * iD[j];
+        mon = nanmax(mon, sc[j]);
     }
+    if (latR) lattice_max(g, latR, i0, sc);
     st4(st.r64 + i0, r);
     st4(v + i0, vv);
     if (lat) {
@@ -890,6 +949,15 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
     const double target = rp.target_scale ? rp.target * __longlong_as_double((long long)*rp.target_scale) : rp.target;
     int vL = rp.cur, vP = rp.prev, vF = 3 - rp.cur - rp.prev;
     bool have_prev = rp.have_prev != 0;
+    // per-lattice residual maxima (lattice inner solve): two buffers, `lat_par` is the one
+    // the latest FP64 pass wrote; the host clears both before the launch
+    const bool per_lat = MIXED && rp.lat_k > 0 && ctl.lat_R != nullptr;
+    int lat_par = 0;
+    auto lat_buf = [&](int b) { return per_lat ? ctl.lat_R + (size_t)b * g.n_lats : nullptr; };
+    auto lat_clear = [&](int b) {
+        if (per_lat && blockIdx.x == 0)
+            for (int q = threadIdx.x; q < g.n_lats; q += blockDim.x) ctl.lat_R[(size_t)b * g.n_lats + q] = 0ull;
+    };
 
     for (int sl = 0; sl < rp.nsteps; ++sl) {
         const long long sabs = rp.step0 + sl + 1;
@@ -904,11 +972,12 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
             for (int tt = 0; tt < wc->cnt[c]; ++tt) {
                 const int s = wc->lo[c] + tt;
                 mon = nanmax(mon, phase_rhs<MIXED>(g, wc, warp_desc(g, *wc, c, tt, s), st, rp, s, lane, vL, vP, vF,
-                                                   extrap, t, dsel));
+                                                   extrap, t, dsel, lat_buf(lat_par ^ 1)));
             }
         BarrierResult br = barrier(true, mon);
         if (!br.ok) { publish(-1); return; }
         double R = br.val;
+        lat_par ^= 1;
 
         int sweeps = 0, outer = 0;
         bool ok = true;
@@ -923,11 +992,13 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
             double est_mark = INFINITY;   // monitor value at the last stagnation check
             bool est_nan = false;         // a non-finite update (diverged, or a failed copy)
             int inner = 0;
+            lat_clear(lat_par ^ 1);       // the next FP64 pass writes there; its readers are done
             while (MIXED && rp.lat_k > 0) {
-                // lattice rounds: lat_k exact red-black sweeps per device barrier
+                // lattice rounds: lat_k exact block sweeps per device barrier
                 const float* dold = dbuf<float>(st, dsel);
                 float* dnew = dbuf<float>(st, dsel ^ 1);
-                const double m = lattice_round(g, dold, dnew, st.r32, (float)omega, rp.lat_k, s_dyn);
+                const double m = lattice_round(g, dold, dnew, st.r32, (float)omega, rp.lat_k, s_dyn,
+                                               lat_buf(lat_par), target, inner == 0);
                 const BarrierResult be = barrier(true, m);
                 if (!be.ok) { publish(-1); return; }
                 const double est = be.val;
@@ -980,17 +1051,19 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
                     const int s = wc->lo[c] + tt;
                     m = nanmax(m, outer_slice<T>(g, wc, warp_desc(g, *wc, c, tt, s), st, dd, dn,
                                                  MIXED ? st.r32 : nullptr, s, lane, vbuf(st, vF),
-                                                 MIXED && rp.lat_k > 0));
+                                                 MIXED && rp.lat_k > 0, lat_buf(lat_par ^ 1)));
                 }
             br = barrier(true, m);
             if (!br.ok) { publish(-1); return; }
             R = br.val;
+            lat_par ^= 1;
             dsel ^= 1;
             ++outer;
         }
         if (!ok) { fail(sabs); return; }
 
         // ---- post: inductor currents (Eq. 10), outputs
+        lat_clear(lat_par ^ 1);           // the next step's phase A writes there
         const double* vnew = vbuf(st, vF);
         if (rp.mode == kModeTransient) {
             for (int e = gtid; e < g.n_l; e += nthreads) {
@@ -1109,55 +1182,72 @@ __global__ void __launch_bounds__(256) power_step_kernel(DevGrid g, const double
 }
 
 // Power iteration for the column-block Jacobi operator B^-1 W (lattice form): one
-// thread per column, y = (x + B^-1 W x) / 2 with x scaled by 1 / xmax_prev; accumulates
-// x.(W x) and x.(B x), whose ratio is a Rayleigh quotient of W v = lambda B v.
+// thread per column (x, y) of any lattice, y = (x + B^-1 W x) / 2 with x scaled by
+// 1 / xmax_prev; accumulates x.(W x) and x.(B x), whose ratio is a Rayleigh quotient of
+// W v = lambda B v.
 template <int NL>
+__device__ __forceinline__ void lattice_power_column(const DevGrid& g, int off, int nx, int ny, long long c,
+                                                     const double* x, double* y, double sc, double& num,
+                                                     double& den, double& mx) {
+    const long long plane = (long long)nx * ny;
+    const int cx = (int)(c % nx), cy = (int)(c / nx);
+    const long long o0 = off + c;
+    double xv[NL], wx[NL], f[NL], dl[NL], u[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        const long long o = o0 + l * plane;
+        xv[l] = x[o] * sc;
+        double s = 0.0;
+        if (cx + 1 < nx) s += (double)__ldg(g.lwE + o) * x[o + 1] * sc;
+        if (cx > 0) s += (double)__ldg(g.lwE + o - 1) * x[o - 1] * sc;
+        if (cy + 1 < ny) s += (double)__ldg(g.lwN + o) * x[o + nx] * sc;
+        if (cy > 0) s += (double)__ldg(g.lwN + o - nx) * x[o - nx] * sc;
+        wx[l] = s;
+        u[l] = (double)__ldg(g.lwU + o);
+        // block diagonal from the Thomas factors: d_l = d'_l + m_l u_{l-1}
+        dl[l] = 1.0 / (double)__ldg(g.lip + o) + (l > 0 ? (double)__ldg(g.lm + o) * u[l - 1] : 0.0);
+    }
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        double bx = dl[l] * xv[l];
+        if (l > 0) bx -= u[l - 1] * xv[l - 1];
+        if (l + 1 < NL) bx -= u[l] * xv[l + 1];
+        num += xv[l] * wx[l];
+        den += xv[l] * bx;
+        f[l] = wx[l];
+    }
+#pragma unroll
+    for (int l = 1; l < NL; ++l) f[l] += (double)__ldg(g.lm + o0 + l * plane) * f[l - 1];
+    double z[NL];
+    z[NL - 1] = f[NL - 1] * (double)__ldg(g.lip + o0 + (NL - 1) * plane);
+#pragma unroll
+    for (int l = NL - 2; l >= 0; --l) z[l] = (f[l] + u[l] * z[l + 1]) * (double)__ldg(g.lip + o0 + l * plane);
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        const double yv = 0.5 * (xv[l] + z[l]);
+        y[o0 + l * plane] = yv;
+        mx = fmax(mx, yv);
+    }
+}
+
 __global__ void __launch_bounds__(256) lattice_power_kernel(DevGrid g, const double* x, double* y,
                                                            const unsigned long long* xmax_prev, double* acc,
                                                            unsigned long long* ymax) {
-    const int nx = g.lat_nx, ny = g.lat_ny;
-    const long long plane = (long long)nx * ny;
     const double sc = xmax_prev ? 1.0 / __longlong_as_double((long long)*xmax_prev) : 1.0;
     double num = 0.0, den = 0.0, mx = 0.0;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < plane;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.lat_cols;
          c += (long long)gridDim.x * blockDim.x) {
-        const int cx = (int)(c % nx), cy = (int)(c / nx);
-        double xv[NL], wx[NL], f[NL], dl[NL], u[NL];
-#pragma unroll
-        for (int l = 0; l < NL; ++l) {
-            const long long o = c + l * plane;
-            xv[l] = x[o] * sc;
-            double s = 0.0;
-            if (cx + 1 < nx) s += (double)__ldg(g.lwE + o) * x[o + 1] * sc;
-            if (cx > 0) s += (double)__ldg(g.lwE + o - 1) * x[o - 1] * sc;
-            if (cy + 1 < ny) s += (double)__ldg(g.lwN + o) * x[o + nx] * sc;
-            if (cy > 0) s += (double)__ldg(g.lwN + o - nx) * x[o - nx] * sc;
-            wx[l] = s;
-            u[l] = (double)__ldg(g.lwU + o);
-            // block diagonal from the Thomas factors: d_l = d'_l + m_l u_{l-1}
-            dl[l] = 1.0 / (double)__ldg(g.lip + o) + (l > 0 ? (double)__ldg(g.lm + o) * u[l - 1] : 0.0);
+        int lo = 0, hi = g.n_lats;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(g.lat_col0 + mid) <= c) lo = mid; else hi = mid;
         }
-#pragma unroll
-        for (int l = 0; l < NL; ++l) {
-            double bx = dl[l] * xv[l];
-            if (l > 0) bx -= u[l - 1] * xv[l - 1];
-            if (l + 1 < NL) bx -= u[l] * xv[l + 1];
-            num += xv[l] * wx[l];
-            den += xv[l] * bx;
-            f[l] = wx[l];
-        }
-#pragma unroll
-        for (int l = 1; l < NL; ++l) f[l] += (double)__ldg(g.lm + c + l * plane) * f[l - 1];
-        double z[NL];
-        z[NL - 1] = f[NL - 1] * (double)__ldg(g.lip + c + (NL - 1) * plane);
-#pragma unroll
-        for (int l = NL - 2; l >= 0; --l) z[l] = (f[l] + u[l] * z[l + 1]) * (double)__ldg(g.lip + c + l * plane);
-#pragma unroll
-        for (int l = 0; l < NL; ++l) {
-            const double yv = 0.5 * (xv[l] + z[l]);
-            y[c + l * plane] = yv;
-            mx = fmax(mx, yv);
-        }
+        const int off = __ldg(g.lat_info + 4 * lo), nx = __ldg(g.lat_info + 4 * lo + 1),
+                  ny = __ldg(g.lat_info + 4 * lo + 2), nl = __ldg(g.lat_info + 4 * lo + 3);
+        const long long cc = c - __ldg(g.lat_col0 + lo);
+        if (nl == 1) lattice_power_column<1>(g, off, nx, ny, cc, x, y, sc, num, den, mx);
+        else if (nl == 2) lattice_power_column<2>(g, off, nx, ny, cc, x, y, sc, num, den, mx);
+        else lattice_power_column<3>(g, off, nx, ny, cc, x, y, sc, num, den, mx);
     }
     for (int o = 16; o; o >>= 1) {
         num += __shfl_xor_sync(kFull, num, o);
@@ -1291,11 +1381,7 @@ cudaError_t launch_adjoint_grad(const DevGrid& g, const double* lam, const doubl
 
 cudaError_t launch_lattice_power(const DevGrid& g, const double* x, double* y, const unsigned long long* xmax_prev,
                                  double* acc, unsigned long long* ymax, int blocks, cudaStream_t stream) {
-    switch (g.lat_nl) {
-        case 1: lattice_power_kernel<1><<<blocks, 256, 0, stream>>>(g, x, y, xmax_prev, acc, ymax); break;
-        case 2: lattice_power_kernel<2><<<blocks, 256, 0, stream>>>(g, x, y, xmax_prev, acc, ymax); break;
-        default: lattice_power_kernel<3><<<blocks, 256, 0, stream>>>(g, x, y, xmax_prev, acc, ymax); break;
-    }
+    lattice_power_kernel<<<blocks, 256, 0, stream>>>(g, x, y, xmax_prev, acc, ymax);
     return cudaGetLastError();
 }
 

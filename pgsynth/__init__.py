@@ -70,6 +70,8 @@ class Netlist:
     i_v: np.ndarray
     lattice: Optional[Tuple[int, int, int]] = None
     name: str = ""
+    # independent lattices side by side: (first node id, nx, ny, nl) each
+    lattices: Optional[list] = None
     meta: dict = field(default_factory=dict)
 
     @property
@@ -319,6 +321,7 @@ def config3(seed: int = 3, n_grids: int = 256, side_lo: int = 64, side_hi: int =
                                   "c_b": sh(p.c_b), "l_a": sh(p.l_a), "l_b": sh(p.l_b),
                                   "i_a": sh(p.i_a), "i_b": sh(p.i_b)}))
     net = concat_netlists(shifted, name=f"batched_{n_grids}_rc_grids")
+    net.lattices = [(off, *p.lattice) for off, p in parts]
     net.meta = dict(h=10e-12, nsteps=500, precision="mixed",
                     grid_sizes=[p.n_nodes for _, p in parts],
                     grid_shapes=[p.lattice for _, p in parts],

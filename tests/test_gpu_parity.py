@@ -235,3 +235,22 @@ def test_lattice_block_inner_solve(B, shape, k):
     with B.Grid(net, precision=1, lattice_sweeps=k) as g:
         assert g.info["n_nodes"] == nx * ny * nl
     check_against_oracle(B, net, net.meta["h"], 40, 1, lattice_sweeps=k)
+
+
+def test_batched_lattices_skip_converged_grids(B):
+    """A batch of lattices (1 and 2 layers) where some grids carry no load: those
+    converge at once and their tiles are skipped while the others iterate; every
+    node still matches the oracle.  Also checks the lattice inner solve is the one
+    that ran."""
+    net = pgsynth.config3(n_grids=7, side_lo=20, side_hi=52, seed=2)
+    parts = pgsynth.config3_parts(n_grids=7, side_lo=20, side_hi=52, seed=2)
+    net.i_v = net.i_v.copy()
+    ptr = net.i_ptr
+    for k in (1, 4):                                  # silence every load of grids 1 and 4
+        off, p = parts[k]
+        sel = (net.i_a >= off) & (net.i_a < off + p.n_nodes)
+        for e in np.nonzero(sel)[0]:
+            net.i_v[ptr[e]:ptr[e + 1]] = 0.0
+    assert any(p.lattice[2] == 2 for _, p in parts) and any(p.lattice[2] == 1 for _, p in parts)
+    err, st = check_against_oracle(B, net, net.meta["h"], 50, 1)
+    assert st.lattice_sweeps == 2
