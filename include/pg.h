@@ -228,7 +228,10 @@ pg_status pg_step(pg_grid* g, double h, double* v_out, pg_run_stats* stats);
 /*
  * Solve M x = b once for the assembled h (b, x: device, [n_nodes], caller
  * numbering) to the absolute error target `tol` (V-like units of x), starting
- * from x = 0.  Exposes the relaxation kernel on its own.
+ * from x = 0.  Exposes the relaxation kernel on its own.  b is read on the
+ * grid's stream; the first call allocates one [n_nodes]-sized device buffer that
+ * the grid keeps.  tol must exceed kappa * 1e-13 (the rounding allowance of the
+ * stopping rule), else PG_ERR_INVALID_ARG.
  */
 pg_status pg_solve(pg_grid* g, double h, const double* b, double* x, double tol,
                    pg_run_stats* stats);

@@ -1138,26 +1138,22 @@ pg_status pg_solve(pg_grid* g, double h, const double* b, double* x, double tol,
     if (!g || !b || !x || !(tol > 0.0)) return PG_ERR_INVALID_ARG;
     pg_status s = prepare_h(g, h);
     if (s) return s;
-    const Packed& P = g->P;
-    std::vector<double> hb(P.n), bp(P.n_pad, 0.0);
-    CK(cudaMemcpy(hb.data(), b, P.n * sizeof(double), cudaMemcpyDeviceToHost));
-    for (int i = 0; i < P.n_pad; ++i)
-        if (P.orig[i] >= 0) bp[i] = hb[P.orig[i]];
-    double* d_b = nullptr;
-    CK(cudaMalloc(&d_b, P.n_pad * sizeof(double)));
-    cudaMemcpy(d_b, bp.data(), P.n_pad * sizeof(double), cudaMemcpyHostToDevice);
+    if (!g->d_rhs && !(g->d_rhs = g->alloc<double>(g->P.n_pad))) return PG_ERR_OOM;
     RunParams rp = base_params(g);
     rp.mode = kModeSolve;
     rp.nsteps = 1;
     rp.target = tol / g->kappa - 1e-13;
     rp.solve_out = x;
-    g->ds.rhs = d_b;
+    if (!(rp.target > 0.0)) {
+        g_last_error = "tol below the rounding floor (kappa * 1e-13)";
+        return PG_ERR_INVALID_ARG;
+    }
+    CK(launch_permute_in(g->dg.orig, b, 0.0, g->d_rhs, g->P.n_pad, g->n_sm, g->stream));
     double st[kStatCount];
     float ms = 0.f;
-    if (!(rp.target > 0.0)) { cudaFree(d_b); g->ds.rhs = nullptr; return PG_ERR_INVALID_ARG; }
+    g->ds.rhs = g->d_rhs;
     s = run(g, rp, st, &ms);
     g->ds.rhs = nullptr;
-    cudaFree(d_b);
     fill_stats(g, st, ms, stats);
     return s;
 }

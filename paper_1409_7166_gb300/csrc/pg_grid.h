@@ -81,6 +81,7 @@ struct pg_grid {
     DevState ds{};
     DevCtl dc{};
     double* d_x = nullptr;        // scratch [n] for setup solves (caller numbering)
+    double* d_rhs = nullptr;      // pg_solve's permuted right-hand side [n_pad], allocated on first use
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // per-h
     double h = -1.0;

@@ -18,6 +18,12 @@ RC grids).
 * 256 batched grids: every grid is an independent sub-circuit (Fig. 1), so the
   oracle solves sampled grids exactly on their own and compares every node of
   them, every step (read through the probe output).
+* RC 2048x2048, 500 steps (the adjoint workload): the forward trajectory is
+  certified like the 1024x1024x3 one; the gradients of pg_adjoint (no
+  counterpart in the paper) are checked at full size by properties that hold at
+  any size: an exact scaling identity over all parameters, a tangent-linear
+  (forward-mode) dot-product test along a capacitor direction, a central
+  difference along a random resistor direction, bit-identical checkpoint replay.
 """
 import json
 import os
@@ -142,3 +148,111 @@ def test_config3_full_size_sampled_grids(B):
         col += part.n_nodes
         err = float(np.max(np.abs(got - Vo[1:])))
         assert err <= TOL_V, f"grid {k} ({part.lattice}): max error {err:.3e} V"
+
+
+@pytest.mark.skipif(not os.path.exists(GOLDEN), reason="run tests/golden/make_fullsize_bounds.py")
+def test_config4_full_size_certified(B):
+    net = pgsynth.config4()
+    with open(GOLDEN) as f:
+        bounds = json.load(f)["config4"]
+    err, per_step = _certify_rc(B, net, bounds)
+    print(f"config 4: per-step bound {per_step:.3e} V, accumulated bound {err:.3e} V")
+    assert err <= TOL_V
+
+
+def _dJ_dv(V, vref, margin):
+    u = vref - V - margin
+    return -2.0 * torch.nn.functional.softplus(u, threshold=1e9) * torch.sigmoid(u)
+
+
+def test_config4_full_size_adjoint(B):
+    """Gradients of J = sum_s sum_i softplus(1 - v - 0.05)^2 over 500 steps of
+    the 2048x2048 grid (checkpoints every 50 steps).
+
+    * Scaling identity: multiplying every conductance and capacitance by a
+      leaves M v = b invariant up to v - Vdd -> (v - Vdd)/a (the supply is the
+      only source and the DC point is v = Vdd), so
+      sum_e g_e dJ/dg_e + sum_k C_k dJ/dC_k = sum_{s,i} 2 sp(u) sig(u) (v - Vdd)
+      exactly; both sides in FP64, equal to 1e-9 relative.
+    * Tangent linear model along dC = K C w (w = 1 on the left half): with
+      M dv_s = (C/h) dv_{s-1} - (dC/h)(v_s - v_{s-1}), dv_0 = 0, the directional
+      derivative is sum_{s,i} dJ/dv_{s,i} dv_{s,i}.  Each solve is certified to
+      tol_s; T = M^-1 C/h >= 0 carries the errors, so
+      |error| <= kacc tol_s sum|dJ/dv|, the test's bound.
+    * Central difference along a random-sign relative perturbation of every
+      resistor (eps = 1e-3, per-term differences of J): relative 1e-4.
+    """
+    net = pgsynth.config4()
+    h, S, n = net.meta["h"], net.meta["nsteps"], net.n_nodes
+    vref, margin, vdd = 1.0, 0.05, float(net.vdd[0])
+    dev = "cuda"
+    with B.Grid(net, precision=B.PG_PREC_MIXED, tol=1e-9) as g:
+        B.pg_set_stream(g.handle, torch.cuda.current_stream().cuda_stream)
+        gG = torch.zeros(len(net.r_g), dtype=torch.float64, device=dev)
+        gC = torch.zeros(len(net.c_val), dtype=torch.float64, device=dev)
+        J, st = B.pg_adjoint(g.handle, h, S, vref=vref, margin=margin, ckpt_every=50, dJ_dG=gG, dJ_dC=gC)
+        # the backward pass replays segments from checkpoints: their spacing changes nothing
+        gG2, gC2 = torch.zeros_like(gG), torch.zeros_like(gC)
+        J2, _ = B.pg_adjoint(g.handle, h, S, vref=vref, margin=margin, ckpt_every=125, dJ_dG=gG2, dJ_dC=gC2)
+        assert J2 == J and torch.equal(gG, gG2) and torch.equal(gC, gC2)
+        del gG2, gC2
+
+        B.pg_reset(g.handle)
+        V = torch.empty((S, n), dtype=torch.float64, device=dev)
+        fst = B.pg_transient(g.handle, h, S, v_all=V)
+        chunks = range(0, S, 25)
+        Jv = sum(float((torch.nn.functional.softplus(vref - V[a:a + 25] - margin, threshold=1e9) ** 2).sum())
+                 for a in chunks)
+        assert Jv == pytest.approx(J, rel=1e-12)
+
+        r_g = torch.tensor(net.r_g, device=dev)
+        c_val = torch.tensor(net.c_val, device=dev)
+        lhs = float((r_g * gG).sum()) + float((c_val * gC).sum())
+        rhs = sum(float((-_dJ_dv(V[a:a + 25], vref, margin) * (V[a:a + 25] - vdd)).sum()) for a in chunks)
+        assert lhs == pytest.approx(rhs, rel=1e-9), (lhs, rhs)
+
+        # tangent linear model along a capacitor direction
+        cnode = np.where(net.c_a >= 0, net.c_a, net.c_b)
+        xs = (cnode % 2048) < 1024                       # left half of the grid
+        K = 1e4
+        dc = np.where(xs, K * net.c_val, 0.0)
+        Ch = torch.tensor(np.bincount(cnode, net.c_val / h, minlength=n), device=dev)
+        dCh = torch.tensor(np.bincount(cnode, dc / h, minlength=n), device=dev)
+        tol_s = 1e-10
+        dv = torch.zeros(n, dtype=torch.float64, device=dev)
+        nxt = torch.empty_like(dv)
+        v_prev = torch.full((n,), vdd, dtype=torch.float64, device=dev)   # DC point v_0 = Vdd
+        tl, absw = 0.0, 0.0
+        for s_ in range(S):
+            b = Ch * dv - dCh * (V[s_] - v_prev)
+            B.pg_solve(g.handle, h, b, nxt, tol_s)
+            w = _dJ_dv(V[s_], vref, margin)
+            tl += float((w * nxt).sum())
+            absw += float(w.abs().sum())
+            dv, nxt = nxt, dv
+            v_prev = V[s_]
+        ad = float((torch.tensor(dc, device=dev) * gC).sum())
+        bound = st.kacc * tol_s * absw
+        print(f"tangent linear {tl:.12e} adjoint {ad:.12e} bound {bound:.2e}")
+        assert abs(tl - ad) <= bound + 1e-9 * abs(ad)
+        del V, dv, nxt, v_prev
+
+        # central difference along a random resistor direction, per-term J differences
+        rng = np.random.default_rng(44)
+        sgn = rng.choice([-1.0, 1.0], size=len(net.r_g))
+        eps = 1e-3
+        Vp = torch.empty((S, n), dtype=torch.float64, device=dev)
+        Vm = torch.empty_like(Vp)
+        for sign, Vx in ((1.0, Vp), (-1.0, Vm)):
+            B.pg_update_values(g.handle, r_g=net.r_g * (1.0 + sign * eps * sgn))
+            B.pg_reset(g.handle)
+            B.pg_transient(g.handle, h, S, v_all=Vx)
+        dJ = 0.0
+        for a in chunks:
+            sp_p = torch.nn.functional.softplus(vref - Vp[a:a + 25] - margin, threshold=1e9)
+            sp_m = torch.nn.functional.softplus(vref - Vm[a:a + 25] - margin, threshold=1e9)
+            dJ += float(((sp_p - sp_m) * (sp_p + sp_m)).sum())
+        fd = dJ / (2.0 * eps)
+        ad = float((torch.tensor(sgn * net.r_g, device=dev) * gG).sum())
+        print(f"central difference {fd:.12e} adjoint {ad:.12e}")
+        assert fd == pytest.approx(ad, rel=1e-4)

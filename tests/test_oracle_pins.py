@@ -406,3 +406,23 @@ def test_adjoint_matches_central_differences():
         fd = (vals[0] - vals[1]) / (2 * d)
         ad = dG[k] if kind == "r" else dC[k]
         assert ad == pytest.approx(fd, rel=2e-5, abs=1e-9 * abs(J) / arr[k]), (kind, k)
+
+
+def test_adjoint_scaling_identity():
+    """Multiplying every conductance and capacitance by a maps v - Vdd to
+    (v - Vdd)/a when the supply is the only source (Eq. 2 with the DC point
+    G v_0 = b_0), so sum_e g_e dJ/dg_e + sum_k C_k dJ/dC_k equals
+    sum_{s,i} 2 softplus(u) sigmoid(u) (v_{s,i} - Vdd): a closed-form check of
+    every gradient entry at once, including the DC-point term (loads on at t = 0)."""
+    from oracle import adjoint, transient
+    net = pgsynth.config0(nx=9, ny=8)
+    net.i_v = net.i_v.copy() * 40.0
+    net.i_v[0::4] = 3e-3
+    h, S = 10e-12, 20
+    J, dG, dC = adjoint.gradients(net, h, S)
+    V, _ = transient.transient(net, h, S)
+    u = 1.0 - V[1:] - 0.05
+    rhs = float(np.sum(2.0 * adjoint.softplus(u) * adjoint.sigmoid(u) * (V[1:] - net.vdd[0])))
+    lhs = float(np.dot(net.r_g, dG) + np.dot(net.c_val, dC))
+    assert abs(V[0] - net.vdd[0]).max() > 1e-4          # the DC point is not trivial
+    assert lhs == pytest.approx(rhs, rel=1e-10)
