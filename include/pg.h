@@ -222,6 +222,58 @@ typedef struct pg_run_stats {
 pg_status pg_transient(pg_grid* g, double h, int32_t nsteps, const pg_output* out,
                        pg_run_stats* stats);
 
+/*
+ * Option search by timed trials (the paper leaves omega and the sweep schedule
+ * open, Section IV).  Builds the netlist once per structural candidate (lattice
+ * block sweeps per barrier k in {off, 1, 2, 3} when the netlist describes
+ * lattices and the precision is mixed; blocks per SM in {as many as fit, 1})
+ * and, on each, times trial_steps transient steps from the DC point (best of
+ * two runs, CUDA events) for every runtime candidate (inner reduction in {1e-3,
+ * 1e-2, 1e-1} when mixed; omega - 1 scaled by {1, 0.97, 0.94} below Young's
+ * value when omega is not fixed).  Every trial runs under the certified
+ * stopping rule of `base` (tol), so only time is compared.  `base` (NULL ->
+ * defaults) supplies every other field.  On success *best is `base` with
+ * lattice_sweeps, blocks_per_sm, inner_reduction and omega (0 = Young's value;
+ * a scaled value is tied to this h) set to the fastest candidate and *best_ms
+ * (may be NULL) to its trial time.  stream: cudaStream_t for the trials or
+ * NULL.  Errors: PG_ERR_INVALID_ARG, or the last failure when no candidate ran.
+ */
+pg_status pg_autotune(const pg_netlist* nl, const pg_options* base, double h, int32_t trial_steps, void* stream,
+                      pg_options* best, double* best_ms);
+
+/* Size in bytes of the device record pg_transient_async writes (dstats). */
+#define PG_ASYNC_STATS_BYTES 128
+
+/*
+ * pg_transient as pure stream-ordered work, for replay under a CUDA graph (the
+ * paper's Algorithm 1 loop as one persistent launch; the graph packaging has no
+ * counterpart in the paper).  Runs nsteps backward-Euler steps (Eq. 2 / Eq. 10)
+ * starting at step 0 from v0 (device, [n_nodes], caller numbering) with zero
+ * inductor currents; v0 = NULL puts every node at the supply voltage, which is
+ * the DC point when all loads are zero at t = 0 (needs a single supply level).
+ * Only memsets, kernel launches and device-to-device copies are issued on the
+ * grid's stream and nothing waits on the host, so the call can be captured
+ * (cudaStreamBeginCapture, torch.cuda.graph) and the graph replayed: each replay
+ * reads the source waveforms and element values current at replay time
+ * (pg_update_sources between replays), but the grid must be assembled for h
+ * beforehand (pg_transient(g, h, 0, NULL, NULL)) and must not be used by another
+ * call while a replay runs.  out: device pointers only (on_host = 0, no probes).
+ * dstats (device, PG_ASYNC_STATS_BYTES, may be NULL) receives the launch's
+ * statistics and error word; decode it with pg_async_stats.  The grid's host
+ * transient state is left undefined: the next pg_transient starts from the DC
+ * point.  Errors at the call: PG_ERR_INVALID_ARG, PG_ERR_CUDA.
+ */
+pg_status pg_transient_async(pg_grid* g, double h, int32_t nsteps, const double* v0, const pg_output* out,
+                             void* dstats);
+
+/*
+ * Decode a record written by pg_transient_async once the work that wrote it has
+ * finished (synchronise the stream the graph was replayed on first).  Returns
+ * the launch's status (PG_OK, PG_ERR_NOT_CONVERGED, PG_ERR_TIMEOUT); stats may be
+ * NULL (device_ms is 0: not timed).
+ */
+pg_status pg_async_stats(pg_grid* g, const void* dstats, pg_run_stats* stats);
+
 /* One step (pg_transient with nsteps = 1); v_out (device, [n_nodes]) may be NULL. */
 pg_status pg_step(pg_grid* g, double h, double* v_out, pg_run_stats* stats);
 

@@ -19,6 +19,8 @@ from .build import LIB
 PG_GROUND = -1
 STATUS = {0: "PG_OK", 1: "PG_ERR_INVALID_ARG", 2: "PG_ERR_FLOATING_NODE", 3: "PG_ERR_OOM",
           4: "PG_ERR_CUDA", 5: "PG_ERR_NOT_CONVERGED", 6: "PG_ERR_TIMEOUT", 7: "PG_ERR_UNSUPPORTED"}
+(PG_OK, PG_ERR_INVALID_ARG, PG_ERR_FLOATING_NODE, PG_ERR_OOM, PG_ERR_CUDA, PG_ERR_NOT_CONVERGED,
+ PG_ERR_TIMEOUT, PG_ERR_UNSUPPORTED) = range(8)
 PG_PREC_FP64, PG_PREC_MIXED = 0, 1
 PG_DEBUG_SKIP_ARRIVAL = 1
 
@@ -110,9 +112,13 @@ def lib(path: Optional[str] = None) -> C.CDLL:
     L.pg_update_values.argtypes = [vp, vp, vp, vp, C.c_int32]
     L.pg_adjoint.argtypes = [vp, C.c_double, C.c_int32, C.POINTER(pg_objective), C.c_int32, _f64p, vp, vp,
                              C.c_int32, C.POINTER(pg_run_stats)]
+    L.pg_transient_async.argtypes = [vp, C.c_double, C.c_int32, vp, C.POINTER(pg_output), vp]
+    L.pg_async_stats.argtypes = [vp, vp, C.POINTER(pg_run_stats)]
+    L.pg_autotune.argtypes = [C.POINTER(pg_netlist), C.POINTER(pg_options), C.c_double, C.c_int32, vp,
+                              C.POINTER(pg_options), _f64p]
     for name in ("pg_create_grid", "pg_set_stream", "pg_grid_info", "pg_set_state", "pg_get_state",
                  "pg_reset", "pg_update_sources", "pg_transient", "pg_step", "pg_solve", "pg_solve_noalloc",
-                 "pg_update_values", "pg_adjoint"):
+                 "pg_update_values", "pg_adjoint", "pg_transient_async", "pg_async_stats", "pg_autotune"):
         getattr(L, name).restype = C.c_int
     if path is None:
         _LIB = L
@@ -153,8 +159,8 @@ def pg_default_options(**over) -> pg_options:
     return o
 
 
-def pg_create_grid(net, opt: Optional[pg_options] = None):
-    """Create a grid from a ``pgsynth.Netlist``-like object; returns an opaque handle."""
+def _netlist(net):
+    """Marshal a ``pgsynth.Netlist``-like object into a ``pg_netlist`` (plus the arrays it points into)."""
     keep = []
 
     def arr(a, dt):
@@ -175,6 +181,12 @@ def pg_create_grid(net, opt: Optional[pg_options] = None):
     if lats:
         nl.n_lat = len(lats)
         nl.lat_desc = arr(np.asarray(lats, dtype=np.int32).reshape(-1), np.int32)
+    return nl, keep
+
+
+def pg_create_grid(net, opt: Optional[pg_options] = None):
+    """Create a grid from a ``pgsynth.Netlist``-like object; returns an opaque handle."""
+    nl, keep = _netlist(net)
     h = C.c_void_p()
     _check(lib().pg_create_grid(C.byref(nl), C.byref(opt) if opt is not None else None, C.byref(h)),
            "pg_create_grid")
@@ -233,6 +245,31 @@ def pg_transient_status(h, step_h: float, nsteps: int) -> tuple:
     return rc, st
 
 
+PG_ASYNC_STATS_BYTES = 128
+
+
+def pg_transient_async(h, step_h: float, nsteps: int, v0=None, v_all=None, il_all=None, vmin=None,
+                       vmin_node=None, dstats=None):
+    """Stream-ordered transient from step 0 (capturable into a CUDA graph); device buffers only."""
+    for name, b in (("v0", v0), ("v_all", v_all), ("il_all", il_all), ("vmin", vmin),
+                    ("vmin_node", vmin_node), ("dstats", dstats)):
+        if b is not None and not (hasattr(b, "data_ptr") and getattr(b, "is_cuda", False)):
+            raise TypeError(f"pg_transient_async: {name} must be a CUDA tensor")
+    out = pg_output()
+    out.on_host = 0
+    out.v_all = _ptr(v_all); out.il_all = _ptr(il_all); out.vmin = _ptr(vmin)
+    out.vmin_node = _ptr(vmin_node)
+    _check(lib().pg_transient_async(h, float(step_h), int(nsteps), _ptr(v0), C.byref(out), _ptr(dstats)),
+           "pg_transient_async")
+
+
+def pg_async_stats(h, dstats) -> tuple:
+    """``(status, stats)`` of a record written by :func:`pg_transient_async`."""
+    st = pg_run_stats()
+    rc = lib().pg_async_stats(h, _ptr(dstats), C.byref(st))
+    return rc, st
+
+
 def pg_step(h, step_h: float, v_out=None) -> pg_run_stats:
     st = pg_run_stats()
     _check(lib().pg_step(h, float(step_h), _ptr(v_out), C.byref(st)), "pg_step")
@@ -267,6 +304,24 @@ def pg_solve_noalloc(h, step_h: float, b, x, tol: float) -> pg_run_stats:
     _check(lib().pg_solve_noalloc(h, float(step_h), _ptr(b), _ptr(x), float(tol), C.byref(st)),
            "pg_solve_noalloc")
     return st
+
+
+def pg_autotune(net, step_h: float, trial_steps: int, stream=None, **base):
+    """Fastest options for ``net`` by timed trials; returns ``(pg_options, trial_ms)``."""
+    nl, keep = _netlist(net)
+    b = pg_default_options(**base)
+    best = pg_options()
+    ms = C.c_double()
+    _check(lib().pg_autotune(C.byref(nl), C.byref(b), float(step_h), int(trial_steps),
+                             None if stream is None else C.c_void_p(stream), C.byref(best), C.byref(ms)),
+           "pg_autotune")
+    del keep
+    return best, ms.value
+
+
+def options_dict(o: pg_options) -> dict:
+    """The fields of a ``pg_options`` as keyword arguments for :class:`Grid`."""
+    return {name: getattr(o, name) for name, _ in o._fields_}
 
 
 class Grid:

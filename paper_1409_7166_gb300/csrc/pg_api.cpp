@@ -307,14 +307,21 @@ RunParams pg::base_params(const pg_grid* g) {
 
 namespace {
 
-// One persistent launch; reads back the status word and statistics.
-pg_status run(pg_grid* g, const RunParams& rp, double* stats, float* ms) {
+// Clear the launch's control words (barrier, error flag, reduction slots); stream-ordered.
+pg_status clear_ctl(pg_grid* g) {
     CK(cudaMemsetAsync(g->dc.bar_count, 0, sizeof(unsigned), g->stream));
     CK(cudaMemsetAsync(g->dc.bar_gen, 0, sizeof(unsigned), g->stream));
     CK(cudaMemsetAsync(g->dc.err, 0, sizeof(int32_t), g->stream));
     CK(cudaMemsetAsync(g->dc.red, 0, kRedSlots * sizeof(unsigned long long), g->stream));
     if (g->dc.lat_R)
         CK(cudaMemsetAsync(g->dc.lat_R, 0, 2 * (size_t)g->dg.n_lats * sizeof(unsigned long long), g->stream));
+    return PG_OK;
+}
+
+// One persistent launch; reads back the status word and statistics.
+pg_status run(pg_grid* g, const RunParams& rp, double* stats, float* ms) {
+    pg_status s0 = clear_ctl(g);
+    if (s0) return s0;
     CK(cudaEventRecord(g->ev0, g->stream));
     CK(launch_persistent(g->mixed, g->dg, g->ds, g->dc, rp, g->blocks, g->threads, g->stream));
     CK(cudaEventRecord(g->ev1, g->stream));
@@ -907,6 +914,89 @@ pg_status pg_transient(pg_grid* g, double h, int32_t nsteps, const pg_output* ou
     cleanup();
     fill_stats(g, st, ms, stats);
     return s;
+}
+
+pg_status pg_transient_async(pg_grid* g, double h, int32_t nsteps, const double* v0, const pg_output* out,
+                             void* dstats) {
+    if (!g || nsteps < 1) return PG_ERR_INVALID_ARG;
+    const bool any_out = out && (out->v_all || out->il_all || out->vmin || out->vmin_node);
+    if (out && ((any_out && out->on_host) || out->n_probes > 0)) {
+        g_last_error = "pg_transient_async takes device outputs and no probes";
+        return PG_ERR_INVALID_ARG;
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(g->stream, &cap));
+    if (cap == cudaStreamCaptureStatusNone) {
+        // outside a capture, refuse pointers the device cannot address
+        const void* ptrs[] = {v0, out ? out->v_all : nullptr, out ? out->il_all : nullptr,
+                              out ? out->vmin : nullptr, out ? out->vmin_node : nullptr, dstats};
+        for (const void* p : ptrs) {
+            if (!p) continue;
+            cudaPointerAttributes a{};
+            if (cudaPointerGetAttributes(&a, p) != cudaSuccess ||
+                (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
+                cudaGetLastError();
+                g_last_error = "pg_transient_async: a buffer is not device memory";
+                return PG_ERR_INVALID_ARG;
+            }
+        }
+    }
+    pg_status s;
+    if (g->h != h) {
+        if (cap != cudaStreamCaptureStatusNone) {
+            g_last_error = "h is not assembled: call pg_transient(g, h, 0, ...) before capturing";
+            return PG_ERR_INVALID_ARG;
+        }
+        if ((s = prepare_h(g, h))) return s;
+    }
+    const NetCopy& nc = g->nc;
+    if (!v0) {
+        bool one = nc.p > 0;
+        for (int k = 1; k < nc.p && one; ++k) one = nc.vdd[k] == nc.vdd[0];
+        if (!one) {
+            g_last_error = "v0 = NULL needs a single supply level";
+            return PG_ERR_INVALID_ARG;
+        }
+    }
+    if ((s = set_state_device(g, v0, v0 ? 0.0 : nc.vdd[0], nullptr, 0))) return s;
+    RunParams rp = base_params(g);
+    rp.mode = kModeTransient;
+    rp.nsteps = nsteps;
+    rp.step0 = 0;
+    rp.have_prev = 0;
+    if (out) {
+        rp.v_all = out->v_all;
+        rp.il_all = g->P.n_l ? out->il_all : nullptr;
+        rp.vmin = out->vmin;
+        rp.vmin_node = out->vmin_node;
+    }
+    g->has_state = false;          // the host does not follow the device state of this launch
+    if ((s = clear_ctl(g))) return s;
+    CK(launch_persistent(g->mixed, g->dg, g->ds, g->dc, rp, g->blocks, g->threads, g->stream));
+    if (dstats) {
+        CK(cudaMemcpyAsync(dstats, g->dc.stats, kStatCount * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+        CK(cudaMemcpyAsync(static_cast<char*>(dstats) + kStatCount * sizeof(double), g->dc.err, sizeof(int32_t),
+                           cudaMemcpyDeviceToDevice, g->stream));
+    }
+    return PG_OK;
+}
+
+pg_status pg_async_stats(pg_grid* g, const void* dstats, pg_run_stats* stats) {
+    if (!g || !dstats) return PG_ERR_INVALID_ARG;
+    static_assert(kStatCount * sizeof(double) + sizeof(int32_t) <= PG_ASYNC_STATS_BYTES, "stats record size");
+    unsigned char rec[PG_ASYNC_STATS_BYTES];
+    CK(cudaMemcpyAsync(rec, dstats, kStatCount * sizeof(double) + sizeof(int32_t), cudaMemcpyDeviceToHost,
+                       g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    double st[kStatCount];
+    int32_t err = 0;
+    std::memcpy(st, rec, sizeof(st));
+    std::memcpy(&err, rec + sizeof(st), sizeof(err));
+    fill_stats(g, st, 0.f, stats);
+    if (err == PG_ERR_TIMEOUT) { g_last_error = "device barrier timed out"; return PG_ERR_TIMEOUT; }
+    if (err == PG_ERR_NOT_CONVERGED) { g_last_error = "relaxation did not converge"; return PG_ERR_NOT_CONVERGED; }
+    if (err != 0) { g_last_error = "device error"; return PG_ERR_CUDA; }
+    return PG_OK;
 }
 
 pg_status pg_step(pg_grid* g, double h, double* v_out, pg_run_stats* stats) {

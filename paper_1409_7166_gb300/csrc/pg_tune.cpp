@@ -1,0 +1,92 @@
+// pg_autotune: choose solver and launch options for one netlist by timed trials.
+//
+// The paper fixes neither the relaxation factor nor the parallel schedule
+// (Section IV leaves omega and the sweep order open), and the best choice
+// depends on the grid: its size and layer count decide whether the column-block
+// inner solve pays for its ghost zones, how far the FP32 inner solve should
+// reduce the defect before the next FP64 residual pass, and whether a slightly
+// under-relaxed omega beats Young's value when the Jacobi radius is only
+// estimated.  Every candidate runs under the same certified stopping rule, so
+// any candidate that converges meets the tolerance and the search only compares
+// time.
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "pg_grid.h"
+
+namespace {
+
+constexpr double kInnerReductions[] = {1e-3, 1e-2, 1e-1};
+constexpr double kOmegaScales[] = {1.0, 0.97, 0.94};   // applied to omega - 1
+
+}  // namespace
+
+extern "C" pg_status pg_autotune(const pg_netlist* nl, const pg_options* base, double h, int32_t trial_steps,
+                                 void* stream, pg_options* best, double* best_ms) {
+    if (!nl || !best || trial_steps < 1 || !(h > 0.0) || !std::isfinite(h)) return PG_ERR_INVALID_ARG;
+    pg_options b0;
+    if (base) b0 = *base;
+    else pg_default_options(&b0);
+    const bool mixed = b0.precision == PG_PREC_MIXED;
+    const bool lattice = mixed && (nl->n_lat > 0 || (nl->lat_nx > 0 && nl->lat_ny > 0 && nl->lat_nl > 0));
+    std::vector<int32_t> ks = lattice ? std::vector<int32_t>{-1, 1, 2, 3} : std::vector<int32_t>{b0.lattice_sweeps};
+    const std::vector<int32_t> bps = {0, 1};
+    std::vector<double> reds;
+    if (mixed) reds.assign(std::begin(kInnerReductions), std::end(kInnerReductions));
+    else reds.push_back(b0.inner_reduction);
+
+    double best_t = INFINITY;
+    pg_options win = b0;
+    pg_status last = PG_OK;
+    for (int32_t k : ks) {
+        for (int32_t bp : bps) {
+            pg_options o = b0;
+            o.lattice_sweeps = k;
+            o.blocks_per_sm = bp;
+            pg_grid* g = nullptr;
+            pg_status s = pg_create_grid(nl, &o, &g);
+            if (s) { last = s; continue; }
+            if (stream) pg_set_stream(g, stream);
+            pg_run_stats st;
+            if ((s = pg_transient(g, h, 0, nullptr, &st))) {   // assemble h: omega, kappa, stopping rule
+                last = s;
+                pg_destroy(g);
+                continue;
+            }
+            const double w0 = g->omega;
+            const bool fixed_omega = b0.omega > 0.0 || !(w0 > 1.0);
+            for (double red : reds) {
+                for (double sc : kOmegaScales) {
+                    if (fixed_omega && sc != 1.0) continue;
+                    g->opt.inner_reduction = red;
+                    g->omega = 1.0 + (w0 - 1.0) * sc;
+                    double t = INFINITY;
+                    for (int rep = 0; rep < 2 && !s; ++rep) {   // first run warms caches and clocks
+                        if ((s = pg_reset(g))) break;
+                        if ((s = pg_transient(g, h, trial_steps, nullptr, &st))) break;
+                        t = std::min(t, (double)st.device_ms);
+                    }
+                    if (s) {
+                        last = s;
+                        s = PG_OK;
+                        continue;
+                    }
+                    if (t < best_t) {
+                        best_t = t;
+                        win = o;
+                        win.inner_reduction = red;
+                        win.omega = sc == 1.0 ? b0.omega : g->omega;
+                    }
+                }
+            }
+            g->omega = w0;
+            pg_destroy(g);
+        }
+    }
+    if (!std::isfinite(best_t)) return last ? last : PG_ERR_NOT_CONVERGED;
+    *best = win;
+    if (best_ms) *best_ms = best_t;
+    return PG_OK;
+}
