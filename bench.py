@@ -106,7 +106,7 @@ class ClockSampler:
 
 
 def algorithmic_bytes(st, n, mn, n_src, mixed: bool, nsteps: int, extrap: bool = True) -> float:
-    """Bytes the method must move for the work recorded in ``st`` (see DESIGN.md).
+    """Bytes the method must move for the work recorded in ``st``.
 
     per node-sweep (FP32 sweep on the correction): 16 + 4 m/n  (delta r/w, r, 1/D, each weight once)
     per node-sweep (FP32 column-block sweep):      20 + 4 m/n  (the block's two Thomas factors

@@ -150,6 +150,13 @@ const char* pg_last_error(void);
 /* Order subsequent work on this cudaStream_t (NULL = legacy default stream). */
 pg_status pg_set_stream(pg_grid* g, void* stream);
 
+/*
+ * Connected components: sub-circuits that share no element (Section III-B,
+ * Fig. 1), numbered in the order of their smallest node id.  *n_comp receives
+ * the count; comp_of (host, [n_nodes], may be NULL) each node's component.
+ */
+pg_status pg_grid_components(const pg_grid* g, int32_t* n_comp, int32_t* comp_of);
+
 /* Node count, inductor count, colour count and permuted (padded) node count. */
 pg_status pg_grid_info(const pg_grid* g, int32_t* n_nodes, int32_t* n_inductors,
                        int32_t* n_colours, int32_t* n_padded);
@@ -186,6 +193,8 @@ typedef struct pg_output {
     int32_t n_probes;
     const int32_t* probes;/* [n_probes] node ids (same memory kind as the outputs) */
     double* probe_v;      /* [nsteps x n_probes] */
+    double* comp_vmin;    /* [nsteps x n_components] smallest voltage of each connected component
+                             (independent sub-circuit, Fig. 1; numbering of pg_grid_components) */
 } pg_output;
 
 typedef struct pg_run_stats {

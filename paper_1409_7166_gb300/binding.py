@@ -51,7 +51,7 @@ class pg_options(C.Structure):
 class pg_output(C.Structure):
     _fields_ = [("on_host", C.c_int32), ("v_all", C.c_void_p), ("il_all", C.c_void_p),
                 ("vmin", C.c_void_p), ("vmin_node", C.c_void_p), ("n_probes", C.c_int32),
-                ("probes", C.c_void_p), ("probe_v", C.c_void_p)]
+                ("probes", C.c_void_p), ("probe_v", C.c_void_p), ("comp_vmin", C.c_void_p)]
 
 
 class pg_objective(C.Structure):
@@ -102,6 +102,7 @@ def lib(path: Optional[str] = None) -> C.CDLL:
     L.pg_set_stream.argtypes = [vp, vp]
     L.pg_grid_info.argtypes = [vp, _i32p, _i32p, _i32p, _i32p]
     L.pg_set_state.argtypes = [vp, vp, vp, C.c_int64, C.c_int32]
+    L.pg_grid_components.argtypes = [vp, _i32p, vp]
     L.pg_get_state.argtypes = [vp, vp, vp, _i64p, C.c_int32]
     L.pg_reset.argtypes = [vp]
     L.pg_update_sources.argtypes = [vp, vp, vp, C.c_int32]
@@ -118,7 +119,7 @@ def lib(path: Optional[str] = None) -> C.CDLL:
                               C.POINTER(pg_options), _f64p]
     for name in ("pg_create_grid", "pg_set_stream", "pg_grid_info", "pg_set_state", "pg_get_state",
                  "pg_reset", "pg_update_sources", "pg_transient", "pg_step", "pg_solve", "pg_solve_noalloc",
-                 "pg_update_values", "pg_adjoint", "pg_transient_async", "pg_async_stats", "pg_autotune"):
+                 "pg_update_values", "pg_adjoint", "pg_transient_async", "pg_async_stats", "pg_autotune", "pg_grid_components"):
         getattr(L, name).restype = C.c_int
     if path is None:
         _LIB = L
@@ -207,6 +208,14 @@ def pg_grid_info(h):
     return dict(n_nodes=n.value, n_inductors=nl.value, n_colours=nc.value, n_padded=npad.value)
 
 
+def pg_grid_components(h, n_nodes: Optional[int] = None):
+    """``(n_components, comp_of)``; ``comp_of`` (node -> component) when ``n_nodes`` is given."""
+    nc = C.c_int32()
+    comp = None if n_nodes is None else np.zeros(int(n_nodes), dtype=np.int32)
+    _check(lib().pg_grid_components(h, C.byref(nc), _ptr(comp)), "pg_grid_components")
+    return nc.value, comp
+
+
 def pg_set_state(h, v, il=None, step: int = 0):
     _check(lib().pg_set_state(h, _ptr(v), _ptr(il), int(step), _on_host(v, il)), "pg_set_state")
 
@@ -226,13 +235,14 @@ def pg_update_sources(h, i_t=None, i_v=None):
 
 
 def pg_transient(h, step_h: float, nsteps: int, v_all=None, il_all=None, vmin=None, vmin_node=None,
-                 probes=None, probe_v=None) -> pg_run_stats:
+                 probes=None, probe_v=None, comp_vmin=None) -> pg_run_stats:
     out = pg_output()
-    out.on_host = _on_host(v_all, il_all, vmin, vmin_node, probes, probe_v)
+    out.on_host = _on_host(v_all, il_all, vmin, vmin_node, probes, probe_v, comp_vmin)
     out.v_all = _ptr(v_all); out.il_all = _ptr(il_all); out.vmin = _ptr(vmin)
     out.vmin_node = _ptr(vmin_node)
     out.n_probes = 0 if probes is None else int(len(probes))
     out.probes = _ptr(probes); out.probe_v = _ptr(probe_v)
+    out.comp_vmin = _ptr(comp_vmin)
     st = pg_run_stats()
     _check(lib().pg_transient(h, float(step_h), int(nsteps), C.byref(out), C.byref(st)), "pg_transient")
     return st
@@ -249,16 +259,17 @@ PG_ASYNC_STATS_BYTES = 128
 
 
 def pg_transient_async(h, step_h: float, nsteps: int, v0=None, v_all=None, il_all=None, vmin=None,
-                       vmin_node=None, dstats=None):
+                       vmin_node=None, comp_vmin=None, dstats=None):
     """Stream-ordered transient from step 0 (capturable into a CUDA graph); device buffers only."""
     for name, b in (("v0", v0), ("v_all", v_all), ("il_all", il_all), ("vmin", vmin),
-                    ("vmin_node", vmin_node), ("dstats", dstats)):
+                    ("vmin_node", vmin_node), ("comp_vmin", comp_vmin), ("dstats", dstats)):
         if b is not None and not (hasattr(b, "data_ptr") and getattr(b, "is_cuda", False)):
             raise TypeError(f"pg_transient_async: {name} must be a CUDA tensor")
     out = pg_output()
     out.on_host = 0
     out.v_all = _ptr(v_all); out.il_all = _ptr(il_all); out.vmin = _ptr(vmin)
     out.vmin_node = _ptr(vmin_node)
+    out.comp_vmin = _ptr(comp_vmin)
     _check(lib().pg_transient_async(h, float(step_h), int(nsteps), _ptr(v0), C.byref(out), _ptr(dstats)),
            "pg_transient_async")
 

@@ -146,6 +146,17 @@ pg_status alloc_device(pg_grid* g) {
     d.ind_hl = ind_hl; d.ind_ptr = ind_ptr; d.ind_idx = ind_idx; d.vdd = vdd;
     d.w64 = w64; d.D64 = D64; d.invD64 = invD64; d.ch = ch; d.cinj = cinj; d.w32 = w32; d.invD32 = invD32;
     pg_status s;
+    {
+        // component of each permuted node (independent sub-circuits, Fig. 1)
+        std::vector<int32_t> nc(np, -1);
+        for (int i = 0; i < np; ++i)
+            if (P.orig[i] >= 0) nc[i] = P.comp_of[P.orig[i]];
+        int32_t* node_comp = g->alloc<int32_t>(np);
+        if (!node_comp) return PG_ERR_OOM;
+        if ((s = upload(g, node_comp, nc))) return s;
+        d.n_comp = P.n_comp;
+        d.node_comp = node_comp;
+    }
     if (d.lwE &&
         ((s = upload(g, const_cast<int32_t*>(d.lat_info), lat_info)) ||
          (s = upload(g, const_cast<int32_t*>(d.lat_tile0), lat_tile0)) ||
@@ -734,6 +745,13 @@ pg_status pg_grid_info(const pg_grid* g, int32_t* n, int32_t* nl, int32_t* ncol,
     return PG_OK;
 }
 
+pg_status pg_grid_components(const pg_grid* g, int32_t* n_comp, int32_t* comp_of) {
+    if (!g) return PG_ERR_INVALID_ARG;
+    if (n_comp) *n_comp = g->P.n_comp;
+    if (comp_of) std::memcpy(comp_of, g->P.comp_of.data(), g->P.n * sizeof(int32_t));
+    return PG_OK;
+}
+
 pg_status pg_set_state(pg_grid* g, const double* v, const double* il, int64_t step, int32_t on_host) {
     if (!g) return PG_ERR_INVALID_ARG;
     if (!v) {
@@ -869,6 +887,7 @@ pg_status pg_transient(pg_grid* g, double h, int32_t nsteps, const pg_output* ou
         rp.il_all = P.n_l ? (double*)stage(out->il_all, (size_t)nsteps * P.n_l * sizeof(double)) : nullptr;
         rp.vmin = (double*)stage(out->vmin, (size_t)nsteps * sizeof(double));
         rp.vmin_node = (int32_t*)stage(out->vmin_node, (size_t)nsteps * sizeof(int32_t));
+        rp.comp_vmin = (double*)stage(out->comp_vmin, (size_t)nsteps * P.n_comp * sizeof(double));
         if (out->n_probes > 0 && out->probes && out->probe_v) {
             std::vector<int32_t> pr(out->n_probes);
             if (host) std::memcpy(pr.data(), out->probes, pr.size() * sizeof(int32_t));
@@ -887,7 +906,10 @@ pg_status pg_transient(pg_grid* g, double h, int32_t nsteps, const pg_output* ou
             rp.probes_perm = probes_perm;
             rp.probe_v = (double*)stage(out->probe_v, (size_t)nsteps * out->n_probes * sizeof(double));
         }
-        if ((out->v_all && !rp.v_all) || (out->vmin && !rp.vmin)) { cleanup(); return PG_ERR_OOM; }
+        if ((out->v_all && !rp.v_all) || (out->vmin && !rp.vmin) || (out->comp_vmin && !rp.comp_vmin)) {
+            cleanup();
+            return PG_ERR_OOM;
+        }
     }
     double st[kStatCount];
     float ms = 0.f;
@@ -910,6 +932,7 @@ pg_status pg_transient(pg_grid* g, double h, int32_t nsteps, const pg_output* ou
         back(out->vmin, rp.vmin, (size_t)done * sizeof(double));
         back(out->vmin_node, rp.vmin_node, (size_t)done * sizeof(int32_t));
         back(out->probe_v, rp.probe_v, (size_t)done * rp.n_probes * sizeof(double));
+        back(out->comp_vmin, rp.comp_vmin, (size_t)done * P.n_comp * sizeof(double));
     }
     cleanup();
     fill_stats(g, st, ms, stats);
@@ -919,7 +942,7 @@ pg_status pg_transient(pg_grid* g, double h, int32_t nsteps, const pg_output* ou
 pg_status pg_transient_async(pg_grid* g, double h, int32_t nsteps, const double* v0, const pg_output* out,
                              void* dstats) {
     if (!g || nsteps < 1) return PG_ERR_INVALID_ARG;
-    const bool any_out = out && (out->v_all || out->il_all || out->vmin || out->vmin_node);
+    const bool any_out = out && (out->v_all || out->il_all || out->vmin || out->vmin_node || out->comp_vmin);
     if (out && ((any_out && out->on_host) || out->n_probes > 0)) {
         g_last_error = "pg_transient_async takes device outputs and no probes";
         return PG_ERR_INVALID_ARG;
@@ -929,7 +952,8 @@ pg_status pg_transient_async(pg_grid* g, double h, int32_t nsteps, const double*
     if (cap == cudaStreamCaptureStatusNone) {
         // outside a capture, refuse pointers the device cannot address
         const void* ptrs[] = {v0, out ? out->v_all : nullptr, out ? out->il_all : nullptr,
-                              out ? out->vmin : nullptr, out ? out->vmin_node : nullptr, dstats};
+                              out ? out->vmin : nullptr, out ? out->vmin_node : nullptr,
+                              out ? out->comp_vmin : nullptr, dstats};
         for (const void* p : ptrs) {
             if (!p) continue;
             cudaPointerAttributes a{};
@@ -969,6 +993,7 @@ pg_status pg_transient_async(pg_grid* g, double h, int32_t nsteps, const double*
         rp.il_all = g->P.n_l ? out->il_all : nullptr;
         rp.vmin = out->vmin;
         rp.vmin_node = out->vmin_node;
+        rp.comp_vmin = out->comp_vmin;
     }
     g->has_state = false;          // the host does not follow the device state of this launch
     if ((s = clear_ctl(g))) return s;

@@ -119,6 +119,9 @@ struct DevGrid {
     const float* lwU;        // weight to (x, y, l+1)
     const float* lm;         // column block (via couplings): Thomas multiplier u_{l-1} / d'_{l-1} (0 for l = 0)
     const float* lip;        // column block: inverse Thomas pivot 1 / d'_l
+    // connected components (independent sub-circuits, Fig. 1)
+    int32_t n_comp;
+    const int32_t* node_comp;   // [n_pad] component of each permuted node, -1 for padding
 };
 
 enum Mode : int32_t { kModeTransient = 0, kModeSolve = 1 };
@@ -176,6 +179,7 @@ struct RunParams {
     const int32_t* probes_perm;
     double* probe_v;
     double* solve_out;        // kModeSolve: x in caller numbering
+    double* comp_vmin;        // [nsteps x n_comp] smallest voltage per component (keys until converted)
     // kModeSolve extras
     const double* x0;                              // initial guess (permuted) or null (x = 0)
     const unsigned long long* target_scale;        // if set, target *= this double (device)

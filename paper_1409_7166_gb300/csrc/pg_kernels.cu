@@ -946,6 +946,20 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
         }
     };
 
+    // per-component minima: order keys, all rows set to the largest key before the first
+    // barrier; row s receives atomics in step s's post phase and is turned into volts
+    // after the barrier that ends step s
+    unsigned long long* const comp_key = reinterpret_cast<unsigned long long*>(rp.comp_vmin);
+    if (comp_key)
+        for (long long q = gtid; q < (long long)rp.nsteps * g.n_comp; q += nthreads) comp_key[q] = ~0ull;
+    auto finalize_comp = [&](int sl) {
+        if (comp_key)
+            for (int q = gtid; q < g.n_comp; q += nthreads) {
+                const long long e = (long long)sl * g.n_comp + q;
+                rp.comp_vmin[e] = key_value(comp_key[e]);
+            }
+    };
+
     const double target = rp.target_scale ? rp.target * __longlong_as_double((long long)*rp.target_scale) : rp.target;
     int vL = rp.cur, vP = rp.prev, vF = 3 - rp.cur - rp.prev;
     bool have_prev = rp.have_prev != 0;
@@ -964,7 +978,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
         const double t = (double)sabs * rp.h;
         const bool extrap = rp.mode == kModeTransient && rp.warm_extrap && have_prev;
         int dsel = 0;
-        if (sl > 0) finalize_vmin(sl - 1);
+        if (sl > 0) { finalize_vmin(sl - 1); finalize_comp(sl - 1); }
 
         // ---- phase A: RHS + warm start + residual, all colours
         double mon = 0.0;
@@ -1096,6 +1110,27 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
         if (rp.probe_v)
             for (int k = gtid; k < rp.n_probes; k += nthreads)
                 rp.probe_v[(long long)sl * rp.n_probes + k] = vnew[rp.probes_perm[k]];
+        if (comp_key) {
+            // warp-aggregated: one atomic when a warp's 32 nodes lie in one component
+            unsigned long long* row = comp_key + (long long)sl * g.n_comp;
+            for (int base = gwarp * 32; base < g.n_pad; base += nwarps * 32) {
+                const int i = base + lane;
+                const int c = i < g.n_pad ? __ldg(g.node_comp + i) : -1;
+                unsigned long long k = c >= 0 ? order_key(vnew[i]) : ~0ull;
+                int chi = c, clo = c >= 0 ? c : 0x7fffffff;
+                for (int o = 16; o; o >>= 1) {
+                    chi = max(chi, __shfl_xor_sync(kFull, chi, o));
+                    clo = min(clo, __shfl_xor_sync(kFull, clo, o));
+                }
+                if (chi < 0) continue;
+                if (clo == chi) {
+                    for (int o = 16; o; o >>= 1) k = min(k, __shfl_xor_sync(kFull, k, o));
+                    if (lane == 0) atomicMin(row + chi, k);
+                } else if (c >= 0) {
+                    atomicMin(row + c, k);
+                }
+            }
+        }
         if (rp.vmin) {
             __shared__ unsigned long long s_k[32];
             __shared__ int s_a[32];
@@ -1137,7 +1172,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
         have_prev = true;
         if (!barrier(false, 0.0).ok) { publish(-1); return; }
     }
-    if (rp.nsteps > 0) finalize_vmin(rp.nsteps - 1);
+    if (rp.nsteps > 0) { finalize_vmin(rp.nsteps - 1); finalize_comp(rp.nsteps - 1); }
     publish(-1);
 }
 
