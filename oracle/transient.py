@@ -28,7 +28,10 @@ source of value ``i_l(0)`` (default 0):
 
 The first transient step is an ordinary backward-Euler step from
 ``(v(0), i_l(0))``; the paper's explicit half-step (its step 2) is replaced by
-this consistent BE step.
+this consistent BE step.  The paper's own three-step procedure (DC with the
+capacitors as voltage sources, a forward update of ``v_c`` and ``i_l``, DC at
+``h``), which yields the two levels ``v(0)``, ``v(h)`` of the three-level
+form, is :func:`paper_initial_conditions`.
 
 Solves are direct: a dense Cholesky for tiny systems, otherwise a sparse LU
 factorisation (SuperLU, symmetric minimum-degree ordering) computed once per
@@ -88,8 +91,11 @@ def dc_operating_point(net, mats: Optional[NodalMatrices] = None, il0=None, t: f
 
 
 def simulate(net, h: float, nsteps: int, v0=None, il0=None,
-             mats: Optional[NodalMatrices] = None) -> Iterator[Tuple[int, np.ndarray, np.ndarray]]:
-    """Yield ``(s, v(s), i_l(s))`` for ``s = 0 .. nsteps`` (explicit-i_l form)."""
+             mats: Optional[NodalMatrices] = None, s0: int = 0) -> Iterator[Tuple[int, np.ndarray, np.ndarray]]:
+    """Yield ``(s, v(s), i_l(s))`` for ``s = 0 .. nsteps`` (explicit-i_l form).
+
+    ``s0`` shifts the time axis: the given state is the one at ``t = s0 h`` and
+    step ``s`` lands at ``t = (s0 + s) h``."""
     mats = mats or nodal_matrices(net)
     m_l = mats.A_l.shape[0]
     il = np.zeros(m_l) if il0 is None else np.asarray(il0, dtype=np.float64).copy()
@@ -100,7 +106,7 @@ def simulate(net, h: float, nsteps: int, v0=None, il0=None,
     Ch = mats.C / h
     const = source_terms(mats, h)
     for s in range(1, nsteps + 1):
-        t = s * h
+        t = (s0 + s) * h
         rhs = Ch @ v - load_current(net, mats, t) + const
         if m_l:
             rhs -= mats.A_l.T @ il
@@ -110,10 +116,10 @@ def simulate(net, h: float, nsteps: int, v0=None, il0=None,
         yield s, v, il
 
 
-def transient(net, h: float, nsteps: int, v0=None, il0=None) -> Tuple[np.ndarray, np.ndarray]:
+def transient(net, h: float, nsteps: int, v0=None, il0=None, s0: int = 0) -> Tuple[np.ndarray, np.ndarray]:
     """Full waveforms ``V[s, node]`` and ``IL[s, inductor]``, ``s = 0..nsteps``."""
     vs, ils = [], []
-    for _, v, il in simulate(net, h, nsteps, v0, il0):
+    for _, v, il in simulate(net, h, nsteps, v0, il0, s0=s0):
         vs.append(v); ils.append(il)
     return np.stack(vs), np.stack(ils)
 
@@ -137,3 +143,71 @@ def simulate_three_level(net, h: float, nsteps: int, v0: np.ndarray, v1: np.ndar
         vn = solver.solve(rhs)
         yield s, vn
         vm, vc = vc, vn
+
+
+def _dc_with_fixed_caps(mats: NodalMatrices, net, t: float, v_cap: np.ndarray, capped: np.ndarray,
+                        il: np.ndarray):
+    """One DC analysis of the initial-condition procedure (Section IV-B, steps 1
+    and 3): every node that carries a capacitor is held at ``v_cap`` (the
+    capacitors act as voltage sources), every inductor acts as a current source
+    of value ``il``; the remaining nodes solve their rows of
+    ``G v = -G_s v_d - A_i^T I_s(t) - A_l^T i_l``.  Returns ``v`` and the
+    capacitor currents ``i_c = -(G v + G_s v_d + A_i^T I_s(t) + A_l^T i_l)``
+    (zero on nodes without a capacitor)."""
+    n = mats.n
+    rest = -(mats.G_s @ mats.vd) - load_current(net, mats, t)
+    if mats.A_l.shape[0]:
+        rest = rest - mats.A_l.T @ il
+    v = np.where(capped, v_cap, 0.0)
+    free = ~capped
+    if free.any():
+        G = mats.G.tocsr()
+        Gff = G[free][:, free]
+        Gfc = G[free][:, capped]
+        b = rest[free] - Gfc @ v[capped]
+        v[free] = DirectSolver(Gff.tocsc()).solve(b)
+    i_c = np.where(capped, -(mats.G @ v) + rest, 0.0)
+    return v, i_c
+
+
+def paper_initial_conditions(net, h: float, vc0=None, il0=None, mats: Optional[NodalMatrices] = None):
+    """The three-step initial-condition procedure of Section IV-B.
+
+    1. DC at t = 0 with capacitors as voltage sources ``v_c(0)`` and inductors
+       as current sources ``i_l(0)``: gives ``v(0)``, the capacitor currents
+       ``i_c(0)`` and the inductor voltages ``v_l(0) = A_l v(0) + A_ls v_d``.
+    2. ``v_c(h) = v_c(0) + h i_c(0) / C`` and ``i_l(h) = i_l(0) + h v_l(0) / L``.
+    3. DC at t = h with capacitors as voltage sources ``v_c(h)`` and inductors
+       as current sources ``i_l(h)``: gives ``v(h)``.
+
+    ``vc0`` holds one voltage per capacitor element (netlist order; parallel
+    capacitors on one node must agree); None takes the DC operating point with
+    the capacitors open.  ``il0`` defaults to zero.  Returns
+    ``(v(0), v(h), i_l(h))``, the two levels the three-level form (Eq. 11)
+    starts from, with the inductor currents the explicit form needs."""
+    mats = mats or nodal_matrices(net)
+    n = mats.n
+    m_l = mats.A_l.shape[0]
+    il = np.zeros(m_l) if il0 is None else np.asarray(il0, dtype=np.float64).copy()
+    cdiag = mats.C.diagonal()
+    capped = cdiag > 0.0
+    ca, cb = np.asarray(net.c_a), np.asarray(net.c_b)
+    cnode = np.where(ca >= 0, ca, cb)
+    if vc0 is None:
+        vdc = dc_operating_point(net, mats, il)
+        v_cap = np.where(capped, vdc, 0.0)
+    else:
+        vc0 = np.asarray(vc0, dtype=np.float64)
+        v_cap = np.zeros(n)
+        v_cap[cnode[::-1]] = vc0[::-1]          # the first capacitor of a node wins
+        if not np.allclose(v_cap[cnode], vc0, rtol=0.0, atol=0.0):
+            raise ValueError("parallel capacitors on one node need one voltage")
+    v0, i_c = _dc_with_fixed_caps(mats, net, 0.0, v_cap, capped, il)
+    if m_l:
+        v_l = mats.A_l @ v0 + mats.A_ls @ mats.vd
+        il1 = il + h * mats.Ldiag_inv * v_l
+    else:
+        il1 = il
+    v_cap1 = np.where(capped, v_cap + h * np.divide(i_c, cdiag, out=np.zeros(n), where=capped), 0.0)
+    v1, _ = _dc_with_fixed_caps(mats, net, h, v_cap1, capped, il1)
+    return v0, v1, il1

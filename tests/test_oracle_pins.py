@@ -426,3 +426,69 @@ def test_adjoint_scaling_identity():
     lhs = float(np.dot(net.r_g, dG) + np.dot(net.c_val, dC))
     assert abs(V[0] - net.vdd[0]).max() > 1e-4          # the DC point is not trivial
     assert lhs == pytest.approx(rhs, rel=1e-10)
+
+
+# ---------------------------------------------------------------- initial conditions of Section IV-B
+
+def test_paper_initial_conditions_capped_and_free_node():
+    """Node 0 carries C and a pad G0; node 1 has no capacitor, joins node 0
+    through g, has a pad g2 and a load I1 (constant) -- solved by hand:
+      step 1: v1 = (g vc0 + g2 Vdd - I1) / (g + g2),
+              i_c = -(G0 (vc0 - Vdd) + g (vc0 - v1))
+      step 2: vc(h) = vc0 + h i_c / C
+      step 3: v1(h) = (g vc(h) + g2 Vdd - I1) / (g + g2), v0(h) = vc(h)."""
+    G0, g, g2, C, I1, vdd, vc0, h = 6.0, 1.5, 0.7, 40e-15, 2e-3, 1.0, 0.93, 10e-12
+    net = make_netlist(2, [vdd], R=[(0, S(0), G0), (0, 1, g), (1, S(0), g2)], C=[(0, GROUND, C)],
+                       I=[(1, GROUND, [0.0], [I1])])
+    v0, v1, il1 = transient.paper_initial_conditions(net, h, vc0=[vc0])
+    f0 = (g * vc0 + g2 * vdd - I1) / (g + g2)
+    ic = -(G0 * (vc0 - vdd) + g * (vc0 - f0))
+    vch = vc0 + h * ic / C
+    f1 = (g * vch + g2 * vdd - I1) / (g + g2)
+    np.testing.assert_allclose(v0, [vc0, f0], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(v1, [vch, f1], rtol=0, atol=1e-12)
+    assert il1.size == 0
+
+
+def test_paper_initial_conditions_lc_node():
+    """C to ground and L to Vdd on one node, load I(t) ramping from I0 at t = 0:
+    i_c(0) = -(i_l(0) + I0) (the inductor and the load both draw from the node),
+    v(h) = vc0 + h i_c(0) / C, i_l(h) = i_l(0) + h (vc0 - Vdd) / L."""
+    C, Lh, vdd, vc0, il0, I0, h = 50e-15, 4e-12, 1.0, 0.97, 3e-4, 1e-4, 2e-12
+    net = make_netlist(1, [vdd], C=[(0, GROUND, C)], L=[(0, S(0), Lh)],
+                       I=[(0, GROUND, [0.0, 1e-9], [I0, 0.0])])
+    v0, v1, il1 = transient.paper_initial_conditions(net, h, vc0=[vc0], il0=[il0])
+    ic = -(il0 + I0)
+    np.testing.assert_allclose(v0, [vc0], rtol=0, atol=0)
+    np.testing.assert_allclose(v1, [vc0 + h * ic / C], rtol=1e-15, atol=1e-15)
+    np.testing.assert_allclose(il1, [il0 + h * (vc0 - vdd) / Lh], rtol=1e-14, atol=0)
+
+
+def test_paper_initial_conditions_consistent_dc_state_is_stationary():
+    """From the DC operating point (capacitors open, the default v_c(0)) with no
+    load at t = 0 and t = h, nothing moves: v(h) = v(0) and i_l(h) = i_l(0);
+    on an RLC grid with loads off until later, both levels are the supply."""
+    net = pgsynth.config2(nx=7, ny=6)
+    h = net.meta["h"]
+    I = pwl.pwl_values(net.i_ptr, net.i_t, net.i_v, 0.0)
+    Ih = pwl.pwl_values(net.i_ptr, net.i_t, net.i_v, h)
+    net.i_v = net.i_v.copy()
+    net.i_v[:] = np.where(np.repeat((I != 0) | (Ih != 0), np.diff(net.i_ptr)), 0.0, net.i_v)
+    v0, v1, il1 = transient.paper_initial_conditions(net, h)
+    np.testing.assert_allclose(v0, net.vdd[0], rtol=0, atol=1e-13)
+    # i_c(0) is a KCL sum over up to ~40 S of conductance at ~1 V: rounding
+    # 16 eps 40 A ~ 1.4e-13 A, which step 2 multiplies by h / C <= 200
+    np.testing.assert_allclose(v1, v0, rtol=0, atol=5e-11)
+    np.testing.assert_allclose(il1, 0.0, rtol=0, atol=1e-15)
+
+
+def test_three_level_from_paper_initial_conditions_tracks_explicit_form():
+    """Eq. 11 started from the two levels of Section IV-B equals the explicit
+    form (Eq. 10) started from (v(h), i_l(h)) at t = h, step by step (direct
+    solves: only rounding separates the two recurrences)."""
+    net = pgsynth.config2(nx=6, ny=5)
+    h = net.meta["h"]
+    v0, v1, il1 = transient.paper_initial_conditions(net, h)
+    V3 = [v for _, v in transient.simulate_three_level(net, h, 40, v0, v1)]
+    VE, _ = transient.transient(net, h, 39, v0=v1, il0=il1, s0=1)
+    np.testing.assert_allclose(np.stack(V3), VE[1:], rtol=0, atol=1e-11)
