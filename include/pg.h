@@ -118,7 +118,17 @@ typedef struct pg_options {
                                  on shared-memory tiles with ghost zones, k exact block sweeps per device
                                  barrier.  k > 0 (<= 7): that k; 0 (default): k = 2 for 2-3 layers,
                                  off for 1 layer; < 0: off (neighbour-list point SOR) */
+    int32_t form;             /* PG_FORM_EXPLICIT (default): inductor currents kept as state (Eq. 10);
+                                 PG_FORM_THREE_LEVEL: the three-level recurrence of Eq. 11 / Eq. 14,
+                                 whose state is v(s-1), v(s-2) alone.  A step from a single level (the
+                                 DC point, pg_set_state) is an ordinary backward-Euler step with the
+                                 state's inductor currents; pg_initial_conditions gives the paper's two
+                                 levels instead.  No il_all output; step errors add up over the steps
+                                 instead of decaying, so err_bound is NaN */
 } pg_options;
+
+#define PG_FORM_EXPLICIT 0
+#define PG_FORM_THREE_LEVEL 1
 
 /* Fill *opt with the defaults listed above. */
 void pg_default_options(pg_options* opt);
@@ -282,6 +292,23 @@ pg_status pg_transient_async(pg_grid* g, double h, int32_t nsteps, const double*
  * NULL (device_ms is 0: not timed).
  */
 pg_status pg_async_stats(pg_grid* g, const void* dstats, pg_run_stats* stats);
+
+/*
+ * The initial-condition procedure of Section IV-B: (1) DC at t = 0 with every
+ * capacitor a voltage source v_c(0) and every inductor a current source i_l(0);
+ * (2) v_c(h) = v_c(0) + h i_c(0) / C, i_l(h) = i_l(0) + h v_l(0) / L;
+ * (3) DC at t = h with the capacitors at v_c(h) and the inductors carrying
+ * i_l(h).  Both DC analyses are relaxation solves of derived grids (the
+ * capacitor nodes fixed) to the grid's per-step target.  The grid's state
+ * becomes v(h) at step 1 with v(0) as the previous level and i_l(h) as the
+ * inductor currents, which is what both forms continue from.  vc0 ([n_c], one
+ * voltage per capacitor element; parallel capacitors on one node must agree) or
+ * NULL for the DC operating point with the capacitors open; il0 ([n_l]) or NULL
+ * for zero; host or device per on_host.  Errors: PG_ERR_INVALID_ARG,
+ * PG_ERR_FLOATING_NODE (a node with no conductive path to a source, a capacitor
+ * node or ground once the inductors are current sources), PG_ERR_CUDA.
+ */
+pg_status pg_initial_conditions(pg_grid* g, double h, const double* vc0, const double* il0, int32_t on_host);
 
 /* One step (pg_transient with nsteps = 1); v_out (device, [n_nodes]) may be NULL. */
 pg_status pg_step(pg_grid* g, double h, double* v_out, pg_run_stats* stats);

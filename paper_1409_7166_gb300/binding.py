@@ -22,6 +22,7 @@ STATUS = {0: "PG_OK", 1: "PG_ERR_INVALID_ARG", 2: "PG_ERR_FLOATING_NODE", 3: "PG
 (PG_OK, PG_ERR_INVALID_ARG, PG_ERR_FLOATING_NODE, PG_ERR_OOM, PG_ERR_CUDA, PG_ERR_NOT_CONVERGED,
  PG_ERR_TIMEOUT, PG_ERR_UNSUPPORTED) = range(8)
 PG_PREC_FP64, PG_PREC_MIXED = 0, 1
+PG_FORM_EXPLICIT, PG_FORM_THREE_LEVEL = 0, 1
 PG_DEBUG_SKIP_ARRIVAL = 1
 
 _i32p = C.POINTER(C.c_int32)
@@ -45,7 +46,7 @@ class pg_options(C.Structure):
                 ("step_tol", C.c_double), ("max_sweeps", C.c_int32), ("warm_start", C.c_int32),
                 ("inner_reduction", C.c_double), ("threads_per_block", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("barrier_timeout_s", C.c_double),
-                ("debug_flags", C.c_int32), ("lattice_sweeps", C.c_int32)]
+                ("debug_flags", C.c_int32), ("lattice_sweeps", C.c_int32), ("form", C.c_int32)]
 
 
 class pg_output(C.Structure):
@@ -103,6 +104,7 @@ def lib(path: Optional[str] = None) -> C.CDLL:
     L.pg_grid_info.argtypes = [vp, _i32p, _i32p, _i32p, _i32p]
     L.pg_set_state.argtypes = [vp, vp, vp, C.c_int64, C.c_int32]
     L.pg_grid_components.argtypes = [vp, _i32p, vp]
+    L.pg_initial_conditions.argtypes = [vp, C.c_double, vp, vp, C.c_int32]
     L.pg_get_state.argtypes = [vp, vp, vp, _i64p, C.c_int32]
     L.pg_reset.argtypes = [vp]
     L.pg_update_sources.argtypes = [vp, vp, vp, C.c_int32]
@@ -119,7 +121,8 @@ def lib(path: Optional[str] = None) -> C.CDLL:
                               C.POINTER(pg_options), _f64p]
     for name in ("pg_create_grid", "pg_set_stream", "pg_grid_info", "pg_set_state", "pg_get_state",
                  "pg_reset", "pg_update_sources", "pg_transient", "pg_step", "pg_solve", "pg_solve_noalloc",
-                 "pg_update_values", "pg_adjoint", "pg_transient_async", "pg_async_stats", "pg_autotune", "pg_grid_components"):
+                 "pg_update_values", "pg_adjoint", "pg_transient_async", "pg_async_stats", "pg_autotune", "pg_grid_components",
+                 "pg_initial_conditions"):
         getattr(L, name).restype = C.c_int
     if path is None:
         _LIB = L
@@ -214,6 +217,12 @@ def pg_grid_components(h, n_nodes: Optional[int] = None):
     comp = None if n_nodes is None else np.zeros(int(n_nodes), dtype=np.int32)
     _check(lib().pg_grid_components(h, C.byref(nc), _ptr(comp)), "pg_grid_components")
     return nc.value, comp
+
+
+def pg_initial_conditions(h, step_h: float, vc0=None, il0=None):
+    """Section IV-B initial conditions: the grid's state becomes v(h) at step 1 (v(0) before it)."""
+    _check(lib().pg_initial_conditions(h, float(step_h), _ptr(vc0), _ptr(il0), _on_host(vc0, il0)),
+           "pg_initial_conditions")
 
 
 def pg_set_state(h, v, il=None, step: int = 0):

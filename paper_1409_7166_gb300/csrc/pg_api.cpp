@@ -313,6 +313,7 @@ RunParams pg::base_params(const pg_grid* g) {
     rp.cur = g->vL; rp.prev = g->vP;
     rp.warm_extrap = g->opt.warm_start;
     rp.lat_k = g->dg.lwE ? g->lat_k : 0;
+    rp.three_level = g->opt.form == PG_FORM_THREE_LEVEL;
     return rp;
 }
 
@@ -634,6 +635,10 @@ pg_status create_impl(const pg_netlist* nl, const pg_options* opt, std::unique_p
     if (o.threads_per_block != 256) { g_last_error = "threads_per_block must be 256"; return PG_ERR_INVALID_ARG; }
     if (o.barrier_timeout_s <= 0.0) o.barrier_timeout_s = 2.0;
     if (o.lattice_sweeps > 7) { g_last_error = "lattice_sweeps must be <= 7"; return PG_ERR_INVALID_ARG; }
+    if (o.form != PG_FORM_EXPLICIT && o.form != PG_FORM_THREE_LEVEL) {
+        g_last_error = "form must be PG_FORM_EXPLICIT or PG_FORM_THREE_LEVEL";
+        return PG_ERR_INVALID_ARG;
+    }
     g->threads = o.threads_per_block;
     g->mixed = o.precision == PG_PREC_MIXED;
     std::string why;
@@ -660,7 +665,8 @@ pg_status fill_stats(pg_grid* g, const double* st, float ms, pg_run_stats* out) 
     out->total_outer = (int64_t)st[kStatOuter];
     out->max_outer_step = (int32_t)st[kStatMaxOuter];
     out->max_step_bound = g->kappa * (st[kStatMaxBound] + 1e-13);
-    out->err_bound = std::isfinite(g->kacc) ? out->max_step_bound * g->kacc : NAN;
+    // the three-level form carries no i_l state: its step errors add up instead of decaying
+    out->err_bound = std::isfinite(g->kacc) && g->opt.form == PG_FORM_EXPLICIT ? out->max_step_bound * g->kacc : NAN;
     out->failed_step = (int64_t)st[kStatFailedStep];
     out->omega = g->omega;
     out->rho_jacobi = g->rho;
@@ -691,6 +697,7 @@ void pg_default_options(pg_options* o) {
     o->blocks_per_sm = 0;
     o->barrier_timeout_s = 2.0;
     o->debug_flags = 0;
+    o->form = PG_FORM_EXPLICIT;
 }
 
 const char* pg_status_str(pg_status s) {
@@ -742,6 +749,44 @@ pg_status pg_grid_info(const pg_grid* g, int32_t* n, int32_t* nl, int32_t* ncol,
     if (nl) *nl = g->P.n_l;
     if (ncol) *ncol = g->P.ncol;
     if (npad) *npad = g->P.n_pad;
+    return PG_OK;
+}
+
+pg_status pg_initial_conditions(pg_grid* g, double h, const double* vc0, const double* il0, int32_t on_host) {
+    if (!g) return PG_ERR_INVALID_ARG;
+    pg_status s = prepare_h(g, h);
+    if (s) return s;
+    const NetCopy& nc = g->nc;
+    std::vector<double> hvc, hil;
+    const double* pvc = vc0;
+    const double* pil = il0;
+    if (!on_host) {
+        if (vc0) {
+            hvc.resize(nc.c_val.size());
+            CK(cudaMemcpy(hvc.data(), vc0, hvc.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            pvc = hvc.data();
+        }
+        if (il0) {
+            hil.resize(nc.l_val.size());
+            CK(cudaMemcpy(hil.data(), il0, hil.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            pil = hil.data();
+        }
+    }
+    std::vector<double> v0, v1, il1;
+    // each DC solve to the per-step target (a derived grid without capacitors has kacc = 1,
+    // so its step target is half its tol)
+    if ((s = pg::paper_initial_levels(nc, h, 2.0 * g->step_tol, g->stream, pvc, pil, v0, v1, il1))) return s;
+    const Packed& P = g->P;
+    std::vector<double> p0(P.n_pad, 0.0), p1(P.n_pad, 0.0);
+    for (int i = 0; i < P.n_pad; ++i)
+        if (P.orig[i] >= 0) { p0[i] = v0[P.orig[i]]; p1[i] = v1[P.orig[i]]; }
+    g->vL = 0; g->vP = 1;
+    if ((s = upload(g, g->ds.v[0], p1)) || (s = upload(g, g->ds.v[1], p0))) return s;
+    if (P.n_l) CK(cudaMemcpyAsync(g->ds.il, il1.data(), P.n_l * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    g->has_state = true;
+    g->step = 1;
+    g->have_prev = true;
     return PG_OK;
 }
 
@@ -858,6 +903,10 @@ pg_status pg_transient(pg_grid* g, double h, int32_t nsteps, const pg_output* ou
     pg_status s = prepare_h(g, h);
     if (s) return s;
     if (!g->has_state && (s = dc_init(g))) return s;
+    if (g->opt.form == PG_FORM_THREE_LEVEL && out && out->il_all) {
+        g_last_error = "the three-level form keeps no inductor currents";
+        return PG_ERR_INVALID_ARG;
+    }
     if (nsteps == 0) {
         double z[kStatCount] = {0};
         z[kStatFailedStep] = -1;
@@ -1035,6 +1084,7 @@ pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* o
     if (!g || nsteps < 1 || !obj || ckpt_every < 0) return PG_ERR_INVALID_ARG;
     if (obj->kind != PG_OBJ_SOFTPLUS_DROP) { g_last_error = "unknown objective"; return PG_ERR_INVALID_ARG; }
     if (g->P.n_l > 0) { g_last_error = "the adjoint covers RC grids (no inductors)"; return PG_ERR_UNSUPPORTED; }
+    if (g->opt.form != PG_FORM_EXPLICIT) { g_last_error = "the adjoint needs the explicit form"; return PG_ERR_UNSUPPORTED; }
     const int ck = ckpt_every > 0 ? ckpt_every : 50;
     pg_status s = prepare_h(g, h);
     if (s) return s;

@@ -115,6 +115,11 @@ struct pg_grid {
 namespace pg {
 // Per-call launch parameters filled from the grid's options and per-h constants.
 RunParams base_params(const pg_grid* g);
+// Section IV-B initial conditions: the levels v(0), v(h) and i_l(h) (host, caller numbering);
+// DC solves on derived grids to `tol`, issued on `stream`.
+pg_status paper_initial_levels(const NetCopy& nc, double h, double tol, void* stream, const double* vc0,
+                               const double* il0, std::vector<double>& v0, std::vector<double>& v1,
+                               std::vector<double>& il1);
 // Record the detail message returned by pg_last_error().
 void set_last_error(const std::string& msg);
 }  // namespace pg

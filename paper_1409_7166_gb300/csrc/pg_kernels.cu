@@ -334,17 +334,48 @@ __device__ __forceinline__ void sell_row(const DevGrid& g, const WarpCache* wc, 
 template <bool MIXED>
 __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* wc, const SliceDesc& sd,
                                             const DevState& st, const RunParams& rp, int s, int lane, int vL, int vP,
-                                            int vF, bool extrap, double t, int dsel, unsigned long long* latR) {
+                                            int vF, bool extrap, bool three, double t, int dsel,
+                                            unsigned long long* latR) {
     const int i0 = s * kSlice + lane * kVec;
     const double* vl = vbuf(st, vL);
     const double* vp = vbuf(st, vP);
     double vw[4], b[4], D[4], iD[4];
     ldg4(g.D64 + i0, D);
     ldg4(g.invD64 + i0, iD);
+    double base[4] = {0.0, 0.0, 0.0, 0.0};       // the residual is taken of M (x0 - base)
     if (rp.mode == kModeSolve) {
         ldg4(st.rhs + i0, b);
         if (rp.x0) ldg4(rp.x0 + i0, vw);
         else vw[0] = vw[1] = vw[2] = vw[3] = 0.0;
+    } else if (three) {
+        // Eq. 11 less M v(s-1), an exact rearrangement:
+        //   b - M v(s-1) = (C/h)(v(s-1) - v(s-2)) - A_l^T h L^-1 (A_l v(s-1) + A_ls v_d)
+        //                  - A_i^T (I_s(t) - I_s(t-h)),
+        // and the residual of x0 is that minus M (x0 - v(s-1)).
+        double pp[4], ch[4];
+        ld4(vl + i0, base);
+        ld4(vp + i0, pp);
+        ldg4(g.ch + i0, ch);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            vw[j] = extrap ? 2.0 * base[j] - pp[j] : base[j];
+            double bj = ch[j] * (base[j] - pp[j]);
+            const int i = i0 + j;
+            for (int q = __ldg(g.ld_ptr + i); q < __ldg(g.ld_ptr + i + 1); ++q) {
+                const int sid = __ldg(g.ld_idx + q);
+                const int e = (sid > 0 ? sid : -sid) - 1;
+                const double dI = pwl_eval(g, e, t) - pwl_eval(g, e, t - rp.h);
+                bj -= sid > 0 ? dI : -dI;
+            }
+            for (int q = __ldg(g.ind_ptr + i); q < __ldg(g.ind_ptr + i + 1); ++q) {
+                const int lid = __ldg(g.ind_idx + q);
+                const int e = (lid > 0 ? lid : -lid) - 1;
+                const double di = __ldg(g.ind_hl + e) *
+                                  (term_volt(g, vl, __ldg(g.ind_a + e)) - term_volt(g, vl, __ldg(g.ind_b + e)));
+                bj -= lid > 0 ? di : -di;
+            }
+            b[j] = bj;
+        }
     } else {
         double a[4], ch[4], cj[4];
         ld4(vl + i0, a);
@@ -380,6 +411,9 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* w
     if (rp.mode == kModeSolve) {
         if (rp.x0) sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return __ldg(rp.x0 + c); }, sig);
         else sig[0] = sig[1] = sig[2] = sig[3] = 0.0;
+    } else if (three) {
+        if (extrap) sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return vl[c] - vp[c]; }, sig);
+        else sig[0] = sig[1] = sig[2] = sig[3] = 0.0;
     } else if (extrap) {
         sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return 2.0 * vl[c] - vp[c]; }, sig);
     } else {
@@ -388,7 +422,7 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* w
     double r[4], sc[4], mon = 0.0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        r[j] = b[j] + sig[j] - D[j] * vw[j];
+        r[j] = b[j] + sig[j] - D[j] * (vw[j] - base[j]);
         sc[j] = fabs(r[j]) * iD[j];
         mon = nanmax(mon, sc[j]);
     }
@@ -977,6 +1011,8 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
         const long long sabs = rp.step0 + sl + 1;
         const double t = (double)sabs * rp.h;
         const bool extrap = rp.mode == kModeTransient && rp.warm_extrap && have_prev;
+        // Eq. 11 needs two levels; a step from a single level is an ordinary backward-Euler step
+        const bool three = rp.mode == kModeTransient && rp.three_level && have_prev;
         int dsel = 0;
         if (sl > 0) { finalize_vmin(sl - 1); finalize_comp(sl - 1); }
 
@@ -986,7 +1022,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
             for (int tt = 0; tt < wc->cnt[c]; ++tt) {
                 const int s = wc->lo[c] + tt;
                 mon = nanmax(mon, phase_rhs<MIXED>(g, wc, warp_desc(g, *wc, c, tt, s), st, rp, s, lane, vL, vP, vF,
-                                                   extrap, t, dsel, lat_buf(lat_par ^ 1)));
+                                                   extrap, three, t, dsel, lat_buf(lat_par ^ 1)));
             }
         BarrierResult br = barrier(true, mon);
         if (!br.ok) { publish(-1); return; }
@@ -1079,7 +1115,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
         // ---- post: inductor currents (Eq. 10), outputs
         lat_clear(lat_par ^ 1);           // the next step's phase A writes there
         const double* vnew = vbuf(st, vF);
-        if (rp.mode == kModeTransient) {
+        if (rp.mode == kModeTransient && !three) {
             for (int e = gtid; e < g.n_l; e += nthreads) {
                 const double va = term_volt(g, vnew, __ldg(g.ind_a + e));
                 const double vb = term_volt(g, vnew, __ldg(g.ind_b + e));
