@@ -226,6 +226,9 @@ typedef struct pg_run_stats {
                                    turning per-step errors into the accumulated error; inf for RLC */
     int32_t lattice_sweeps;     /* inner solve: 0 = neighbour-list point SOR, k > 0 = lattice
                                    column-block SOR with k sweeps per device barrier */
+    double phase_ms[4];         /* device time of the launch by phase, ms: step start (RHS, warm start,
+                                   FP64 residual), inner solves, FP64 outer passes, step end (inductor
+                                   update, outputs); each ends at a device barrier */
 } pg_run_stats;
 
 /*

@@ -65,10 +65,12 @@ class pg_run_stats(C.Structure):
                 ("err_bound", C.c_double), ("failed_step", C.c_int64), ("omega", C.c_double),
                 ("rho_jacobi", C.c_double), ("kappa", C.c_double), ("q", C.c_double),
                 ("step_tol", C.c_double), ("device_ms", C.c_double), ("kacc", C.c_double),
-                ("lattice_sweeps", C.c_int32)]
+                ("lattice_sweeps", C.c_int32), ("phase_ms", C.c_double * 4)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["phase_ms"] = list(d["phase_ms"])
+        return d
 
 
 class PGError(RuntimeError):

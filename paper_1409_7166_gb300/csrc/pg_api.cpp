@@ -179,6 +179,9 @@ pg_status alloc_device(pg_grid* g) {
         CK(cudaMemsetAsync(st.v[k], 0, np * sizeof(double), g->stream));
     }
     st.il = g->alloc<double>(P.n_l);
+    d.n_src = (int32_t)(P.pwl_ptr.size() - 1);
+    st.isrc = g->alloc<double>(2 * (size_t)std::max(d.n_src, 1));
+    if (!st.isrc) return PG_ERR_OOM;
     st.r64 = g->alloc<double>(np);
     if (!st.il || !st.r64) return PG_ERR_OOM;
     CK(cudaMemsetAsync(st.il, 0, std::max(1, P.n_l) * sizeof(double), g->stream));
@@ -676,6 +679,7 @@ pg_status fill_stats(pg_grid* g, const double* st, float ms, pg_run_stats* out) 
     out->device_ms = ms;
     out->kacc = g->kacc;
     out->lattice_sweeps = g->lat_k;
+    for (int k = 0; k < 4; ++k) out->phase_ms[k] = st[kStatTimeA + k] * 1e-6;
     return PG_OK;
 }
 

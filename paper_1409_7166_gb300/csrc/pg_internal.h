@@ -96,6 +96,7 @@ struct DevGrid {
     const int32_t* orig;
     const int32_t* ld_ptr;
     const int32_t* ld_idx;
+    int32_t n_src;           // PWL load sources
     const int64_t* pwl_ptr;
     const double* pwl_t;
     const double* pwl_v;
@@ -134,6 +135,7 @@ struct DevState {
     double* d64[2];          // correction buffers (FP64 sweeps)
     float* d32[2];           // correction buffers (FP32 sweeps)
     const double* rhs;       // kModeSolve: right-hand side (permuted)
+    double* isrc;            // [2 x n_src] load currents I_e(S h), slot S & 1 (transient mode)
 };
 
 struct DevCtl {
@@ -149,7 +151,9 @@ struct DevCtl {
 
 enum Stat : int {
     kStatSteps = 0, kStatSweeps, kStatMaxSweeps, kStatOuter, kStatMaxOuter,
-    kStatMaxBound, kStatFailedStep, kStatLastR, kStatCount
+    kStatMaxBound, kStatFailedStep, kStatLastR,
+    kStatTimeA, kStatTimeInner, kStatTimeOuter, kStatTimePost,   // ns on block 0's clock
+    kStatCount
 };
 
 struct RunParams {

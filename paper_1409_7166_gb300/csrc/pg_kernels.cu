@@ -334,7 +334,7 @@ __device__ __forceinline__ void sell_row(const DevGrid& g, const WarpCache* wc, 
 template <bool MIXED>
 __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* wc, const SliceDesc& sd,
                                             const DevState& st, const RunParams& rp, int s, int lane, int vL, int vP,
-                                            int vF, bool extrap, bool three, double t, int dsel,
+                                            int vF, bool extrap, bool three, long long sabs, int dsel,
                                             unsigned long long* latR) {
     const int i0 = s * kSlice + lane * kVec;
     const double* vl = vbuf(st, vL);
@@ -364,7 +364,7 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* w
             for (int q = __ldg(g.ld_ptr + i); q < __ldg(g.ld_ptr + i + 1); ++q) {
                 const int sid = __ldg(g.ld_idx + q);
                 const int e = (sid > 0 ? sid : -sid) - 1;
-                const double dI = pwl_eval(g, e, t) - pwl_eval(g, e, t - rp.h);
+                const double dI = st.isrc[(sabs & 1) * g.n_src + e] - st.isrc[((sabs - 1) & 1) * g.n_src + e];
                 bj -= sid > 0 ? dI : -dI;
             }
             for (int q = __ldg(g.ind_ptr + i); q < __ldg(g.ind_ptr + i + 1); ++q) {
@@ -396,7 +396,7 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* w
             const int i = i0 + j;
             for (int q = __ldg(g.ld_ptr + i); q < __ldg(g.ld_ptr + i + 1); ++q) {
                 const int sid = __ldg(g.ld_idx + q);
-                const double I = pwl_eval(g, (sid > 0 ? sid : -sid) - 1, t);
+                const double I = st.isrc[(sabs & 1) * g.n_src + (sid > 0 ? sid : -sid) - 1];
                 bj -= sid > 0 ? I : -I;               // A_i^T I_s(t+h)
             }
             for (int q = __ldg(g.ind_ptr + i); q < __ldg(g.ind_ptr + i + 1); ++q) {
@@ -937,8 +937,22 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
     long long tot_sweeps = 0, tot_outer = 0, steps_done = 0;
     int max_sw = 0, max_out = 0;
     double max_bound_R = 0.0, last_R = 0.0;
+    // time per phase, read by block 0 right after the barriers that end the phases
+    double t_phase[4] = {0.0, 0.0, 0.0, 0.0};
+    long long t_mark = lead ? global_ns() : 0ll;
+    auto lap = [&](int k) {
+        if (lead) {
+            const long long t_now = global_ns();
+            t_phase[k] += (double)(t_now - t_mark);
+            t_mark = t_now;
+        }
+    };
     auto publish = [&](long long failed) {
         if (lead) {
+            ctl.stats[kStatTimeA] = t_phase[0];
+            ctl.stats[kStatTimeInner] = t_phase[1];
+            ctl.stats[kStatTimeOuter] = t_phase[2];
+            ctl.stats[kStatTimePost] = t_phase[3];
             ctl.stats[kStatSteps] = (double)steps_done;
             ctl.stats[kStatSweeps] = (double)tot_sweeps;
             ctl.stats[kStatMaxSweeps] = (double)max_sw;
@@ -1007,9 +1021,21 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
             for (int q = threadIdx.x; q < g.n_lats; q += blockDim.x) ctl.lat_R[(size_t)b * g.n_lats + q] = 0ull;
     };
 
+    // load currents of a step, one thread per source (slot S & 1 holds I(S h)); phase A of
+    // step S reads slot S & 1 (and slot (S - 1) & 1 in the three-level form)
+    auto eval_sources = [&](long long S) {
+        double* dst = st.isrc + (S & 1) * g.n_src;
+        const double tS = (double)S * rp.h;
+        for (int e = gtid; e < g.n_src; e += nthreads) dst[e] = pwl_eval(g, e, tS);
+    };
+    if (rp.mode == kModeTransient && g.n_src > 0 && rp.nsteps > 0) {
+        eval_sources(rp.step0 + 1);
+        if (rp.three_level) eval_sources(rp.step0);
+        if (!barrier(false, 0.0).ok) { publish(-1); return; }
+    }
+
     for (int sl = 0; sl < rp.nsteps; ++sl) {
         const long long sabs = rp.step0 + sl + 1;
-        const double t = (double)sabs * rp.h;
         const bool extrap = rp.mode == kModeTransient && rp.warm_extrap && have_prev;
         // Eq. 11 needs two levels; a step from a single level is an ordinary backward-Euler step
         const bool three = rp.mode == kModeTransient && rp.three_level && have_prev;
@@ -1022,12 +1048,13 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
             for (int tt = 0; tt < wc->cnt[c]; ++tt) {
                 const int s = wc->lo[c] + tt;
                 mon = nanmax(mon, phase_rhs<MIXED>(g, wc, warp_desc(g, *wc, c, tt, s), st, rp, s, lane, vL, vP, vF,
-                                                   extrap, three, t, dsel, lat_buf(lat_par ^ 1)));
+                                                   extrap, three, sabs, dsel, lat_buf(lat_par ^ 1)));
             }
         BarrierResult br = barrier(true, mon);
         if (!br.ok) { publish(-1); return; }
         double R = br.val;
         lat_par ^= 1;
+        lap(0);
 
         int sweeps = 0, outer = 0;
         bool ok = true;
@@ -1092,6 +1119,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
                     est_mark = est;
                 }
             }
+            lap(1);
             if (est_nan) { ok = false; break; }
             // outer pass
             double m = 0.0;
@@ -1109,11 +1137,13 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
             lat_par ^= 1;
             dsel ^= 1;
             ++outer;
+            lap(2);
         }
         if (!ok) { fail(sabs); return; }
 
-        // ---- post: inductor currents (Eq. 10), outputs
+        // ---- post: inductor currents (Eq. 10), outputs, the next step's load currents
         lat_clear(lat_par ^ 1);           // the next step's phase A writes there
+        if (rp.mode == kModeTransient && sl + 1 < rp.nsteps) eval_sources(sabs + 1);
         const double* vnew = vbuf(st, vF);
         if (rp.mode == kModeTransient && !three) {
             for (int e = gtid; e < g.n_l; e += nthreads) {
@@ -1207,6 +1237,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
         vP = vL; vL = vF; vF = 3 - vL - vP;
         have_prev = true;
         if (!barrier(false, 0.0).ok) { publish(-1); return; }
+        lap(3);
     }
     if (rp.nsteps > 0) { finalize_vmin(rp.nsteps - 1); finalize_comp(rp.nsteps - 1); }
     publish(-1);
