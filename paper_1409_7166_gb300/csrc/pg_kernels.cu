@@ -645,10 +645,11 @@ __device__ double sweep_colour_tma(const DevGrid& g, const WarpCache* wc, TmaWar
 //
 // The relaxation runs on 32 x 32-column regions of all layers held in shared
 // memory: the region is its tile of (32 - 2H)^2 columns plus a ghost zone of
-// H = 2k columns, k exact sweeps (2k half-sweeps) are applied to the whole
-// region with its outermost ring fixed, and after half-sweep j every column at
-// distance >= j from the edge holds the exact value, so the tile interior
-// equals k global block sweeps.  Tiles read the previous round's corrections
+// H = 2k columns, and k exact sweeps (2k half-sweeps) are applied to the
+// region: half-sweep j (1-based) updates the columns at distance >= j from the
+// region edge, after which every such column holds the exact value (it reads
+// only neighbours at distance >= j - 1, updated by every earlier half-sweep), so
+// the tile interior (distance >= 2k) equals k global block sweeps.  Tiles read the previous round's corrections
 // and write the next buffer: one device barrier per k sweeps, every branch
 // weight stored once (E, N, U per node).
 constexpr int kLatR = 32;                          // region side (columns)
@@ -738,7 +739,9 @@ __device__ float lattice_tile(const DevGrid& g, int off, int nx, int ny, int til
             const int rx = 2 * pair + ((hs + x0 + y) & 1);      // the column of this colour in the pair
             const int x = x0 + rx;
             const int edge = min(min(rx, ry), min(kLatR - 1 - rx, kLatR - 1 - ry));
-            if (edge == 0 || x < 0 || x >= nx || y < 0 || y >= ny) continue;
+            // half-sweep hs only matters at distance > hs from the region edge: what it
+            // would change nearer the edge cannot reach the interior by the last one
+            if (edge <= hs || x < 0 || x >= nx || y < 0 || y >= ny) continue;
             const int a0 = ry * kLatR + rx;
             float f[NL], xs[NL];
 #pragma unroll
