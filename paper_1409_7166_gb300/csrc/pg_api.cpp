@@ -107,6 +107,9 @@ pg_status alloc_device(pg_grid* g) {
     double* cinj = g->alloc<double>(np);
     float* w32 = g->mixed ? g->alloc<float>(P.n_ell) : nullptr;
     float* invD32 = g->mixed ? g->alloc<float>(np) : nullptr;
+    float* w32lo = g->mixed ? g->alloc<float>(P.n_ell) : nullptr;
+    float* D32 = g->mixed ? g->alloc<float>(np) : nullptr;
+    float* D32lo = g->mixed ? g->alloc<float>(np) : nullptr;
     // lattice column-block inner solve: on by default for multi-layer lattices (the via
     // couplings go into the blocks); single-layer grids measure faster on the SELL sweep
     const int lat_k = g->opt.lattice_sweeps > 0 ? g->opt.lattice_sweeps
@@ -138,13 +141,14 @@ pg_status alloc_device(pg_grid* g) {
     }
     if (!colour_slice || !slice_off || !slice_w || !slice_doff || !dia_off || !ell_col || !orig || !ld_ptr ||
         !ld_idx || !pwl_ptr || !pwl_t || !pwl_v || !ind_a || !ind_b || !ind_hl || !ind_ptr || !ind_idx || !vdd ||
-        !w64 || !D64 || !invD64 || !ch || !cinj || (g->mixed && (!w32 || !invD32)))
+        !w64 || !D64 || !invD64 || !ch || !cinj || (g->mixed && (!w32 || !invD32 || !w32lo || !D32 || !D32lo)))
         return PG_ERR_OOM;
     d.colour_slice = colour_slice; d.slice_off = slice_off; d.slice_w = slice_w; d.slice_doff = slice_doff;
     d.dia_off = dia_off; d.ell_col = ell_col; d.orig = orig; d.ld_ptr = ld_ptr; d.ld_idx = ld_idx;
     d.pwl_ptr = pwl_ptr; d.pwl_t = pwl_t; d.pwl_v = pwl_v; d.n_l = P.n_l; d.ind_a = ind_a; d.ind_b = ind_b;
     d.ind_hl = ind_hl; d.ind_ptr = ind_ptr; d.ind_idx = ind_idx; d.vdd = vdd;
     d.w64 = w64; d.D64 = D64; d.invD64 = invD64; d.ch = ch; d.cinj = cinj; d.w32 = w32; d.invD32 = invD32;
+    d.w32lo = w32lo; d.D32 = D32; d.D32lo = D32lo;
     pg_status s;
     {
         // component of each permuted node (independent sub-circuits, Fig. 1)
@@ -289,10 +293,20 @@ pg_status assemble_h(pg_grid* g, double h) {
             return s;
     }
     if (g->mixed) {
-        std::vector<float> w32(P.n_ell), iD32(np);
-        for (int64_t e = 0; e < P.n_ell; ++e) w32[e] = (float)w[e];
-        for (int i = 0; i < np; ++i) iD32[i] = (float)iD[i];
-        if ((s = upload(g, const_cast<float*>(g->dg.w32), w32)) || (s = upload(g, const_cast<float*>(g->dg.invD32), iD32)))
+        // FP32 pairs: hi = the rounded value, lo = the rounded remainder
+        std::vector<float> w32(P.n_ell), wlo(P.n_ell), iD32(np), d32(np), dlo(np);
+        for (int64_t e = 0; e < P.n_ell; ++e) {
+            w32[e] = (float)w[e];
+            wlo[e] = (float)(w[e] - (double)w32[e]);
+        }
+        for (int i = 0; i < np; ++i) {
+            iD32[i] = (float)iD[i];
+            d32[i] = (float)D[i];
+            dlo[i] = (float)(D[i] - (double)d32[i]);
+        }
+        if ((s = upload(g, const_cast<float*>(g->dg.w32), w32)) || (s = upload(g, const_cast<float*>(g->dg.invD32), iD32)) ||
+            (s = upload(g, const_cast<float*>(g->dg.w32lo), wlo)) || (s = upload(g, const_cast<float*>(g->dg.D32), d32)) ||
+            (s = upload(g, const_cast<float*>(g->dg.D32lo), dlo)))
             return s;
     }
     CK(cudaStreamSynchronize(g->stream));
@@ -645,7 +659,7 @@ pg_status create_impl(const pg_netlist* nl, const pg_options* opt, std::unique_p
     g->threads = o.threads_per_block;
     g->mixed = o.precision == PG_PREC_MIXED;
     std::string why;
-    pg_status s = build_packed(nl, &g->P, &why);
+    pg_status s = build_packed(nl, &g->P, &why, g->mixed ? o.lattice_sweeps : INT32_MIN);
     if (s) { g_last_error = why; return s; }
     g->nc.from(nl);
     compute_dc_trivial(g.get());

@@ -31,7 +31,7 @@ inline bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 }  // namespace
 
-pg_status build_packed(const pg_netlist* nl, Packed* P, std::string* why) {
+pg_status build_packed(const pg_netlist* nl, Packed* P, std::string* why, int32_t lattice_policy) {
     auto fail = [&](pg_status s, const std::string& m) { if (why) *why = m; return s; };
     if (!nl || !P) return fail(PG_ERR_INVALID_ARG, "null netlist");
     const int32_t n = nl->n_nodes, p = nl->n_sources;
@@ -225,10 +225,13 @@ pg_status build_packed(const pg_netlist* nl, Packed* P, std::string* why) {
     if (!ok) { P->lats.clear(); P->lat_maxnl = 0; }
     P->lattice = ok;
 
-    // --- colouring: BFS 2-colouring (red-black), else greedy multicolour
-    std::vector<int32_t> colour(n, -1);
-    bool bipartite = true;
-    {
+    // --- colouring: BFS 2-colouring (red-black), else greedy multicolour; a grid that
+    // takes the lattice inner solve keeps its natural order (one colour)
+    const bool natural = P->lattice && lattice_policy != INT32_MIN &&
+                         (lattice_policy > 0 || (lattice_policy == 0 && P->lat_maxnl >= 2));
+    std::vector<int32_t> colour(n, natural ? 0 : -1);
+    bool bipartite = !natural;
+    if (!natural) {
         std::vector<int32_t> q; q.reserve(n);
         for (int s = 0; s < n && bipartite; ++s) {
             if (colour[s] >= 0) continue;
@@ -243,8 +246,10 @@ pg_status build_packed(const pg_netlist* nl, Packed* P, std::string* why) {
             }
         }
     }
-    int ncol = 2;
-    if (!bipartite) {
+    int ncol = natural ? 1 : 2;
+    if (natural) {
+        // one colour
+    } else if (!bipartite) {
         std::fill(colour.begin(), colour.end(), -1);
         ncol = 0;
         std::vector<int32_t> seen(kMaxColours + 1, -1);

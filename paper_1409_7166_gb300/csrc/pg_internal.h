@@ -70,7 +70,12 @@ struct Packed {
     std::vector<int32_t> comp_of;             // caller id -> component
 };
 
-pg_status build_packed(const pg_netlist* nl, Packed* out, std::string* why);
+// lattice_policy: the lattice_sweeps option when the grid runs in mixed precision (the
+// lattice inner solve will be used when the netlist is a lattice), INT32_MIN otherwise.
+// Grids that take the lattice inner solve are packed in natural (caller) order with one
+// colour: no point sweep runs on them, and the FP64 passes then read the lattice-ordered
+// corrections contiguously.
+pg_status build_packed(const pg_netlist* nl, Packed* out, std::string* why, int32_t lattice_policy);
 // Refill the value-dependent parts of a packed grid (merged weights, grounded
 // parts, capacitances, 1/L) from a netlist with the same topology.
 pg_status refill_values(const pg_netlist* nl, Packed* P, std::string* why);
@@ -88,6 +93,9 @@ struct DevGrid {
     const int32_t* ell_col;
     const double* w64;
     const float* w32;
+    const float* w32lo;      // w64 - w32 (FP32): w32 + w32lo carries w64 to about 2^-48
+    const float* D32;        // D as an FP32 pair (D32 + D32lo), for the outer pass
+    const float* D32lo;
     const double* D64;
     const double* invD64;
     const float* invD32;

@@ -328,6 +328,48 @@ __device__ __forceinline__ void sell_row(const DevGrid& g, const WarpCache* wc, 
     }
 }
 
+// ---- double-float products for the outer pass (FP32 pairs; GB300's FP64 rate is a
+// small fraction of its FP32 rate).  (hi, lo) += (a_hi + a_lo) x for an FP32 x: the
+// leading product is split exactly (FMA), the sum kept by TwoSum (Knuth), so the
+// result carries about 48 significant bits.
+// The error-free steps use the _rn intrinsics, which the compiler never contracts
+// into FMAs (a contraction would break the TwoSum identity).
+__device__ __forceinline__ void df_acc(float& hi, float& lo, float a_hi, float a_lo, float x) {
+    const float p = __fmul_rn(a_hi, x);
+    const float e = fmaf(a_hi, x, -p);                 // a_hi x = p + e exactly
+    const float t = __fadd_rn(hi, p);
+    const float bv = __fsub_rn(t, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bv)), __fsub_rn(p, bv));   // hi + p = t + err
+    hi = t;
+    lo += err + fmaf(a_lo, x, e);
+}
+
+// sum_k w_k x_{col_k} of one slice row as a double-float, weights as FP32 pairs
+template <typename Load>
+__device__ __forceinline__ void sell_row_df(const DevGrid& g, const WarpCache* wc, const SliceDesc& d, int s, int lane,
+                                            Load xload, float (&hi)[4], float (&lo)[4]) {
+    const long long base = d.off + lane * kVec;
+    const int i0 = s * kSlice + lane * kVec;
+    const int* offs = d.dpos >= 0 ? wc->pool + d.dpos : (d.dpos <= -2 ? g.dia_off + (-2 - d.dpos) : nullptr);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) hi[j] = lo[j] = 0.f;
+    for (int k = 0; k < d.K; ++k) {
+        const long long e = base + (long long)k * kSlice;
+        float wh[4], wl[4];
+        ldg4(g.w32 + e, wh);
+        ldg4(g.w32lo + e, wl);
+        int c[4];
+        if (offs) {
+            const int o = offs[k];
+            c[0] = i0 + o; c[1] = i0 + 1 + o; c[2] = i0 + 2 + o; c[3] = i0 + 3 + o;
+        } else {
+            ldg4(g.ell_col + e, c);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) df_acc(hi[j], lo[j], wh[j], wl[j], xload(c[j]));
+    }
+}
+
 // ---------------------------------------------------------------- phases
 
 // Start of a step: RHS assembly (Eq. 2 / Eq. 10), warm start, FP64 residual.
@@ -844,25 +886,43 @@ __device__ __forceinline__ double outer_slice(const DevGrid& g, const WarpCache*
     } else {
         ld4(d + i0, dv);
     }
-    double D[4], iD[4], r[4], vv[4], sig[4];
-    ldg4(g.D64 + i0, D);
+    double iD[4], r[4], vv[4];
     ldg4(g.invD64 + i0, iD);
     ld4(st.r64 + i0, r);
     ld4(v + i0, vv);
-    if (lat) {
-        sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) {
-            const int o = __ldg(g.orig + c);
-            return o >= 0 ? (double)d[o] : 0.0;
-        }, sig);
+    double Md[4];                                      // (M delta)_i
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32 correction: M delta as a double-float, minus the neighbour sum, then one
+        // FP64 update of r (its error is far below the stopping rule's rounding slack)
+        float hi[4], lo[4], dh[4], dl[4];
+        if (lat) {
+            sell_row_df(g, wc, sd, s, lane, [&](int c) {
+                const int o = __ldg(g.orig + c);
+                return o >= 0 ? d[o] : 0.f;
+            }, hi, lo);
+        } else {
+            sell_row_df(g, wc, sd, s, lane, [&](int c) { return d[c]; }, hi, lo);
+        }
+        ldg4(g.D32 + i0, dh);
+        ldg4(g.D32lo + i0, dl);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float ph = 0.f, pl = 0.f;
+            df_acc(ph, pl, dh[j], dl[j], dv[j]);           // D delta
+            Md[j] = ((double)ph - (double)hi[j]) + ((double)pl - (double)lo[j]);
+        }
     } else {
+        double D[4], sig[4];
+        ldg4(g.D64 + i0, D);
         sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return (double)d[c]; }, sig);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Md[j] = D[j] * (double)dv[j] - sig[j];
     }
     double mon = 0.0, sc[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const double dj = (double)dv[j];
-        r[j] = r[j] - (D[j] * dj - sig[j]);
-        vv[j] += dj;
+        r[j] -= Md[j];
+        vv[j] += (double)dv[j];
         sc[j] = fabs(r[j]) * iD[j];
         mon = nanmax(mon, sc[j]);
     }
