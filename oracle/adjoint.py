@@ -12,7 +12,7 @@ the Lagrangian gives the backward recurrence
     M lambda_s = dJ/dv_s + (C/h) lambda_{s+1},   lambda_{S+1} = 0,
     G mu       = (C/h) lambda_1                    (adjoint of the DC point)
 
-and the parameter gradients
+and the parameter gradients (inductors: see :func:`gradients`)
 
     dJ/dg_e = -sum_s (lambda_{s,a} - lambda_{s,b}) (v_{s,a} - v_{s,b}) - (mu_a - mu_b)(v_{0,a} - v_{0,b})
     dJ/dC_k = -sum_s lambda_{s,k} (v_{s,k} - v_{s-1,k}) / h
@@ -59,11 +59,25 @@ def _term_adjoint(t, lam):
     return np.where(t >= 0, lam[np.maximum(t, 0)], 0.0)
 
 
-def gradients(net, h, nsteps, vref=1.0, margin=0.05):
-    """Return ``(J, dJ/dg per resistor, dJ/dC per capacitor)`` (RC grids)."""
-    if len(net.l_val):
-        raise ValueError("the adjoint oracle covers RC grids")
+def gradients(net, h, nsteps, vref=1.0, margin=0.05, with_l=False):
+    """Return ``(J, dJ/dg per resistor, dJ/dC per capacitor)``, plus ``dJ/dL per
+    inductor`` when ``with_l`` (grids with inductors need it).
+
+    With inductors the explicit form (Eq. 10) has two constraint families,
+    ``F_s = M v_s - (C/h) v_(s-1) + A_l^T i_(s-1) + A_i^T I_s + G_s v_d + h L_s v_d``
+    and ``H_s = i_s - i_(s-1) - h Ldiag^-1 u_s`` with ``u_s = A_l v_s + A_ls v_d``.
+    Their multipliers obey
+
+        mu_s     = mu_(s+1) - A_l lambda_(s+1)                       (mu_S = 0)
+        M lambda_s = dJ/dv_s + (C/h) lambda_(s+1) + h A_l^T Ldiag^-1 mu_s
+
+    and ``dJ/dL_e = (h / L_e^2) sum_s u_(s,e) ((A_l lambda_s)_e - mu_(s,e))``; the
+    resistor and capacitor gradients keep their RC form.  The DC point (inductors
+    carrying i_l(0) = 0) does not depend on L."""
     mats = nodal_matrices(net)
+    m_l = mats.A_l.shape[0]
+    if m_l and not with_l:
+        raise ValueError("grids with inductors: call with with_l=True")
     V = [v for _, v, _ in simulate(net, h, nsteps, mats=mats)]
     V = np.stack(V)                                   # [S+1, n]
     M = mats.system_matrix(h)
@@ -73,21 +87,35 @@ def gradients(net, h, nsteps, vref=1.0, margin=0.05):
     ra, rb = np.asarray(net.r_a), np.asarray(net.r_b)
     ca = np.asarray(net.c_a)
     cnode = np.where(ca >= 0, ca, np.asarray(net.c_b))
+    Lval = np.asarray(net.l_val, dtype=np.float64)
+    A_l = mats.A_l.tocsr()
     dG = np.zeros(len(net.r_g))
     dC = np.zeros(len(net.c_val))
+    dL = np.zeros(m_l)
     J = 0.0
     lam_next = np.zeros(net.n_nodes)
+    mu_next = np.zeros(m_l)
     for s in range(nsteps, 0, -1):
         v = V[s]
         u = vref - v - margin
         J += float(np.sum(softplus(u) ** 2))
         dJdv = -2.0 * softplus(u) * sigmoid(u)
-        lam = solver.solve(dJdv + Ch * lam_next)
+        rhs = dJdv + Ch * lam_next
+        if m_l:
+            mu = mu_next - A_l @ lam_next
+            rhs = rhs + h * (A_l.T @ (mats.Ldiag_inv * mu))
+        lam = solver.solve(rhs)
         dG -= (_term_adjoint(ra, lam) - _term_adjoint(rb, lam)) * (_term_voltage(ra, v, vd) - _term_voltage(rb, v, vd))
         dC -= lam[cnode] * (V[s][cnode] - V[s - 1][cnode]) / h
+        if m_l:
+            ub = A_l @ v + mats.A_ls @ vd
+            dL += h / Lval ** 2 * ub * (A_l @ lam - mu)
+            mu_next = mu
         lam_next = lam
     # DC point: G v_0 = b_0 depends on the resistors
-    mu = DirectSolver(mats.G.tocsc()).solve(Ch * lam_next)
+    nu = DirectSolver(mats.G.tocsc()).solve(Ch * lam_next)
     v0 = V[0]
-    dG -= (_term_adjoint(ra, mu) - _term_adjoint(rb, mu)) * (_term_voltage(ra, v0, vd) - _term_voltage(rb, v0, vd))
+    dG -= (_term_adjoint(ra, nu) - _term_adjoint(rb, nu)) * (_term_voltage(ra, v0, vd) - _term_voltage(rb, v0, vd))
+    if with_l:
+        return J, dG, dC, dL
     return J, dG, dC

@@ -492,3 +492,79 @@ def test_three_level_from_paper_initial_conditions_tracks_explicit_form():
     V3 = [v for _, v in transient.simulate_three_level(net, h, 40, v0, v1)]
     VE, _ = transient.transient(net, h, 39, v0=v1, il0=il1, s0=1)
     np.testing.assert_allclose(np.stack(V3), VE[1:], rtol=0, atol=1e-11)
+
+
+def _inductive_rlc():
+    """A small RLC grid whose supply path is inductive: the pad resistors are
+    weakened to 0.02 S (they keep the DC point defined) so that the pad
+    inductors (h/L ~ 0.2-2 S) and the via inductors carry the dynamics."""
+    net = pgsynth.config2(nx=6, ny=5)
+    net.r_g = net.r_g.copy()
+    net.r_g[np.asarray(net.r_b) < -1] = 0.02
+    net.i_v = net.i_v.copy() * 20.0
+    # every load starts its ramp 2 ps in, so the drops happen inside the short window
+    net.i_t = net.i_t.copy()
+    ptr = np.asarray(net.i_ptr)
+    for e in range(len(ptr) - 1):
+        net.i_t[ptr[e]:ptr[e + 1]] += 2e-12 - net.i_t[ptr[e]]
+    return net
+
+
+def _objective_difference(net_p, net_m, h, S, vref=1.0, margin=0.05):
+    """J(net_p) - J(net_m) summed term by term over the two trajectories (no
+    cancellation against the size of J)."""
+    from oracle import adjoint
+    Vp, _ = transient.transient(net_p, h, S)
+    Vm, _ = transient.transient(net_m, h, S)
+    sp = adjoint.softplus(vref - Vp[1:] - margin)
+    sm = adjoint.softplus(vref - Vm[1:] - margin)
+    return float(np.sum((sp - sm) * (sp + sm)))
+
+
+def test_rlc_adjoint_matches_central_differences():
+    """The oracle's RLC adjoint (explicit inductor currents, Eq. 10) against central
+    finite differences of the forward objective, for inductors (vias and pad
+    connections), resistors and capacitors, on a grid where the inductors matter
+    (sum_e L_e |dJ/dL_e| is a sizeable fraction of sum_e g_e |dJ/dg_e|)."""
+    from oracle import adjoint
+    net = _inductive_rlc()
+    h, S = net.meta["h"], 60
+    J, dG, dC, dL = adjoint.gradients(net, h, S, with_l=True)
+    assert J == pytest.approx(adjoint.objective(net, h, S), rel=1e-12)
+    Lv = np.asarray(net.l_val)
+    assert np.sum(Lv * np.abs(dL)) > 0.05 * np.sum(np.asarray(net.r_g) * np.abs(dG))
+    rng = np.random.default_rng(11)
+    pad_l = int(np.nonzero(np.asarray(net.l_b) < -1)[0][0])
+    picks = [("l", int(k)) for k in rng.choice(len(net.l_val), 6, replace=False)] + [("l", pad_l)]
+    picks += [("r", int(k)) for k in rng.choice(len(net.r_g), 4, replace=False)]
+    picks += [("c", int(k)) for k in rng.choice(len(net.c_val), 4, replace=False)]
+    field = {"l": "l_val", "r": "r_g", "c": "c_val"}
+    grads = {"l": dL, "r": dG, "c": dC}
+    for kind, k in picks:
+        arr = getattr(net, field[kind])
+        d = 1e-3 * arr[k]
+        nets = []
+        for sgn in (+1, -1):
+            pert = arr.copy(); pert[k] += sgn * d
+            nets.append(pgsynth.Netlist(**{**net.__dict__, field[kind]: pert}))
+        fd = _objective_difference(nets[0], nets[1], h, S) / (2 * d)
+        g = grads[kind][k]
+        # central differences at 1e-3 relative: O(1e-6) truncation; the floor covers
+        # parameters whose gradient is ~1e-6 of the largest of their kind
+        assert g == pytest.approx(fd, rel=1e-4, abs=1e-6 * np.max(np.abs(grads[kind]))), (kind, k, g, fd)
+
+
+def test_rlc_adjoint_scaling_identity():
+    """g -> a g, C -> a C, L -> L / a maps v - Vdd to (v - Vdd)/a and leaves the
+    inductor currents unchanged (Eq. 10 with one supply level), so
+    sum g dJ/dg + sum C dJ/dC - sum L dJ/dL = sum 2 softplus(u) sigmoid(u) (v - Vdd)."""
+    from oracle import adjoint
+    net = _inductive_rlc()
+    h, S = net.meta["h"], 60
+    J, dG, dC, dL = adjoint.gradients(net, h, S, with_l=True)
+    V, _ = transient.transient(net, h, S)
+    u = 1.0 - V[1:] - 0.05
+    rhs = float(np.sum(2.0 * adjoint.softplus(u) * adjoint.sigmoid(u) * (V[1:] - net.vdd[0])))
+    lhs = float(np.dot(net.r_g, dG) + np.dot(net.c_val, dC) - np.dot(net.l_val, dL))
+    assert abs(np.dot(net.l_val, dL)) > 1e-3 * abs(rhs)          # the inductor part is visible
+    assert lhs == pytest.approx(rhs, rel=1e-9)
