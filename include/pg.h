@@ -346,22 +346,25 @@ typedef struct pg_objective {
 } pg_objective;
 
 /*
- * Gradient of a worst-IR-drop objective over an RC transient (no counterpart in
- * the paper; it differentiates the backward-Euler recurrence the paper solves,
- * Eq. 2).  Runs nsteps steps from the DC operating point with a checkpoint every
+ * Gradient of a worst-IR-drop objective over an RC or RLC transient (no
+ * counterpart in the paper; it differentiates the backward-Euler recurrence the
+ * paper solves, Eq. 2 / Eq. 10 with explicit inductor currents).  Runs nsteps
+ * steps from the DC operating point with a checkpoint (v_s, v_{s-1}, i_l) every
  * ckpt_every steps (0 -> 50), then the discrete adjoint backwards:
- *     M lambda_s = dJ/dv_s + (C/h) lambda_{s+1},  lambda_{nsteps+1} = 0,
+ *     mu_s = mu_{s+1} - A_l lambda_{s+1}                      (inductors; mu_nsteps = 0)
+ *     M lambda_s = dJ/dv_s + (C/h) lambda_{s+1} + h A_l^T Ldiag^-1 mu_s,  lambda_{nsteps+1} = 0,
  * each solve by the same relaxation kernel (relative residual 1e-9), recomputing
- * each segment's states from its checkpoint.  Outputs (netlist order, either may
- * be NULL): dJ_dG[n_r] = -sum_s (lambda_a - lambda_b)(v_a - v_b) per resistor,
- * dJ_dC[n_c] = -sum_s lambda_k (v_{s,k} - v_{s-1,k}) / h per capacitor, plus the
- * DC point's own adjoint term when the DC point depends on the resistors.  *J
- * (host) receives the objective.  Host or device outputs per on_host.  The grid's
- * transient state is reset afterwards.  Errors: PG_ERR_UNSUPPORTED for grids with
- * inductors; otherwise as pg_transient.
+ * each segment's states from its checkpoint.  Outputs (netlist order, each may be
+ * NULL): dJ_dG[n_r] = -sum_s (lambda_a - lambda_b)(v_a - v_b) per resistor, plus
+ * the DC point's own adjoint term when the DC point depends on the resistors;
+ * dJ_dC[n_c] = -sum_s lambda_k (v_{s,k} - v_{s-1,k}) / h per capacitor;
+ * dJ_dL[n_l] = (h / L^2) sum_s u_s (lambda_a - lambda_b - mu_s) per inductor,
+ * u_s its branch voltage.  *J (host) receives the objective.  Host or device
+ * outputs per on_host.  The grid's transient state is reset afterwards.  Errors:
+ * PG_ERR_UNSUPPORTED for the three-level form; otherwise as pg_transient.
  */
 pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* obj, int32_t ckpt_every,
-                     double* J, double* dJ_dG, double* dJ_dC, int32_t on_host, pg_run_stats* stats);
+                     double* J, double* dJ_dG, double* dJ_dC, double* dJ_dL, int32_t on_host, pg_run_stats* stats);
 
 /*
  * pg_solve without device allocations.  The paper has no counterpart: this

@@ -115,7 +115,7 @@ def lib(path: Optional[str] = None) -> C.CDLL:
     L.pg_solve.argtypes = [vp, C.c_double, vp, vp, C.c_double, C.POINTER(pg_run_stats)]
     L.pg_solve_noalloc.argtypes = [vp, C.c_double, vp, vp, C.c_double, C.POINTER(pg_run_stats)]
     L.pg_update_values.argtypes = [vp, vp, vp, vp, C.c_int32]
-    L.pg_adjoint.argtypes = [vp, C.c_double, C.c_int32, C.POINTER(pg_objective), C.c_int32, _f64p, vp, vp,
+    L.pg_adjoint.argtypes = [vp, C.c_double, C.c_int32, C.POINTER(pg_objective), C.c_int32, _f64p, vp, vp, vp,
                              C.c_int32, C.POINTER(pg_run_stats)]
     L.pg_transient_async.argtypes = [vp, C.c_double, C.c_int32, vp, C.POINTER(pg_output), vp]
     L.pg_async_stats.argtypes = [vp, vp, C.POINTER(pg_run_stats)]
@@ -310,13 +310,14 @@ def pg_update_values(h, r_g=None, c_val=None, l_val=None):
 
 
 def pg_adjoint(h, step_h: float, nsteps: int, vref: float = 1.0, margin: float = 0.05, ckpt_every: int = 50,
-               dJ_dG=None, dJ_dC=None):
-    """Returns ``(J, stats)``; gradients land in ``dJ_dG`` / ``dJ_dC`` (netlist order)."""
+               dJ_dG=None, dJ_dC=None, dJ_dL=None):
+    """Returns ``(J, stats)``; gradients land in ``dJ_dG`` / ``dJ_dC`` / ``dJ_dL`` (netlist order)."""
     obj = pg_objective(0, float(vref), float(margin))
     J = C.c_double()
     st = pg_run_stats()
     _check(lib().pg_adjoint(h, float(step_h), int(nsteps), C.byref(obj), int(ckpt_every), C.byref(J),
-                            _ptr(dJ_dG), _ptr(dJ_dC), _on_host(dJ_dG, dJ_dC), C.byref(st)), "pg_adjoint")
+                            _ptr(dJ_dG), _ptr(dJ_dC), _ptr(dJ_dL), _on_host(dJ_dG, dJ_dC, dJ_dL), C.byref(st)),
+           "pg_adjoint")
     return J.value, st
 
 

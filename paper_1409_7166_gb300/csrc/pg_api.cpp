@@ -1098,10 +1098,9 @@ pg_status pg_step(pg_grid* g, double h, double* v_out, pg_run_stats* stats) {
 }
 
 pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* obj, int32_t ckpt_every,
-                     double* J, double* dJ_dG, double* dJ_dC, int32_t on_host, pg_run_stats* stats) {
+                     double* J, double* dJ_dG, double* dJ_dC, double* dJ_dL, int32_t on_host, pg_run_stats* stats) {
     if (!g || nsteps < 1 || !obj || ckpt_every < 0) return PG_ERR_INVALID_ARG;
     if (obj->kind != PG_OBJ_SOFTPLUS_DROP) { g_last_error = "unknown objective"; return PG_ERR_INVALID_ARG; }
-    if (g->P.n_l > 0) { g_last_error = "the adjoint covers RC grids (no inductors)"; return PG_ERR_UNSUPPORTED; }
     if (g->opt.form != PG_FORM_EXPLICIT) { g_last_error = "the adjoint needs the explicit form"; return PG_ERR_UNSUPPORTED; }
     const int ck = ckpt_every > 0 ? ckpt_every : 50;
     pg_status s = prepare_h(g, h);
@@ -1122,8 +1121,12 @@ pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* o
     double* acc_l = sc.get<double>(np);
     double* acc_dv = sc.get<double>(np);
     unsigned long long* scale = sc.get<unsigned long long>(1);
+    const int nl = P.n_l;
+    double* ck_il = nl ? sc.get<double>((size_t)nseg * nl) : nullptr;   // i_l at each segment start
+    double* mu_l = nl ? sc.get<double>(nl) : nullptr;                   // inductor multipliers
+    double* acc_L = nl ? sc.get<double>(nl) : nullptr;
     if (!ck_v || !ck_vp || !part || !vseg || !lam || !lam_next || !rhs || !acc_slot || !acc_lv || !acc_l ||
-        !acc_dv || !scale)
+        !acc_dv || !scale || (nl && (!ck_il || !mu_l || !acc_L)))
         return PG_ERR_OOM;
     std::vector<int> ck_have(nseg, 0);
     auto advance = [&](int64_t done) {
@@ -1147,6 +1150,9 @@ pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* o
         const int s0 = k * ck, len = std::min(ck, nsteps - s0);
         CK(cudaMemcpyAsync(ck_v + (size_t)k * np, g->ds.v[g->vL], np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
         CK(cudaMemcpyAsync(ck_vp + (size_t)k * np, g->ds.v[g->vP], np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+        if (nl)
+            CK(cudaMemcpyAsync(ck_il + (size_t)k * nl, g->ds.il, nl * sizeof(double), cudaMemcpyDeviceToDevice,
+                               g->stream));
         ck_have[k] = g->have_prev;
         RunParams rp = base_params(g);
         rp.mode = kModeTransient;
@@ -1180,6 +1186,10 @@ pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* o
     CK(cudaMemsetAsync(acc_lv, 0, np * sizeof(double), g->stream));
     CK(cudaMemsetAsync(acc_l, 0, np * sizeof(double), g->stream));
     CK(cudaMemsetAsync(acc_dv, 0, np * sizeof(double), g->stream));
+    if (nl) {
+        CK(cudaMemsetAsync(mu_l, 0, nl * sizeof(double), g->stream));
+        CK(cudaMemsetAsync(acc_L, 0, nl * sizeof(double), g->stream));
+    }
     const int kb = std::max(1, std::min(g->n_sm * 4, (P.n_slices + 7) / 8));
     for (int k = nseg - 1; k >= 0; --k) {
         const int s0 = k * ck, len = std::min(ck, nsteps - s0);
@@ -1187,6 +1197,9 @@ pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* o
         CK(cudaMemcpyAsync(g->ds.v[0], ck_v + (size_t)k * np, np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
         CK(cudaMemcpyAsync(g->ds.v[1], ck_vp + (size_t)k * np, np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
         CK(cudaMemcpyAsync(vseg, ck_v + (size_t)k * np, np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+        if (nl)
+            CK(cudaMemcpyAsync(g->ds.il, ck_il + (size_t)k * nl, nl * sizeof(double), cudaMemcpyDeviceToDevice,
+                               g->stream));
         g->have_prev = ck_have[k] != 0;
         g->step = s0;
         RunParams rp = base_params(g);
@@ -1201,7 +1214,8 @@ pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* o
             const double* v_s = vseg + (size_t)t * np;
             const double* v_p = vseg + (size_t)(t - 1) * np;
             CK(cudaMemsetAsync(scale, 0, sizeof(unsigned long long), g->stream));
-            CK(launch_adjoint_rhs(g->dg, v_s, lam_next, rhs, obj->vref, obj->margin, scale, kb, g->stream));
+            if (nl) CK(launch_adjoint_mu(g->dg, lam_next, mu_l, kb, g->stream));   // mu_s from lambda_(s+1)
+            CK(launch_adjoint_rhs(g->dg, v_s, lam_next, mu_l, rhs, obj->vref, obj->margin, scale, kb, g->stream));
             RunParams sp = base_params(g);
             sp.mode = kModeSolve;
             sp.nsteps = 1;
@@ -1220,6 +1234,7 @@ pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* o
             const int vF = 3 - g->vL - g->vP;
             CK(cudaMemcpyAsync(lam, g->ds.v[vF], np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
             CK(launch_adjoint_grad(g->dg, lam, v_s, v_p, acc_slot, acc_lv, acc_l, acc_dv, kb, g->stream));
+            if (nl) CK(launch_adjoint_lgrad(g->dg, lam, v_s, mu_l, acc_L, kb, g->stream));
             std::swap(lam, lam_next);
         }
     }
@@ -1304,7 +1319,14 @@ pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* o
         else CK(cudaMemcpy(dst, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice));
         return PG_OK;
     };
-    if ((s = emit(dJ_dG, gG)) || (s = emit(dJ_dC, gC))) return s;
+    std::vector<double> gL(nc.l_val.size(), 0.0);
+    if (nl) {
+        // dJ/dL_e = (h / L_e^2) sum_s u_(s,e) (A_l lambda_s - mu_s)_e
+        std::vector<double> hL(nl);
+        CK(cudaMemcpy(hL.data(), acc_L, nl * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int e = 0; e < nl; ++e) gL[e] = h / (nc.l_val[e] * nc.l_val[e]) * hL[e];
+    }
+    if ((s = emit(dJ_dG, gG)) || (s = emit(dJ_dC, gC)) || (s = emit(dJ_dL, gL))) return s;
     if (stats) {
         double z[kStatCount] = {0};
         z[kStatSteps] = nsteps;

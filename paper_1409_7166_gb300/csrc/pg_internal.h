@@ -218,8 +218,12 @@ cudaError_t launch_lattice_power(const DevGrid& g, const double* x, double* y, c
                                  double* acc, unsigned long long* ymax, int blocks, cudaStream_t stream);
 cudaError_t launch_permute_in(const int32_t* orig, const double* src, double fill, double* dst, int n_pad,
                               int n_sm, cudaStream_t stream);
-cudaError_t launch_adjoint_rhs(const DevGrid& g, const double* v, const double* lam_next, double* rhs, double vref,
-                               double margin, unsigned long long* scale_slot, int blocks, cudaStream_t stream);
+cudaError_t launch_adjoint_rhs(const DevGrid& g, const double* v, const double* lam_next, const double* mu,
+                               double* rhs, double vref, double margin, unsigned long long* scale_slot, int blocks,
+                               cudaStream_t stream);
+cudaError_t launch_adjoint_mu(const DevGrid& g, const double* lam_next, double* mu, int blocks, cudaStream_t stream);
+cudaError_t launch_adjoint_lgrad(const DevGrid& g, const double* lam, const double* v, const double* mu,
+                                 double* acc_L, int blocks, cudaStream_t stream);
 cudaError_t launch_adjoint_grad(const DevGrid& g, const double* lam, const double* v, const double* v_prev,
                                 double* acc_slot, double* acc_lv, double* acc_l, double* acc_dv, int blocks,
                                 cudaStream_t stream);

@@ -1441,8 +1441,10 @@ __global__ void permute_in_kernel(const int32_t* __restrict__ orig, const double
 
 // rhs = dJ/dv_s + (C/h) lambda_{s+1} with dJ/dv = -2 softplus(u) sigmoid(u), u = vref - v - margin;
 // also max |rhs| / D into *scale_slot (sets the relative solve target).
+// With inductors (explicit form, Eq. 10) the rhs also carries h A_l^T Ldiag^-1 mu_s.
 __global__ void __launch_bounds__(256) adjoint_rhs_kernel(DevGrid g, const double* __restrict__ v,
                                                          const double* __restrict__ lam_next,
+                                                         const double* __restrict__ mu,
                                                          double* __restrict__ rhs, double vref, double margin,
                                                          unsigned long long* scale_slot) {
     double m = 0.0;
@@ -1451,6 +1453,13 @@ __global__ void __launch_bounds__(256) adjoint_rhs_kernel(DevGrid g, const doubl
         if (__ldg(g.orig + i) >= 0) {
             const double u = vref - v[i] - margin;
             r = -2.0 * softplus_d(u) * sigmoid_d(u) + __ldg(g.ch + i) * lam_next[i];
+            if (mu)
+                for (int q = __ldg(g.ind_ptr + i); q < __ldg(g.ind_ptr + i + 1); ++q) {
+                    const int lid = __ldg(g.ind_idx + q);
+                    const int e = (lid > 0 ? lid : -lid) - 1;
+                    const double t = __ldg(g.ind_hl + e) * mu[e];
+                    r += lid > 0 ? t : -t;
+                }
             m = fmax(m, fabs(r) * __ldg(g.invD64 + i));
         }
         rhs[i] = r;
@@ -1498,6 +1507,30 @@ __global__ void __launch_bounds__(256) adjoint_grad_kernel(DevGrid g, const doub
     }
 }
 
+// Inductor multipliers of the explicit RLC form: mu_s = mu_(s+1) - A_l lambda_(s+1)
+// (a source or ground terminal carries no multiplier).
+__global__ void __launch_bounds__(256) adjoint_mu_kernel(DevGrid g, const double* __restrict__ lam_next,
+                                                        double* __restrict__ mu) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < g.n_l; e += gridDim.x * blockDim.x) {
+        const int a = __ldg(g.ind_a + e), b = __ldg(g.ind_b + e);
+        mu[e] -= (a >= 0 ? lam_next[a] : 0.0) - (b >= 0 ? lam_next[b] : 0.0);
+    }
+}
+
+// Per inductor: acc_L += u_s (A_l lambda_s - mu_s), u_s = A_l v_s + A_ls v_d (its branch voltage);
+// dJ/dL = (h / L^2) acc_L.
+__global__ void __launch_bounds__(256) adjoint_lgrad_kernel(DevGrid g, const double* __restrict__ lam,
+                                                           const double* __restrict__ v,
+                                                           const double* __restrict__ mu,
+                                                           double* __restrict__ acc_L) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < g.n_l; e += gridDim.x * blockDim.x) {
+        const int a = __ldg(g.ind_a + e), b = __ldg(g.ind_b + e);
+        const double u = term_volt(g, v, a) - term_volt(g, v, b);
+        const double dl = (a >= 0 ? lam[a] : 0.0) - (b >= 0 ? lam[b] : 0.0);
+        acc_L[e] += u * (dl - mu[e]);
+    }
+}
+
 // ---------------------------------------------------------------- host-side launch helpers
 
 // Dynamic shared memory of the persistent kernel: the TMA stages of the FP32 sweep, or
@@ -1531,9 +1564,21 @@ cudaError_t launch_power_step(const DevGrid& g, const double* x, double* y, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_rhs(const DevGrid& g, const double* v, const double* lam_next, double* rhs, double vref,
-                               double margin, unsigned long long* scale_slot, int blocks, cudaStream_t stream) {
-    adjoint_rhs_kernel<<<blocks, 256, 0, stream>>>(g, v, lam_next, rhs, vref, margin, scale_slot);
+cudaError_t launch_adjoint_rhs(const DevGrid& g, const double* v, const double* lam_next, const double* mu,
+                               double* rhs, double vref, double margin, unsigned long long* scale_slot, int blocks,
+                               cudaStream_t stream) {
+    adjoint_rhs_kernel<<<blocks, 256, 0, stream>>>(g, v, lam_next, mu, rhs, vref, margin, scale_slot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_mu(const DevGrid& g, const double* lam_next, double* mu, int blocks, cudaStream_t stream) {
+    adjoint_mu_kernel<<<blocks, 256, 0, stream>>>(g, lam_next, mu);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_lgrad(const DevGrid& g, const double* lam, const double* v, const double* mu,
+                                 double* acc_L, int blocks, cudaStream_t stream) {
+    adjoint_lgrad_kernel<<<blocks, 256, 0, stream>>>(g, lam, v, mu, acc_L);
     return cudaGetLastError();
 }
 

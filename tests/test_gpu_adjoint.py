@@ -1,4 +1,4 @@
-"""pg_adjoint (discrete adjoint of the BE RC transient, not in the paper)
+"""pg_adjoint (discrete adjoint of the BE RC and RLC transient, not in the paper)
 against the oracle's exact adjoint, plus pg_update_values and the
 torch.autograd.Function wrapper.
 
@@ -103,3 +103,50 @@ def test_autograd_function(B):
     assert float(J.detach()) == pytest.approx(J0, rel=1e-8)
     assert _close(r.grad.cpu().numpy() / 2.0, dG0)[0] == 0
     assert _close(c.grad.cpu().numpy() / 2.0, dC0)[0] == 0
+
+
+def _inductive_rlc(nx, ny):
+    """config-2 recipe with an inductive supply path (pad resistors 0.02 S) and every
+    load starting 2 ps in, so that dJ/dL is a sizeable part of the gradient."""
+    net = pgsynth.config2(nx=nx, ny=ny)
+    net.r_g = net.r_g.copy()
+    net.r_g[np.asarray(net.r_b) < -1] = 0.02
+    net.i_v = net.i_v.copy() * 20.0
+    net.i_t = net.i_t.copy()
+    ptr = np.asarray(net.i_ptr)
+    for e in range(len(ptr) - 1):
+        net.i_t[ptr[e]:ptr[e + 1]] += 2e-12 - net.i_t[ptr[e]]
+    return net
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_rlc_adjoint_matches_oracle(B, precision):
+    net = _inductive_rlc(19, 15)
+    h, S = net.meta["h"], 60
+    J0, dG0, dC0, dL0 = oadj.gradients(net, h, S, with_l=True)
+    # default tol: the per-step target of a grid with inductors is 1e-4 tol, which with this
+    # grid's kappa (about 630) is close to what FP64 residuals can certify
+    with B.Grid(net, precision=precision) as g:
+        gG = np.zeros(len(net.r_g)); gC = np.zeros(len(net.c_val)); gL = np.zeros(len(net.l_val))
+        J, st = B.pg_adjoint(g.handle, h, S, ckpt_every=17, dJ_dG=gG, dJ_dC=gC, dJ_dL=gL)
+    assert J == pytest.approx(J0, rel=1e-8)
+    for name, got, ref in (("dJ/dG", gG, dG0), ("dJ/dC", gC, dC0), ("dJ/dL", gL, dL0)):
+        nbad, worst = _close(got, ref)
+        assert nbad == 0, f"{name}: {nbad} entries off, worst {worst:.2e}"
+
+
+def test_autograd_function_rlc(B):
+    from paper_1409_7166_gb300.autograd import IRDropObjective
+    net = _inductive_rlc(13, 11)
+    h, S = net.meta["h"], 40
+    J0, dG0, dC0, dL0 = oadj.gradients(net, h, S, with_l=True)
+    with B.Grid(net) as g:
+        r = torch.tensor(net.r_g, device="cuda", requires_grad=True)
+        c = torch.tensor(net.c_val, device="cuda", requires_grad=True)
+        lv = torch.tensor(net.l_val, device="cuda", requires_grad=True)
+        J = IRDropObjective.apply(g, r, c, h, S, 1.0, 0.05, 50, lv)
+        J.backward()
+    assert float(J.detach()) == pytest.approx(J0, rel=1e-8)
+    assert _close(r.grad.cpu().numpy(), dG0)[0] == 0
+    assert _close(c.grad.cpu().numpy(), dC0)[0] == 0
+    assert _close(lv.grad.cpu().numpy(), dL0)[0] == 0
