@@ -92,8 +92,23 @@ __device__ __forceinline__ T nanmax_t(T a, T b) { return (a > b || a != a) ? a :
 
 // Per-lattice maxima of val over the lane's 4 nodes (warp-collective): one atomic
 // per warp when the slice lies in one lattice (the common case), else per node.
+// Per-lattice maxima of |r|/D (the FP64 passes feed the lattice solve's skip test).
+// A warp's slices are contiguous and almost always inside one lattice, so the
+// warp keeps a running (lattice, max) pair (warp-uniform) and publishes it with
+// one atomic when the lattice changes and at the end of the pass (lat_flush);
+// a slice that straddles lattices publishes its values directly.
+struct LatAcc {
+    int L = -1;
+    double m = 0.0;
+};
+__device__ __forceinline__ void lat_flush(unsigned long long* latR, LatAcc& acc) {
+    if ((threadIdx.x & 31) == 0 && acc.L >= 0 && acc.m != 0.0)
+        atomicMax(latR + acc.L, (unsigned long long)__double_as_longlong(acc.m));
+    acc.L = -1;
+    acc.m = 0.0;
+}
 __device__ __forceinline__ void lattice_max(const DevGrid& g, unsigned long long* latR, int i0,
-                                            const double (&val)[4]) {
+                                            const double (&val)[4], LatAcc& acc) {
     int L[4];
     bool same = true;
     const int L0 = __shfl_sync(0xffffffffu, __ldg(g.node_lat + i0), 0);
@@ -106,8 +121,10 @@ __device__ __forceinline__ void lattice_max(const DevGrid& g, unsigned long long
     }
     if (__all_sync(0xffffffffu, same)) {
         for (int o = 16; o; o >>= 1) m = nanmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if ((threadIdx.x & 31) == 0 && L0 >= 0 && m != 0.0)
-            atomicMax(latR + L0, (unsigned long long)__double_as_longlong(m));
+        if (L0 < 0) return;
+        if (L0 != acc.L) lat_flush(latR, acc);
+        acc.L = L0;
+        acc.m = nanmax(acc.m, m);
     } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
@@ -377,7 +394,7 @@ template <bool MIXED>
 __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* wc, const SliceDesc& sd,
                                             const DevState& st, const RunParams& rp, int s, int lane, int vL, int vP,
                                             int vF, bool extrap, bool three, long long sabs, int dsel,
-                                            unsigned long long* latR) {
+                                            unsigned long long* latR, LatAcc& lacc) {
     const int i0 = s * kSlice + lane * kVec;
     const double* vl = vbuf(st, vL);
     const double* vp = vbuf(st, vP);
@@ -468,7 +485,7 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* w
         sc[j] = fabs(r[j]) * iD[j];
         mon = nanmax(mon, sc[j]);
     }
-    if (latR) lattice_max(g, latR, i0, sc);
+    if (latR) lattice_max(g, latR, i0, sc, lacc);
     st4(vbuf(st, vF) + i0, vw);
     st4(st.r64 + i0, r);
     if (MIXED && rp.lat_k > 0) {
@@ -873,7 +890,7 @@ __device__ double lattice_round(const DevGrid& g, const float* dold, float* dnew
 template <typename T>
 __device__ __forceinline__ double outer_slice(const DevGrid& g, const WarpCache* wc, const SliceDesc& sd,
                                               const DevState& st, const T* d, T* dnext, float* r32, int s, int lane,
-                                              double* v, bool lat, unsigned long long* latR) {
+                                              double* v, bool lat, unsigned long long* latR, LatAcc& lacc) {
     const int i0 = s * kSlice + lane * kVec;
     T dv[4];
     if (lat) {
@@ -926,7 +943,7 @@ __device__ __forceinline__ double outer_slice(const DevGrid& g, const WarpCache*
         sc[j] = fabs(r[j]) * iD[j];
         mon = nanmax(mon, sc[j]);
     }
-    if (latR) lattice_max(g, latR, i0, sc);
+    if (latR) lattice_max(g, latR, i0, sc, lacc);
     st4(st.r64 + i0, r);
     st4(v + i0, vv);
     if (lat) {
@@ -1107,12 +1124,17 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
 
         // ---- phase A: RHS + warm start + residual, all colours
         double mon = 0.0;
-        for (int c = 0; c < g.ncol; ++c)
-            for (int tt = 0; tt < wc->cnt[c]; ++tt) {
-                const int s = wc->lo[c] + tt;
-                mon = nanmax(mon, phase_rhs<MIXED>(g, wc, warp_desc(g, *wc, c, tt, s), st, rp, s, lane, vL, vP, vF,
-                                                   extrap, three, sabs, dsel, lat_buf(lat_par ^ 1)));
-            }
+        {
+            LatAcc lacc;
+            unsigned long long* lb = lat_buf(lat_par ^ 1);
+            for (int c = 0; c < g.ncol; ++c)
+                for (int tt = 0; tt < wc->cnt[c]; ++tt) {
+                    const int s = wc->lo[c] + tt;
+                    mon = nanmax(mon, phase_rhs<MIXED>(g, wc, warp_desc(g, *wc, c, tt, s), st, rp, s, lane, vL, vP,
+                                                       vF, extrap, three, sabs, dsel, lb, lacc));
+                }
+            if (lb) lat_flush(lb, lacc);
+        }
         BarrierResult br = barrier(true, mon);
         if (!br.ok) { publish(-1); return; }
         double R = br.val;
@@ -1187,13 +1209,18 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
             // outer pass
             double m = 0.0;
             T* dn = dbuf<T>(st, dsel ^ 1);
-            for (int c = 0; c < g.ncol; ++c)
-                for (int tt = 0; tt < wc->cnt[c]; ++tt) {
-                    const int s = wc->lo[c] + tt;
-                    m = nanmax(m, outer_slice<T>(g, wc, warp_desc(g, *wc, c, tt, s), st, dd, dn,
-                                                 MIXED ? st.r32 : nullptr, s, lane, vbuf(st, vF),
-                                                 MIXED && rp.lat_k > 0, lat_buf(lat_par ^ 1)));
-                }
+            {
+                LatAcc lacc;
+                unsigned long long* lb = lat_buf(lat_par ^ 1);
+                for (int c = 0; c < g.ncol; ++c)
+                    for (int tt = 0; tt < wc->cnt[c]; ++tt) {
+                        const int s = wc->lo[c] + tt;
+                        m = nanmax(m, outer_slice<T>(g, wc, warp_desc(g, *wc, c, tt, s), st, dd, dn,
+                                                     MIXED ? st.r32 : nullptr, s, lane, vbuf(st, vF),
+                                                     MIXED && rp.lat_k > 0, lb, lacc));
+                    }
+                if (lb) lat_flush(lb, lacc);
+            }
             br = barrier(true, m);
             if (!br.ok) { publish(-1); return; }
             R = br.val;
