@@ -118,6 +118,9 @@ typedef struct pg_options {
                                  on shared-memory tiles with ghost zones, k exact block sweeps per device
                                  barrier.  k > 0 (<= 7): that k; 0 (default): k = 2 for 2-3 layers,
                                  off for 1 layer; < 0: off (neighbour-list point SOR) */
+    int32_t jacobi;           /* 0 (default): coloured Gauss-Seidel / SOR inner sweeps (Eq. 16-17);
+                                 1: damped Jacobi, every node updated from the previous iterate with
+                                 omega <= 1 (default 1), one device barrier per sweep; no lattice solve */
     int32_t form;             /* PG_FORM_EXPLICIT (default): inductor currents kept as state (Eq. 10);
                                  PG_FORM_THREE_LEVEL: the three-level recurrence of Eq. 11 / Eq. 14,
                                  whose state is v(s-1), v(s-2) alone.  A step from a single level (the
@@ -252,10 +255,11 @@ pg_status pg_transient(pg_grid* g, double h, int32_t nsteps, const pg_output* ou
  * and, on each, times trial_steps transient steps from the DC point (best of
  * two runs, CUDA events) for every runtime candidate (inner reduction in {1e-3,
  * 1e-2, 1e-1} when mixed; omega - 1 scaled by {1, 0.97, 0.94} below Young's
- * value when omega is not fixed).  Every trial runs under the certified
+ * value when omega is not fixed), then damped Jacobi (jacobi = 1, omega 1) with
+ * at most 4x the winner's sweeps per step.  Every trial runs under the certified
  * stopping rule of `base` (tol), so only time is compared.  `base` (NULL ->
  * defaults) supplies every other field.  On success *best is `base` with
- * lattice_sweeps, blocks_per_sm, inner_reduction and omega (0 = Young's value;
+ * lattice_sweeps, blocks_per_sm, inner_reduction, jacobi and omega (0 = Young's value;
  * a scaled value is tied to this h) set to the fastest candidate and *best_ms
  * (may be NULL) to its trial time.  stream: cudaStream_t for the trials or
  * NULL.  Errors: PG_ERR_INVALID_ARG, or the last failure when no candidate ran.

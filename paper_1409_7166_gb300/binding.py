@@ -46,7 +46,8 @@ class pg_options(C.Structure):
                 ("step_tol", C.c_double), ("max_sweeps", C.c_int32), ("warm_start", C.c_int32),
                 ("inner_reduction", C.c_double), ("threads_per_block", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("barrier_timeout_s", C.c_double),
-                ("debug_flags", C.c_int32), ("lattice_sweeps", C.c_int32), ("form", C.c_int32)]
+                ("debug_flags", C.c_int32), ("lattice_sweeps", C.c_int32), ("jacobi", C.c_int32),
+                ("form", C.c_int32)]
 
 
 class pg_output(C.Structure):

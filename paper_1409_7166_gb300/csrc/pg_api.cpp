@@ -112,7 +112,8 @@ pg_status alloc_device(pg_grid* g) {
     float* D32lo = g->mixed ? g->alloc<float>(np) : nullptr;
     // lattice column-block inner solve: on by default for multi-layer lattices (the via
     // couplings go into the blocks); single-layer grids measure faster on the SELL sweep
-    const int lat_k = g->opt.lattice_sweeps > 0 ? g->opt.lattice_sweeps
+    const int lat_k = g->opt.jacobi ? 0
+                    : g->opt.lattice_sweeps > 0 ? g->opt.lattice_sweeps
                     : (g->opt.lattice_sweeps == 0 && P.lat_maxnl >= 2 ? 2 : 0);
     std::vector<int32_t> lat_tile0, lat_info;
     std::vector<int64_t> lat_col0;
@@ -331,6 +332,7 @@ RunParams pg::base_params(const pg_grid* g) {
     rp.warm_extrap = g->opt.warm_start;
     rp.lat_k = g->dg.lwE ? g->lat_k : 0;
     rp.three_level = g->opt.form == PG_FORM_THREE_LEVEL;
+    rp.jacobi = g->opt.jacobi;
     return rp;
 }
 
@@ -369,6 +371,12 @@ pg_status run(pg_grid* g, const RunParams& rp, double* stats, float* ms) {
 pg_status solve_internal(pg_grid* g, const double* rhs_perm, double tgt, double* final_R) {
     RunParams rp = base_params(g);
     rp.max_sweeps = std::max(g->opt.max_sweeps, kSetupSweeps);   // setup solves ignore the per-step cap
+    // the stopping-rule constants are properties of M, not of the iteration: setup solves
+    // always take the coloured SOR (its red-black omega when Jacobi runs the steps)
+    if (rp.jacobi) {
+        rp.jacobi = 0;
+        rp.omega = g->sor_omega;
+    }
     rp.mode = kModeSolve;
     rp.nsteps = 1;
     rp.step0 = 0;
@@ -440,6 +448,7 @@ pg_status ensure_dc_grid(pg_grid* g) {
     pg_netlist d = g->nc.dc_view();
     pg_options o = g->opt;          // same precision as the grid (FP64 sweeps are slow on GB300)
     o.omega = 0.0;
+    o.jacobi = 0;                   // the DC network is solved once: coloured SOR
     o.step_tol = 0.5 * g->opt.tol;
     d.lat_nx = g->nc.nx; d.lat_ny = g->nc.ny; d.lat_nl = g->nc.nl;
     d.n_lat = (int32_t)(g->nc.lat_desc.size() / 4);
@@ -521,12 +530,24 @@ pg_status prepare_h(pg_grid* g, double h) {
     if (g->opt.omega > 0.0) {
         g->omega = g->opt.omega;
         g->rho = 0.0;
+    } else if (g->opt.jacobi) {
+        g->omega = 1.0;              // undamped Jacobi unless the caller damps it
+        g->rho = 0.0;
     } else {
         if ((s = g->dg.lwE ? estimate_rho_lattice(g, &g->rho) : estimate_rho(g, &g->rho))) return s;
         const double r = std::min(g->rho, 1.0 - 1e-12);
         // red-black (2-cyclic, consistently ordered; the column blocks of the lattice solve
         // are too): Young's optimum; other colourings use Gauss-Seidel
         g->omega = (g->P.ncol == 2 || g->dg.lwE) ? 2.0 / (1.0 + std::sqrt(1.0 - r * r)) : 1.0;
+    }
+    g->sor_omega = g->omega;
+    if (g->opt.jacobi) {
+        // the setup solves below run the coloured SOR: Young's omega for red-black grids
+        double r = 0.0;
+        if ((s = estimate_rho(g, &r))) return s;
+        r = std::min(r, 1.0 - 1e-12);
+        g->sor_omega = g->P.ncol == 2 ? 2.0 / (1.0 + std::sqrt(1.0 - r * r)) : 1.0;
+        g->rho = r;
     }
     // kappa >= ||M^-1 D||_inf: solve M x = D 1 to max|r|/D <= 1e-3, then bound the remainder.
     g->kappa = 1.0;
@@ -652,6 +673,8 @@ pg_status create_impl(const pg_netlist* nl, const pg_options* opt, std::unique_p
     if (o.threads_per_block != 256) { g_last_error = "threads_per_block must be 256"; return PG_ERR_INVALID_ARG; }
     if (o.barrier_timeout_s <= 0.0) o.barrier_timeout_s = 2.0;
     if (o.lattice_sweeps > 7) { g_last_error = "lattice_sweeps must be <= 7"; return PG_ERR_INVALID_ARG; }
+    if (o.jacobi != 0 && o.jacobi != 1) { g_last_error = "jacobi must be 0 or 1"; return PG_ERR_INVALID_ARG; }
+    if (o.jacobi && o.omega > 1.0) { g_last_error = "damped Jacobi needs omega <= 1"; return PG_ERR_INVALID_ARG; }
     if (o.form != PG_FORM_EXPLICIT && o.form != PG_FORM_THREE_LEVEL) {
         g_last_error = "form must be PG_FORM_EXPLICIT or PG_FORM_THREE_LEVEL";
         return PG_ERR_INVALID_ARG;
@@ -659,7 +682,7 @@ pg_status create_impl(const pg_netlist* nl, const pg_options* opt, std::unique_p
     g->threads = o.threads_per_block;
     g->mixed = o.precision == PG_PREC_MIXED;
     std::string why;
-    pg_status s = build_packed(nl, &g->P, &why, g->mixed ? o.lattice_sweeps : INT32_MIN);
+    pg_status s = build_packed(nl, &g->P, &why, g->mixed && !o.jacobi ? o.lattice_sweeps : INT32_MIN);
     if (s) { g_last_error = why; return s; }
     g->nc.from(nl);
     compute_dc_trivial(g.get());

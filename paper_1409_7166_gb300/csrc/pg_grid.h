@@ -87,6 +87,7 @@ struct pg_grid {
     double h = -1.0;
     double omega = 0.0, rho = 0.0, kappa = 0.0, q = 0.0, step_tol = 0.0, target = 0.0;
     double kacc = 0.0;             // bound of sum_j ||(M^-1 C/h)^j||: per-step errors -> accumulated error
+    double sor_omega = 0.0;        // omega of the setup solves (coloured SOR even when Jacobi runs the steps)
     // transient state
     bool has_state = false;
     int64_t step = 0;

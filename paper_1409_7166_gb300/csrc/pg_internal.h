@@ -201,6 +201,7 @@ struct RunParams {
     double obj_vref, obj_margin;
     int32_t lat_k;            // > 0: lattice inner solve, lat_k exact red-black sweeps per round
     int32_t three_level;      // 1: right-hand side of Eq. 11 (state v(s-1), v(s-2); no i_l)
+    int32_t jacobi;           // 1: damped-Jacobi inner sweeps instead of coloured SOR
 };
 
 }  // namespace pg

@@ -529,6 +529,29 @@ __device__ __forceinline__ double sweep_slice(const DevGrid& g, const WarpCache*
     return (double)mon;
 }
 
+// One damped-Jacobi sweep over a slice: every node from the previous iterate
+// (dold), written to dnew.  Returns max |unrelaxed update|.
+template <typename T>
+__device__ __forceinline__ double jacobi_slice(const DevGrid& g, const WarpCache* wc, const SliceDesc& sd, const T* w,
+                                               const T* invD, const T* r, const T* dold, T* dnew, int s, int lane,
+                                               T omega) {
+    const int i0 = s * kSlice + lane * kVec;
+    T dv[4], rv[4], iD[4], sig[4];
+    ld4(dold + i0, dv);
+    ld4(r + i0, rv);
+    ldg4(invD + i0, iD);
+    sell_row<kSweepUnroll, T>(g, wc, sd, w, s, lane, [&](int c) { return dold[c]; }, sig);
+    T mon = T(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const T upd = (rv[j] + sig[j]) * iD[j] - dv[j];
+        dv[j] = fma(omega, upd, dv[j]);
+        mon = nanmax_t<T>(mon, fabs(upd));
+    }
+    st4(dnew + i0, dv);
+    return (double)mon;
+}
+
 // ---- TMA-fed sweep (FP32 path)
 //
 // The streaming operands of a slice (its K weight slots, its own corrections,
@@ -1176,7 +1199,32 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
                     est_mark = est;
                 }
             }
-            while (!(MIXED && rp.lat_k > 0)) {
+            while (rp.jacobi) {
+                // damped Jacobi: all colours from the previous iterate, one barrier per sweep
+                const T* dold = dbuf<T>(st, dsel);
+                T* dnew = dbuf<T>(st, dsel ^ 1);
+                double m = 0.0;
+                for (int c = 0; c < g.ncol; ++c)
+                    for (int tt = 0; tt < wc->cnt[c]; ++tt) {
+                        const int s = wc->lo[c] + tt;
+                        m = nanmax(m, jacobi_slice<T>(g, wc, warp_desc(g, *wc, c, tt, s), ww, iD, rr, dold, dnew, s,
+                                                      lane, omega));
+                    }
+                const BarrierResult be = barrier(true, m);
+                if (!be.ok) { publish(-1); return; }
+                const double est = be.val;
+                dsel ^= 1;
+                dd = dbuf<T>(st, dsel);
+                ++sweeps;
+                ++inner;
+                if (!(est == est)) { est_nan = true; break; }
+                if (est <= inner_tgt || sweeps >= rp.max_sweeps) break;
+                if ((inner & 15) == 0) {
+                    if (est > 0.9 * est_mark) break;
+                    est_mark = est;
+                }
+            }
+            while (!rp.jacobi && !(MIXED && rp.lat_k > 0)) {
                 double est = 0.0;
                 for (int c = 0; c < g.ncol; ++c) {
                     double m = 0.0;

@@ -38,6 +38,7 @@ extern "C" pg_status pg_autotune(const pg_netlist* nl, const pg_options* base, d
     else reds.push_back(b0.inner_reduction);
 
     double best_t = INFINITY;
+    int32_t best_sweeps_step = 0;       // most sweeps a step of the winner needed
     pg_options win = b0;
     pg_status last = PG_OK;
     for (int32_t k : ks) {
@@ -63,10 +64,12 @@ extern "C" pg_status pg_autotune(const pg_netlist* nl, const pg_options* base, d
                     g->opt.inner_reduction = red;
                     g->omega = 1.0 + (w0 - 1.0) * sc;
                     double t = INFINITY;
+                    int32_t msw = 0;
                     for (int rep = 0; rep < 2 && !s; ++rep) {   // first run warms caches and clocks
                         if ((s = pg_reset(g))) break;
                         if ((s = pg_transient(g, h, trial_steps, nullptr, &st))) break;
                         t = std::min(t, (double)st.device_ms);
+                        msw = std::max(msw, st.max_sweeps_step);
                     }
                     if (s) {
                         last = s;
@@ -75,6 +78,7 @@ extern "C" pg_status pg_autotune(const pg_netlist* nl, const pg_options* base, d
                     }
                     if (t < best_t) {
                         best_t = t;
+                        best_sweeps_step = msw;
                         win = o;
                         win.inner_reduction = red;
                         win.omega = sc == 1.0 ? b0.omega : g->omega;
@@ -82,6 +86,33 @@ extern "C" pg_status pg_autotune(const pg_netlist* nl, const pg_options* base, d
                 }
             }
             g->omega = w0;
+            pg_destroy(g);
+        }
+    }
+    // damped Jacobi (undamped, omega = 1): allowed 4x the winner's sweeps per step, so a
+    // candidate that cannot compete fails fast instead of running to the sweep cap
+    if (std::isfinite(best_t) && b0.jacobi == 0) {
+        pg_options o = b0;
+        o.jacobi = 1;
+        o.lattice_sweeps = -1;
+        o.omega = 0.0;
+        o.max_sweeps = std::max<int32_t>(16, 4 * best_sweeps_step);
+        pg_grid* g = nullptr;
+        pg_run_stats st;
+        if (pg_create_grid(nl, &o, &g) == PG_OK) {
+            if (stream) pg_set_stream(g, stream);
+            double t = INFINITY;
+            pg_status s = pg_transient(g, h, 0, nullptr, &st);
+            for (int rep = 0; rep < 2 && !s; ++rep) {
+                if ((s = pg_reset(g))) break;
+                if ((s = pg_transient(g, h, trial_steps, nullptr, &st))) break;
+                t = std::min(t, (double)st.device_ms);
+            }
+            if (!s && t < best_t) {
+                best_t = t;
+                win = o;
+                win.max_sweeps = b0.max_sweeps;
+            }
             pg_destroy(g);
         }
     }

@@ -94,3 +94,14 @@ def test_valid_netlist_reaches_cuda(B):
         pytest.skip("GPU present: covered by the GPU tests")
     net = pgsynth.config0(nx=8, ny=8)
     assert _create_status(B, net) == "PG_ERR_CUDA"
+
+
+def test_jacobi_option_validation():
+    """Damped Jacobi accepts jacobi in {0, 1} and omega <= 1 only; checked on the
+    host before any device work."""
+    from paper_1409_7166_gb300 import binding as B
+    net = pgsynth.config0(nx=6, ny=5)
+    for bad in (dict(jacobi=2), dict(jacobi=1, omega=1.5)):
+        with pytest.raises(B.PGError) as ei:
+            B.pg_create_grid(net, B.pg_default_options(**bad))
+        assert ei.value.status == B.PG_ERR_INVALID_ARG

@@ -49,7 +49,10 @@ def test_autotune_choice_is_exact(B, case):
     opts = B.options_dict(best)
     assert ms > 0.0 and opts["precision"] == prec
     assert opts["blocks_per_sm"] in (0, 1)
-    if prec == 1:
+    assert opts["jacobi"] in (0, 1)
+    if opts["jacobi"]:
+        assert opts["lattice_sweeps"] == -1
+    elif prec == 1:
         assert opts["lattice_sweeps"] in (-1, 1, 2, 3)
         assert opts["inner_reduction"] in (1e-3, 1e-2, 1e-1)
     else:

@@ -254,3 +254,17 @@ def test_batched_lattices_skip_converged_grids(B):
     assert any(p.lattice[2] == 2 for _, p in parts) and any(p.lattice[2] == 1 for _, p in parts)
     err, st = check_against_oracle(B, net, net.meta["h"], 50, 1)
     assert st.lattice_sweeps == 2
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_damped_jacobi_inner_sweeps(B, precision):
+    """The damped-Jacobi inner sweep (every node from the previous iterate) reaches
+    the same certified solution as the coloured SOR, with more sweeps."""
+    net = pgsynth.config0(nx=33, ny=27)
+    h = net.meta["h"]
+    err, st_j = check_against_oracle(B, net, h, 30, precision, jacobi=1)
+    _, st_s = check_against_oracle(B, net, h, 30, precision)
+    assert st_j.omega == 1.0 and st_j.total_sweeps > st_s.total_sweeps
+    # damping
+    err, st_d = check_against_oracle(B, net, h, 10, precision, jacobi=1, omega=0.8)
+    assert st_d.omega == 0.8
