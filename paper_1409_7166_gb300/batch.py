@@ -114,6 +114,29 @@ def solve_grids_gpu(grids: Sequence, h: float, nsteps: int, device: Optional[int
         return out.cpu().numpy()
 
 
+def scenario_copies(net, load_values: Sequence) -> List[SimpleNamespace]:
+    """Copies of ``net`` that differ only in their load values: copy j draws the PWL
+    currents ``load_values[j]`` (same breakpoints as ``net.i_t``, same length as
+    ``net.i_v``).  Solved together (:func:`solve_grids_gpu`), the scenarios share one
+    persistent launch and its device barriers; each copy keeps its own weights."""
+    fields = ("n_nodes", "vdd", "r_a", "r_b", "r_g", "c_a", "c_b", "c_val", "l_a", "l_b", "l_val",
+              "i_a", "i_b", "i_ptr", "i_t")
+    base = {k: getattr(net, k) for k in fields}
+    out = []
+    for iv in load_values:
+        iv = np.asarray(iv, dtype=np.float64)
+        if iv.shape != np.asarray(net.i_v).shape:
+            raise ValueError("every scenario needs one value per PWL breakpoint")
+        out.append(SimpleNamespace(**base, i_v=iv, lattice=getattr(net, "lattice", None)))
+    return out
+
+
+def solve_scenarios(net, load_values: Sequence, h: float, nsteps: int, **options) -> np.ndarray:
+    """Worst-drop waveform of every load scenario of ``net``: ``[nsteps, len(load_values)]``,
+    all scenarios in one persistent launch on this process's GPU."""
+    return solve_grids_gpu(scenario_copies(net, load_values), h, nsteps, **options)
+
+
 def solve_sharded(grids: Sequence, h: float, nsteps: int,
                   solver: Optional[Callable[[Sequence, float, int], np.ndarray]] = None,
                   costs: Optional[Sequence[float]] = None, **options) -> Optional[np.ndarray]:

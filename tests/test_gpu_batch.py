@@ -52,3 +52,20 @@ def test_sharded_driver_matches_oracle_per_grid(B):
         Vo, _ = transient.transient(p, h, S)
         err = float(np.max(np.abs(res[:, j] - Vo[1:].min(axis=1))))
         assert err <= TOL_V, f"grid {j}: {err:.3e} V"
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_load_scenarios_in_one_launch(B, precision):
+    """Several load scenarios of one grid in one launch: each scenario's worst-drop
+    waveform equals the oracle's for that scenario alone."""
+    net = pgsynth.config0(nx=23, ny=19)
+    h, S = net.meta["h"], 40
+    rng = np.random.default_rng(21)
+    n_src = len(net.i_ptr) - 1
+    scen = [net.i_v * np.repeat(rng.uniform(0.2, 3.0, n_src), np.diff(net.i_ptr)) for _ in range(5)]
+    res = batch.solve_scenarios(net, scen, h, S, precision=precision)
+    assert res.shape == (S, 5)
+    for j, iv in enumerate(scen):
+        Vo, _ = transient.transient(pgsynth.Netlist(**{**net.__dict__, "i_v": iv}), h, S)
+        err = float(np.max(np.abs(res[:, j] - Vo[1:].min(axis=1))))
+        assert err <= TOL_V, f"scenario {j}: {err:.3e} V"
