@@ -106,8 +106,10 @@ typedef struct pg_options {
                                  0.5 tol / kacc (see pg_run_stats), grids with inductors 1e-4 tol */
     int32_t max_sweeps;       /* cap on relaxation sweeps per step (0 -> 20000) */
     int32_t warm_start;       /* 0: V(s-1) as in Algorithm 1; 1: linear extrapolation (default) */
-    double inner_reduction;   /* PG_PREC_MIXED: residual reduction asked of one FP32 inner solve
-                                 (0 -> 1e-3); an inner solve also ends when it stalls */
+    double inner_reduction;   /* PG_PREC_MIXED: residual reduction asked of one FP32 inner solve;
+                                 0 (default) -> 1e-1 for netlists of more than 8 lattices (a batch:
+                                 more frequent FP64 passes let converged grids drop out sooner), else
+                                 1e-3; an inner solve also ends when it stalls */
     int32_t threads_per_block;/* 0 -> 256 */
     int32_t blocks_per_sm;    /* 0 -> as many as fit */
     double barrier_timeout_s; /* device barrier time limit (0 -> 2 s) */

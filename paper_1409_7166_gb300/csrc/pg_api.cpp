@@ -668,7 +668,9 @@ pg_status create_impl(const pg_netlist* nl, const pg_options* opt, std::unique_p
     }
     if (o.tol <= 0.0) o.tol = 1e-6;
     if (o.max_sweeps <= 0) o.max_sweeps = 20000;
-    if (o.inner_reduction <= 0.0) o.inner_reduction = 1e-3;
+    // 0 = by grid class (what pg_autotune finds): batches of many lattices take more frequent
+    // FP64 passes, whose per-lattice residuals let converged grids drop out of the inner solve
+    if (o.inner_reduction <= 0.0) o.inner_reduction = nl && nl->n_lat > 8 ? 1e-1 : 1e-3;
     if (o.threads_per_block <= 0) o.threads_per_block = 256;
     if (o.threads_per_block != 256) { g_last_error = "threads_per_block must be 256"; return PG_ERR_INVALID_ARG; }
     if (o.barrier_timeout_s <= 0.0) o.barrier_timeout_s = 2.0;
@@ -733,7 +735,7 @@ void pg_default_options(pg_options* o) {
     o->step_tol = 0.0;
     o->max_sweeps = 20000;
     o->warm_start = 1;
-    o->inner_reduction = 1e-3;
+    o->inner_reduction = 0.0;
     o->threads_per_block = 256;
     o->blocks_per_sm = 0;
     o->barrier_timeout_s = 2.0;

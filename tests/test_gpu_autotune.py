@@ -56,7 +56,7 @@ def test_autotune_choice_is_exact(B, case):
         assert opts["lattice_sweeps"] in (-1, 1, 2, 3)
         assert opts["inner_reduction"] in (1e-3, 1e-2, 1e-1)
     else:
-        assert opts["lattice_sweeps"] == 0 and opts["inner_reduction"] == 1e-3
+        assert opts["lattice_sweeps"] == 0 and opts["inner_reduction"] == 0.0   # by grid class
     assert opts["omega"] == 0.0 or 1.0 < opts["omega"] < 2.0
     st = _parity(B, net, h, 50, opts)
     if opts["omega"] > 0.0:
