@@ -184,6 +184,8 @@ pg_status alloc_device(pg_grid* g) {
         CK(cudaMemsetAsync(st.v[k], 0, np * sizeof(double), g->stream));
     }
     st.il = g->alloc<double>(P.n_l);
+    st.md = g->alloc<double>(np);
+    if (!st.md) return PG_ERR_OOM;
     d.n_src = (int32_t)(P.pwl_ptr.size() - 1);
     st.isrc = g->alloc<double>(2 * (size_t)std::max(d.n_src, 1));
     if (!st.isrc) return PG_ERR_OOM;
@@ -333,6 +335,7 @@ RunParams pg::base_params(const pg_grid* g) {
     rp.lat_k = g->dg.lwE ? g->lat_k : 0;
     rp.three_level = g->opt.form == PG_FORM_THREE_LEVEL;
     rp.jacobi = g->opt.jacobi;
+    rp.inc_start = g->inc_ok && g->have_prev;
     return rp;
 }
 
@@ -361,6 +364,9 @@ pg_status run(pg_grid* g, const RunParams& rp, double* stats, float* ms) {
     CK(cudaMemcpyAsync(stats, g->dc.stats, kStatCount * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
     if (ms) CK(cudaEventElapsedTime(ms, g->ev0, g->ev1));
+    // the final residual and M d of an explicit transient carry into the next launch
+    g->inc_ok = err == 0 && rp.mode == kModeTransient && !rp.three_level && stats[kStatSteps] >= 1.0 &&
+                stats[kStatSteps] == (double)rp.nsteps;
     if (err == PG_ERR_TIMEOUT) { g_last_error = "device barrier timed out"; return PG_ERR_TIMEOUT; }
     if (err == PG_ERR_NOT_CONVERGED) { g_last_error = "relaxation did not converge"; return PG_ERR_NOT_CONVERGED; }
     if (err != 0) { g_last_error = "device error"; return PG_ERR_CUDA; }
@@ -597,6 +603,7 @@ pg_status prepare_h(pg_grid* g, double h) {
 
 pg_status set_state_host(pg_grid* g, const double* v, const double* il, int64_t step) {
     const Packed& P = g->P;
+    g->inc_ok = false;
     std::vector<double> vp(P.n_pad, 0.0);
     for (int i = 0; i < P.n_pad; ++i)
         if (P.orig[i] >= 0) vp[i] = v[P.orig[i]];
@@ -616,6 +623,7 @@ pg_status set_state_host(pg_grid* g, const double* v, const double* il, int64_t 
 
 // State from a device vector in caller numbering (src) or a constant (src == nullptr).
 pg_status set_state_device(pg_grid* g, const double* src, double fill, const double* il, int64_t step) {
+    g->inc_ok = false;
     g->vL = 0; g->vP = 1;
     CK(launch_permute_in(g->dg.orig, src, fill, g->ds.v[0], g->P.n_pad, g->n_sm, g->stream));
     if (g->P.n_l) {
@@ -797,6 +805,7 @@ pg_status pg_grid_info(const pg_grid* g, int32_t* n, int32_t* nl, int32_t* ncol,
 
 pg_status pg_initial_conditions(pg_grid* g, double h, const double* vc0, const double* il0, int32_t on_host) {
     if (!g) return PG_ERR_INVALID_ARG;
+    g->inc_ok = false;              // the carried step-start data no longer match
     pg_status s = prepare_h(g, h);
     if (s) return s;
     const NetCopy& nc = g->nc;
@@ -874,12 +883,14 @@ pg_status pg_get_state(pg_grid* g, double* v, double* il, int64_t* step, int32_t
 
 pg_status pg_reset(pg_grid* g) {
     if (!g) return PG_ERR_INVALID_ARG;
+    g->inc_ok = false;              // the carried step-start data no longer match
     g->has_state = false;
     return PG_OK;
 }
 
 pg_status pg_update_sources(pg_grid* g, const double* i_t, const double* i_v, int32_t on_host) {
     if (!g) return PG_ERR_INVALID_ARG;
+    g->inc_ok = false;              // the carried step-start data no longer match
     const size_t m = g->P.pwl_t.size();
     if (m == 0) return PG_OK;
     auto pull = [&](const double* src, std::vector<double>& dst) -> pg_status {
@@ -913,6 +924,7 @@ pg_status pg_update_sources(pg_grid* g, const double* i_t, const double* i_v, in
 
 pg_status pg_update_values(pg_grid* g, const double* r_g, const double* c_val, const double* l_val, int32_t on_host) {
     if (!g) return PG_ERR_INVALID_ARG;
+    g->inc_ok = false;              // the carried step-start data no longer match
     NetCopy& nc = g->nc;
     auto pull = [&](const double* src, std::vector<double>& dst) -> pg_status {
         if (!src || dst.empty()) return PG_OK;
@@ -1148,6 +1160,12 @@ pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* o
     unsigned long long* scale = sc.get<unsigned long long>(1);
     const int nl = P.n_l;
     double* ck_il = nl ? sc.get<double>((size_t)nseg * nl) : nullptr;   // i_l at each segment start
+    // the step-start residual and M d carried across launches, so that a replayed segment
+    // repeats the forward pass exactly whatever the checkpoint spacing
+    double* ck_r = sc.get<double>((size_t)nseg * np);
+    double* ck_md = sc.get<double>((size_t)nseg * np);
+    if (!ck_r || !ck_md) return PG_ERR_OOM;
+    std::vector<char> ck_inc(nseg, 0);
     double* mu_l = nl ? sc.get<double>(nl) : nullptr;                   // inductor multipliers
     double* acc_L = nl ? sc.get<double>(nl) : nullptr;
     if (!ck_v || !ck_vp || !part || !vseg || !lam || !lam_next || !rhs || !acc_slot || !acc_lv || !acc_l ||
@@ -1179,6 +1197,9 @@ pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* o
             CK(cudaMemcpyAsync(ck_il + (size_t)k * nl, g->ds.il, nl * sizeof(double), cudaMemcpyDeviceToDevice,
                                g->stream));
         ck_have[k] = g->have_prev;
+        CK(cudaMemcpyAsync(ck_r + (size_t)k * np, g->ds.r64, np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+        CK(cudaMemcpyAsync(ck_md + (size_t)k * np, g->ds.md, np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+        ck_inc[k] = g->inc_ok;
         RunParams rp = base_params(g);
         rp.mode = kModeTransient;
         rp.nsteps = len;
@@ -1227,6 +1248,9 @@ pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* o
                                g->stream));
         g->have_prev = ck_have[k] != 0;
         g->step = s0;
+        CK(cudaMemcpyAsync(g->ds.r64, ck_r + (size_t)k * np, np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+        CK(cudaMemcpyAsync(g->ds.md, ck_md + (size_t)k * np, np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+        g->inc_ok = ck_inc[k] != 0;
         RunParams rp = base_params(g);
         rp.mode = kModeTransient;
         rp.nsteps = len;

@@ -93,6 +93,7 @@ struct pg_grid {
     int64_t step = 0;
     int vL = 0, vP = 1;
     bool have_prev = false;
+    bool inc_ok = false;          // r64 and md hold the last step's final residual and M d (see run)
     bool dc_trivial = false;      // DC point is v = Vdd everywhere (see compute_dc_trivial)
     double dc_vdd = 0.0;
     std::unique_ptr<pg_grid> dcgrid;  // DC sub-problem, built on first use

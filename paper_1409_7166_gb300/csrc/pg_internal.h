@@ -144,6 +144,7 @@ struct DevState {
     float* d32[2];           // correction buffers (FP32 sweeps)
     const double* rhs;       // kModeSolve: right-hand side (permuted)
     double* isrc;            // [2 x n_src] load currents I_e(S h), slot S & 1 (transient mode)
+    double* md;              // [n_pad] M (v(s) - v(s-1)) by the end of step s (incremental step start)
 };
 
 struct DevCtl {
@@ -202,6 +203,7 @@ struct RunParams {
     int32_t lat_k;            // > 0: lattice inner solve, lat_k exact red-black sweeps per round
     int32_t three_level;      // 1: right-hand side of Eq. 11 (state v(s-1), v(s-2); no i_l)
     int32_t jacobi;           // 1: damped-Jacobi inner sweeps instead of coloured SOR
+    int32_t inc_start;        // 1: the residual and M d of the previous launch's last step are current
 };
 
 }  // namespace pg

@@ -33,6 +33,7 @@
 #define PG_SWEEP_UNROLL 4
 #endif
 constexpr int kSweepUnroll = PG_SWEEP_UNROLL;
+constexpr int kIncPeriod = 16;        // full recompute of the step-start residual every 16 steps
 
 namespace pg {
 
@@ -389,11 +390,29 @@ __device__ __forceinline__ void sell_row_df(const DevGrid& g, const WarpCache* w
 
 // ---------------------------------------------------------------- phases
 
+// md = M (x0 - v(s-1)) for a step whose start residual is computed in full: M (v(s-1) -
+// v(s-2)) with the extrapolated warm start, 0 without.
+__device__ __forceinline__ void md_slice(const DevGrid& g, const WarpCache* wc, const SliceDesc& sd, const DevState& st,
+                                         int s, int lane, const double* vl, const double* vp, bool extrap) {
+    const int i0 = s * kSlice + lane * kVec;
+    double m[4] = {0.0, 0.0, 0.0, 0.0};
+    if (extrap) {
+        double sig[4], D[4], a[4], p[4];
+        sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return vl[c] - vp[c]; }, sig);
+        ldg4(g.D64 + i0, D);
+        ld4(vl + i0, a);
+        ld4(vp + i0, p);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) m[j] = D[j] * (a[j] - p[j]) - sig[j];
+    }
+    st4(st.md + i0, m);
+}
+
 // Start of a step: RHS assembly (Eq. 2 / Eq. 10), warm start, FP64 residual.
 template <bool MIXED>
 __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* wc, const SliceDesc& sd,
                                             const DevState& st, const RunParams& rp, int s, int lane, int vL, int vP,
-                                            int vF, bool extrap, bool three, long long sabs, int dsel,
+                                            int vF, bool extrap, bool three, bool inc, long long sabs, int dsel,
                                             unsigned long long* latR, LatAcc& lacc) {
     const int i0 = s * kSlice + lane * kVec;
     const double* vl = vbuf(st, vL);
@@ -406,8 +425,9 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* w
         ldg4(st.rhs + i0, b);
         if (rp.x0) ldg4(rp.x0 + i0, vw);
         else vw[0] = vw[1] = vw[2] = vw[3] = 0.0;
-    } else if (three) {
-        // Eq. 11 less M v(s-1), an exact rearrangement:
+    } else if (three || inc) {
+        // Eq. 11 less M v(s-1), an exact rearrangement (the explicit form's incremental step
+        // start adds the previous step's final residual to the same increment):
         //   b - M v(s-1) = (C/h)(v(s-1) - v(s-2)) - A_l^T h L^-1 (A_l v(s-1) + A_ls v_d)
         //                  - A_i^T (I_s(t) - I_s(t-h)),
         // and the residual of x0 is that minus M (x0 - v(s-1)).
@@ -467,21 +487,34 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* w
         }
     }
     double sig[4];
+    // explicit transient steps keep md = M (x0 - v(s-1)) (the outer passes add M delta)
+    const bool track = rp.mode == kModeTransient && !three && st.md != nullptr;
+    double mdv[4] = {0.0, 0.0, 0.0, 0.0};
     if (rp.mode == kModeSolve) {
         if (rp.x0) sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return __ldg(rp.x0 + c); }, sig);
         else sig[0] = sig[1] = sig[2] = sig[3] = 0.0;
     } else if (three) {
         if (extrap) sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return vl[c] - vp[c]; }, sig);
         else sig[0] = sig[1] = sig[2] = sig[3] = 0.0;
+    } else if (inc) {
+        // r = r_final(s-1) + increment - M (x0 - v(s-1)), the last term carried in md
+        double rp_[4];
+        ld4(st.r64 + i0, rp_);
+        if (extrap) ld4(st.md + i0, mdv);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] += rp_[j] - mdv[j];
+        sig[0] = sig[1] = sig[2] = sig[3] = 0.0;
     } else if (extrap) {
         sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return 2.0 * vl[c] - vp[c]; }, sig);
     } else {
         sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return vl[c]; }, sig);
     }
+    // a full step's md (M (x0 - v(s-1))) is written by md_slice before phase A
+    if (track && inc && !extrap) st4(st.md + i0, mdv);
     double r[4], sc[4], mon = 0.0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        r[j] = b[j] + sig[j] - D[j] * (vw[j] - base[j]);
+        r[j] = inc ? b[j] : b[j] + sig[j] - D[j] * (vw[j] - base[j]);
         sc[j] = fabs(r[j]) * iD[j];
         mon = nanmax(mon, sc[j]);
     }
@@ -913,7 +946,8 @@ __device__ double lattice_round(const DevGrid& g, const float* dold, float* dnew
 template <typename T>
 __device__ __forceinline__ double outer_slice(const DevGrid& g, const WarpCache* wc, const SliceDesc& sd,
                                               const DevState& st, const T* d, T* dnext, float* r32, int s, int lane,
-                                              double* v, bool lat, unsigned long long* latR, LatAcc& lacc) {
+                                              double* v, bool lat, unsigned long long* latR, LatAcc& lacc,
+                                              double* md) {
     const int i0 = s * kSlice + lane * kVec;
     T dv[4];
     if (lat) {
@@ -957,6 +991,13 @@ __device__ __forceinline__ double outer_slice(const DevGrid& g, const WarpCache*
         sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return (double)d[c]; }, sig);
 #pragma unroll
         for (int j = 0; j < 4; ++j) Md[j] = D[j] * (double)dv[j] - sig[j];
+    }
+    if (md) {
+        double m4[4];
+        ld4(md + i0, m4);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) m4[j] += Md[j];
+        st4(md + i0, m4);
     }
     double mon = 0.0, sc[4];
 #pragma unroll
@@ -1133,7 +1174,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
     };
     if (rp.mode == kModeTransient && g.n_src > 0 && rp.nsteps > 0) {
         eval_sources(rp.step0 + 1);
-        if (rp.three_level) eval_sources(rp.step0);
+        if (rp.three_level || rp.inc_start) eval_sources(rp.step0);   // the load increment I(t) - I(t - h)
         if (!barrier(false, 0.0).ok) { publish(-1); return; }
     }
 
@@ -1142,11 +1183,25 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
         const bool extrap = rp.mode == kModeTransient && rp.warm_extrap && have_prev;
         // Eq. 11 needs two levels; a step from a single level is an ordinary backward-Euler step
         const bool three = rp.mode == kModeTransient && rp.three_level && have_prev;
+        // explicit form: the step start adds the increment to the previous final residual
+        // except every kIncPeriod-th step (by absolute index, so chunked runs repeat a single
+        // launch exactly), which recomputes it (bounds the drift of rounding)
+        const bool inc = rp.mode == kModeTransient && !rp.three_level && have_prev && st.md != nullptr &&
+                         (sl > 0 || rp.inc_start) && (sabs % kIncPeriod) != 0;
         int dsel = 0;
         if (sl > 0) { finalize_vmin(sl - 1); finalize_comp(sl - 1); }
 
         // ---- phase A: RHS + warm start + residual, all colours
         double mon = 0.0;
+        if (rp.mode == kModeTransient && !three && !inc && st.md != nullptr) {
+            const double* vlp = vbuf(st, vL);
+            const double* vpp = vbuf(st, vP);
+            for (int c = 0; c < g.ncol; ++c)
+                for (int tt = 0; tt < wc->cnt[c]; ++tt) {
+                    const int s = wc->lo[c] + tt;
+                    md_slice(g, wc, warp_desc(g, *wc, c, tt, s), st, s, lane, vlp, vpp, extrap);
+                }
+        }
         {
             LatAcc lacc;
             unsigned long long* lb = lat_buf(lat_par ^ 1);
@@ -1154,7 +1209,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
                 for (int tt = 0; tt < wc->cnt[c]; ++tt) {
                     const int s = wc->lo[c] + tt;
                     mon = nanmax(mon, phase_rhs<MIXED>(g, wc, warp_desc(g, *wc, c, tt, s), st, rp, s, lane, vL, vP,
-                                                       vF, extrap, three, sabs, dsel, lb, lacc));
+                                                       vF, extrap, three, inc, sabs, dsel, lb, lacc));
                 }
             if (lb) lat_flush(lb, lacc);
         }
@@ -1265,7 +1320,8 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
                         const int s = wc->lo[c] + tt;
                         m = nanmax(m, outer_slice<T>(g, wc, warp_desc(g, *wc, c, tt, s), st, dd, dn,
                                                      MIXED ? st.r32 : nullptr, s, lane, vbuf(st, vF),
-                                                     MIXED && rp.lat_k > 0, lb, lacc));
+                                                     MIXED && rp.lat_k > 0, lb, lacc,
+                                                     rp.mode == kModeTransient && !three ? st.md : nullptr));
                     }
                 if (lb) lat_flush(lb, lacc);
             }
