@@ -80,6 +80,8 @@ pg_status alloc_device(pg_grid* g) {
     const int np = P.n_pad;
     DevGrid& d = g->dg;
     d.n_pad = np; d.ncol = P.ncol; d.n_slices = P.n_slices; d.n_real = P.n;
+    d.natural = P.ncol == 1;
+    for (int i = 0; i < P.n && d.natural; ++i) d.natural = P.orig[i] == i;
     std::vector<int32_t> cs(P.ncol + 1);
     for (int c = 0; c <= P.ncol; ++c) cs[c] = P.colour_start[c] / kSlice;
     int32_t* colour_slice = g->alloc<int32_t>(cs.size());
@@ -197,6 +199,10 @@ pg_status alloc_device(pg_grid* g) {
         st.d32[0] = g->alloc<float>(np);
         st.d32[1] = g->alloc<float>(np);
         if (!st.r32 || !st.d32[0] || !st.d32[1]) return PG_ERR_OOM;
+        // padding entries are never written by the lattice solve: they stay zero
+        CK(cudaMemsetAsync(st.d32[0], 0, np * sizeof(float), g->stream));
+        CK(cudaMemsetAsync(st.d32[1], 0, np * sizeof(float), g->stream));
+        CK(cudaMemsetAsync(st.r32, 0, np * sizeof(float), g->stream));
     } else {
         st.d64[0] = g->alloc<double>(np);
         st.d64[1] = g->alloc<double>(np);

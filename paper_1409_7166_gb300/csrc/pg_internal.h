@@ -128,6 +128,7 @@ struct DevGrid {
     const float* lwU;        // weight to (x, y, l+1)
     const float* lm;         // column block (via couplings): Thomas multiplier u_{l-1} / d'_{l-1} (0 for l = 0)
     const float* lip;        // column block: inverse Thomas pivot 1 / d'_l
+    int32_t natural;         // 1: the permutation is the identity on the real nodes (padding after them)
     // connected components (independent sub-circuits, Fig. 1)
     int32_t n_comp;
     const int32_t* node_comp;   // [n_pad] component of each permuted node, -1 for padding

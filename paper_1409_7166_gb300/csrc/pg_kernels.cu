@@ -521,7 +521,7 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* w
     if (latR) lattice_max(g, latR, i0, sc, lacc);
     st4(vbuf(st, vF) + i0, vw);
     st4(st.r64 + i0, r);
-    if (MIXED && rp.lat_k > 0) {
+    if (MIXED && rp.lat_k > 0 && !g.natural) {
         // the lattice inner solve keeps its FP32 residual and correction in caller order
         float* dz = dbuf<float>(st, dsel);
 #pragma unroll
@@ -1320,7 +1320,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
                         const int s = wc->lo[c] + tt;
                         m = nanmax(m, outer_slice<T>(g, wc, warp_desc(g, *wc, c, tt, s), st, dd, dn,
                                                      MIXED ? st.r32 : nullptr, s, lane, vbuf(st, vF),
-                                                     MIXED && rp.lat_k > 0, lb, lacc,
+                                                     MIXED && rp.lat_k > 0 && !g.natural, lb, lacc,
                                                      rp.mode == kModeTransient && !three ? st.md : nullptr));
                     }
                 if (lb) lat_flush(lb, lacc);
