@@ -284,10 +284,10 @@ def main():
     alg = [algorithmic_bytes(s, n, mn, n_src, True, nsteps) for s in stats]
     achieved = sum(alg) / (sum(dev_ms) / 1e3) / 1e9
     # DRAM traffic per launch: ncu measured dram__bytes_read.sum + dram__bytes_write.sum =
-    # 9.61 GB on a 2-step launch of this grid whose algorithmic bytes are 23.9 GB (the
+    # 9.17 GB on a 2-step launch of this grid whose algorithmic bytes are 23.9 GB (the
     # full 1000-step launch is too long to capture); scaled to the timed launch by its
     # algorithmic bytes.  Valid for the kernel as captured; re-capture after kernel changes.
-    traffic_ratio = 9.61 / 23.9 if (args.nx, args.ny) == (1024, 1024) else None
+    traffic_ratio = 9.17 / 23.9 if (args.nx, args.ny) == (1024, 1024) else None
     bpl = sum(alg) / len(alg)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": bpl * traffic_ratio if traffic_ratio else None,
