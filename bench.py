@@ -220,7 +220,10 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    build()
+    if local == 0:
+        build()                                        # one compile per node (a no-op when current)
+    if dist:
+        dist.barrier()
     B.lib()
 
     net = pgsynth.config1(nx=args.nx, ny=args.ny)
