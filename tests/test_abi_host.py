@@ -105,3 +105,14 @@ def test_jacobi_option_validation():
         with pytest.raises(B.PGError) as ei:
             B.pg_create_grid(net, B.pg_default_options(**bad))
         assert ei.value.status == B.PG_ERR_INVALID_ARG
+
+
+def test_degenerate_netlists(B):
+    """An empty netlist is invalid; a sub-circuit with no source at all, or a node
+    held only by a capacitor, has no DC point (Lemma 1 needs a strictly dominant row
+    in DC) and is rejected as floating."""
+    assert _create_status(B, make_netlist(0, [1.0])) == "PG_ERR_INVALID_ARG"
+    no_source = make_netlist(2, [], R=[(0, 1, 1.0)], C=[(0, GROUND, 1e-15), (1, GROUND, 1e-15)])
+    assert _create_status(B, no_source) == "PG_ERR_FLOATING_NODE"
+    cap_only = make_netlist(1, [1.0], C=[(0, GROUND, 1e-15)])
+    assert _create_status(B, cap_only) == "PG_ERR_FLOATING_NODE"

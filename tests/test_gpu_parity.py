@@ -268,3 +268,29 @@ def test_damped_jacobi_inner_sweeps(B, precision):
     # damping
     err, st_d = check_against_oracle(B, net, h, 10, precision, jacobi=1, omega=0.8)
     assert st_d.omega == 0.8
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_grid_without_capacitors(B, precision):
+    """No capacitors: M = G + G0 and every step is a DC solve at the step's loads
+    (q = 0, accumulation gain 1)."""
+    net = pgsynth.config0(nx=19, ny=14)
+    for k in ("c_a", "c_b"):
+        setattr(net, k, np.zeros(0, np.int32))
+    net.c_val = np.zeros(0)
+    err, st = check_against_oracle(B, net, net.meta["h"], 25, precision)
+    assert st.q == 0.0 and st.kacc == 1.0
+
+
+def test_lattices_smaller_than_a_tile(B):
+    """Lattice inner solve on lattices smaller than one tile's interior (24 x 24
+    columns for k = 2), alone and batched with a larger one."""
+    from paper_1409_7166_gb300 import batch
+    tiny = pgsynth.config1(nx=5, ny=3)
+    check_against_oracle(B, tiny, tiny.meta["h"], 20, 1, lattice_sweeps=2)
+    parts = [pgsynth.config1(nx=5, ny=3), pgsynth.config1(nx=30, ny=27), pgsynth.config1(nx=2, ny=7)]
+    net = batch.concat(parts)
+    Vo, _ = transient.transient(net, tiny.meta["h"], 20)
+    V, _, _, _, st = run_gpu(B, net, tiny.meta["h"], 20, 1, lattice_sweeps=2)
+    assert st.lattice_sweeps == 2
+    assert np.max(np.abs(V - Vo[1:])) <= TOL_V
