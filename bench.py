@@ -112,19 +112,24 @@ def algorithmic_bytes(st, n, mn, n_src, mixed: bool, nsteps: int, extrap: bool =
     per node-sweep (FP32 column-block sweep):      20 + 4 m/n  (the block's two Thomas factors
                                                                  replace 1/D)
     per node-sweep (FP64 sweep):                   32 + 8 m/n
-    per node, outer FP64 pass:   52 + 8 m/n (mixed) or 56 + 8 m/n (FP64)
-    per node, step start (RHS, warm start, residual): 56 + 8 m/n (+8 with extrapolation)
-                                  + 56 B per PWL source (index + 3 breakpoints)
+    per node, outer FP64 pass:   52 + 8 m/n (mixed) or 56 + 8 m/n (FP64), plus 16 for the
+                                  carried M d (read and write)
+    per node, step start in full (RHS, warm start, residual): 56 + 8 m/n (+8 with extrapolation)
+                                  + 56 B per PWL source; one step in 16
+    per node, incremental step start (v(s-1), v(s-2), C/h, r_final, M d, 1/D read; v, r, the
+                                  FP32 residual and correction written): 72, + 56 B per PWL source
     per node, step end (read v once for the outputs): 8
     """
     if mixed:
         sweep_b = (20 + 4 * mn) if st.get("lattice_sweeps", 0) > 0 else (16 + 4 * mn)
     else:
         sweep_b = 32 + 8 * mn
-    outer_b = (52 if mixed else 56) + 8 * mn
-    start_b = 56 + (8 if extrap else 0) + 8 * mn
+    outer_b = (52 if mixed else 56) + 8 * mn + 16
+    full_b = 56 + (8 if extrap else 0) + 8 * mn
+    n_full = (nsteps + 15) // 16                      # every 16th step (by absolute index) in full
+    start = n_full * full_b + (nsteps - n_full) * 72
     return (st["total_sweeps"] * sweep_b * n + st["total_outer"] * outer_b * n
-            + nsteps * (start_b * n + 56 * n_src + 8 * n))
+            + start * n + nsteps * (56 * n_src + 8 * n))
 
 
 # ------------------------------------------------------------------ reference arm (the CPU oracle)
@@ -287,10 +292,12 @@ def main():
     alg = [algorithmic_bytes(s, n, mn, n_src, True, nsteps) for s in stats]
     achieved = sum(alg) / (sum(dev_ms) / 1e3) / 1e9
     # DRAM traffic per launch: ncu measured dram__bytes_read.sum + dram__bytes_write.sum =
-    # 9.17 GB on a 2-step launch of this grid whose algorithmic bytes are 23.9 GB (the
-    # full 1000-step launch is too long to capture); scaled to the timed launch by its
+    # 9.17 GB on a 2-step launch of this grid (232 block sweeps, 4 outer passes; the full
+    # 1000-step launch is too long to capture); scaled to the timed launch by the ratio of
     # algorithmic bytes.  Valid for the kernel as captured; re-capture after kernel changes.
-    traffic_ratio = 9.17 / 23.9 if (args.nx, args.ny) == (1024, 1024) else None
+    captured = algorithmic_bytes({"total_sweeps": 232, "total_outer": 4, "lattice_sweeps": 2}, n, mn, n_src,
+                                 True, 2)
+    traffic_ratio = 9.17e9 / captured if (args.nx, args.ny) == (1024, 1024) else None
     bpl = sum(alg) / len(alg)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": bpl * traffic_ratio if traffic_ratio else None,
