@@ -352,6 +352,7 @@ def main():
                             "device barrier" if stats[0]["lattice_sweeps"] > 0 else
                             "neighbour-list (SELL) red-black SOR"),
             "setup_s": setup_s,
+            "transient_ms": {"best": min(ms), "median": float(sorted(ms)[len(ms) // 2]), "mean": sum(ms) / len(ms)},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
