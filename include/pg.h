@@ -118,8 +118,9 @@ typedef struct pg_options {
                                  branches only between lattice neighbours): the inner solve becomes
                                  column-block red-black SOR (each (x, y) column's layers solved exactly)
                                  on shared-memory tiles with ghost zones, k exact block sweeps per device
-                                 barrier.  k > 0 (<= 7): that k; 0 (default): k = 2 for 2-3 layers,
-                                 off for 1 layer; < 0: off (neighbour-list point SOR) */
+                                 barrier.  k > 0 (<= 7): that k; 0 (default): k = 2 for 2-3 layers and
+                                 for single-layer lattices of at most 200k nodes, else off; < 0: off
+                                 (neighbour-list point SOR) */
     int32_t jacobi;           /* 0 (default): coloured Gauss-Seidel / SOR inner sweeps (Eq. 16-17);
                                  1: damped Jacobi, every node updated from the previous iterate with
                                  omega <= 1 (default 1), one device barrier per sweep; no lattice solve */

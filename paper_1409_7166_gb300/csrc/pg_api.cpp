@@ -113,10 +113,10 @@ pg_status alloc_device(pg_grid* g) {
     float* D32 = g->mixed ? g->alloc<float>(np) : nullptr;
     float* D32lo = g->mixed ? g->alloc<float>(np) : nullptr;
     // lattice column-block inner solve: on by default for multi-layer lattices (the via
-    // couplings go into the blocks); single-layer grids measure faster on the SELL sweep
+    // couplings go into the blocks) and for small single-layer ones (auto_lattice_k)
     const int lat_k = g->opt.jacobi ? 0
                     : g->opt.lattice_sweeps > 0 ? g->opt.lattice_sweeps
-                    : (g->opt.lattice_sweeps == 0 && P.lat_maxnl >= 2 ? 2 : 0);
+                    : (g->opt.lattice_sweeps == 0 ? auto_lattice_k(P.lat_maxnl, P.n) : 0);
     std::vector<int32_t> lat_tile0, lat_info;
     std::vector<int64_t> lat_col0;
     if (g->mixed && P.lattice && lat_k > 0) {

@@ -228,7 +228,7 @@ pg_status build_packed(const pg_netlist* nl, Packed* P, std::string* why, int32_
     // --- colouring: BFS 2-colouring (red-black), else greedy multicolour; a grid that
     // takes the lattice inner solve keeps its natural order (one colour)
     const bool natural = P->lattice && lattice_policy != INT32_MIN &&
-                         (lattice_policy > 0 || (lattice_policy == 0 && P->lat_maxnl >= 2));
+                         (lattice_policy > 0 || (lattice_policy == 0 && auto_lattice_k(P->lat_maxnl, n) > 0));
     std::vector<int32_t> colour(n, natural ? 0 : -1);
     bool bipartite = !natural;
     if (!natural) {

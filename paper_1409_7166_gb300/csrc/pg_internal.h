@@ -76,6 +76,15 @@ struct Packed {
 // colour: no point sweep runs on them, and the FP64 passes then read the lattice-ordered
 // corrections contiguously.
 pg_status build_packed(const pg_netlist* nl, Packed* out, std::string* why, int32_t lattice_policy);
+
+// Lattice inner solve chosen automatically (lattice_sweeps = 0): k = 2 block sweeps per
+// barrier for lattices of 2-3 layers, and for single-layer lattices small enough that a
+// round is about one tile pass (up to kSmallLattice nodes), where two sweeps per barrier
+// pay; larger single-layer grids run the point SOR faster.
+constexpr int32_t kSmallLattice = 200000;
+inline int32_t auto_lattice_k(int32_t lat_maxnl, int32_t n_nodes) {
+    return lat_maxnl >= 2 || (lat_maxnl == 1 && n_nodes <= kSmallLattice) ? 2 : 0;
+}
 // Refill the value-dependent parts of a packed grid (merged weights, grounded
 // parts, capacitances, 1/L) from a netlist with the same topology.
 pg_status refill_values(const pg_netlist* nl, Packed* P, std::string* why);
