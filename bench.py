@@ -105,6 +105,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ncu capture of `bench.py --case --nsteps 2` on the 1024x1024x3 grid (the persistent
+# kernel's 2-step launch): its DRAM bytes and the work that launch did
+NCU_CAPTURE = {"dram_bytes": 7.41e9, "total_sweeps": 216, "total_outer": 4, "lattice_sweeps": 3}
+
+
 def algorithmic_bytes(st, n, mn, n_src, mixed: bool, nsteps: int, extrap: bool = True) -> float:
     """Bytes the method must move for the work recorded in ``st``.
 
@@ -291,13 +296,12 @@ def main():
     peak, peak_kind = load_peaks()
     alg = [algorithmic_bytes(s, n, mn, n_src, True, nsteps) for s in stats]
     achieved = sum(alg) / (sum(dev_ms) / 1e3) / 1e9
-    # DRAM traffic per launch: ncu measured dram__bytes_read.sum + dram__bytes_write.sum =
-    # 9.17 GB on a 2-step launch of this grid (232 block sweeps, 4 outer passes; the full
-    # 1000-step launch is too long to capture); scaled to the timed launch by the ratio of
-    # algorithmic bytes.  Valid for the kernel as captured; re-capture after kernel changes.
-    captured = algorithmic_bytes({"total_sweeps": 232, "total_outer": 4, "lattice_sweeps": 2}, n, mn, n_src,
-                                 True, 2)
-    traffic_ratio = 9.17e9 / captured if (args.nx, args.ny) == (1024, 1024) else None
+    # DRAM traffic per launch: ncu's dram__bytes_read.sum + dram__bytes_write.sum on a 2-step
+    # launch of this grid (the full 1000-step launch is too long to capture), scaled to the
+    # timed launch by the ratio of algorithmic bytes.  Valid for the kernel as captured.
+    cap = NCU_CAPTURE
+    captured = algorithmic_bytes(cap, n, mn, n_src, True, 2)
+    traffic_ratio = cap["dram_bytes"] / captured if (args.nx, args.ny) == (1024, 1024) else None
     bpl = sum(alg) / len(alg)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": bpl * traffic_ratio if traffic_ratio else None,

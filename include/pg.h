@@ -99,11 +99,11 @@ typedef enum pg_precision {
 typedef struct pg_options {
     int32_t precision;        /* pg_precision */
     double omega;             /* SOR factor (Eq. 17) in (0, 2); 0 = Young's formula from an estimated
-                                 Jacobi spectral radius */
+                                 Jacobi spectral radius, with omega - 1 taken 1 % high */
     double tol;               /* target max-abs voltage error of every step against the exact
                                  backward-Euler trajectory, V (0 -> 1e-6) */
     double step_tol;          /* per-step solve target, V; 0 -> derived from tol: RC grids use
-                                 0.5 tol / kacc (see pg_run_stats), grids with inductors 1e-4 tol */
+                                 0.9 tol / kacc (see pg_run_stats), grids with inductors 1e-4 tol */
     int32_t max_sweeps;       /* cap on relaxation sweeps per step (0 -> 20000) */
     int32_t warm_start;       /* 0: V(s-1) as in Algorithm 1; 1: linear extrapolation (default) */
     double inner_reduction;   /* PG_PREC_MIXED: residual reduction asked of one FP32 inner solve;
@@ -118,7 +118,7 @@ typedef struct pg_options {
                                  branches only between lattice neighbours): the inner solve becomes
                                  column-block red-black SOR (each (x, y) column's layers solved exactly)
                                  on shared-memory tiles with ghost zones, k exact block sweeps per device
-                                 barrier.  k > 0 (<= 7): that k; 0 (default): k = 2 for 2-3 layers and
+                                 barrier.  k > 0 (<= 7): that k; 0 (default): k = 3 for 2-3 layers and
                                  for single-layer lattices of at most 200k nodes, else off; < 0: off
                                  (neighbour-list point SOR) */
     int32_t jacobi;           /* 0 (default): coloured Gauss-Seidel / SOR inner sweeps (Eq. 16-17);
@@ -220,7 +220,8 @@ typedef struct pg_run_stats {
     int32_t max_outer_step;     /* most defect-correction passes any step needed */
     int64_t total_outer;
     double max_step_bound;      /* largest certified per-step error bound, V */
-    double err_bound;           /* bound on the accumulated error, kacc * max_step_bound, V (RC) */
+    double err_bound;           /* bound on the accumulated error, V (RC): kacc times the largest
+                                   per-step bound since the state was set, the DC solve included */
     int64_t failed_step;        /* step index of a failure, -1 if none */
     double omega;               /* SOR factor used */
     double rho_jacobi;          /* estimated Jacobi spectral radius (lower bound) */
@@ -257,12 +258,12 @@ pg_status pg_transient(pg_grid* g, double h, int32_t nsteps, const pg_output* ou
  * lattices and the precision is mixed; blocks per SM in {as many as fit, 1})
  * and, on each, times trial_steps transient steps from the DC point (best of
  * two runs, CUDA events) for every runtime candidate (inner reduction in {1e-3,
- * 1e-2, 1e-1} when mixed; omega - 1 scaled by {1, 0.97, 0.94} below Young's
- * value when omega is not fixed), then damped Jacobi (jacobi = 1, omega 1) with
+ * 1e-2, 1e-1} when mixed; omega - 1 of the automatic value scaled by {1, 1.01,
+ * 0.98} when omega is not fixed), then damped Jacobi (jacobi = 1, omega 1) with
  * at most 4x the winner's sweeps per step.  Every trial runs under the certified
  * stopping rule of `base` (tol), so only time is compared.  `base` (NULL ->
  * defaults) supplies every other field.  On success *best is `base` with
- * lattice_sweeps, blocks_per_sm, inner_reduction, jacobi and omega (0 = Young's value;
+ * lattice_sweeps, blocks_per_sm, inner_reduction, jacobi and omega (0 = the automatic value;
  * a scaled value is tied to this h) set to the fastest candidate and *best_ms
  * (may be NULL) to its trial time.  stream: cudaStream_t for the trials or
  * NULL.  Errors: PG_ERR_INVALID_ARG, or the last failure when no candidate ran.

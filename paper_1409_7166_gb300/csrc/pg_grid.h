@@ -94,6 +94,10 @@ struct pg_grid {
     int vL = 0, vP = 1;
     bool have_prev = false;
     bool inc_ok = false;          // r64 and md hold the last step's final residual and M d (see run)
+    // largest certified error bound (V) of the state the series started from (the DC solve;
+    // 0 for a state the caller set) and of every step since: the accumulated error of the
+    // current state is at most kacc times this
+    double series_bound = 0.0;
     bool dc_trivial = false;      // DC point is v = Vdd everywhere (see compute_dc_trivial)
     double dc_vdd = 0.0;
     std::unique_ptr<pg_grid> dcgrid;  // DC sub-problem, built on first use

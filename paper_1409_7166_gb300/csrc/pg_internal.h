@@ -77,14 +77,19 @@ struct Packed {
 // corrections contiguously.
 pg_status build_packed(const pg_netlist* nl, Packed* out, std::string* why, int32_t lattice_policy);
 
-// Lattice inner solve chosen automatically (lattice_sweeps = 0): k = 2 block sweeps per
+// Lattice inner solve chosen automatically (lattice_sweeps = 0): k = 3 block sweeps per
 // barrier for lattices of 2-3 layers, and for single-layer lattices small enough that a
-// round is about one tile pass (up to kSmallLattice nodes), where two sweeps per barrier
-// pay; larger single-layer grids run the point SOR faster.
+// round is about one tile pass (up to kSmallLattice nodes), where several sweeps per
+// barrier pay; larger single-layer grids run the point SOR faster.
 constexpr int32_t kSmallLattice = 200000;
 inline int32_t auto_lattice_k(int32_t lat_maxnl, int32_t n_nodes) {
-    return lat_maxnl >= 2 || (lat_maxnl == 1 && n_nodes <= kSmallLattice) ? 2 : 0;
+    return lat_maxnl >= 2 || (lat_maxnl == 1 && n_nodes <= kSmallLattice) ? 3 : 0;
 }
+// Tile geometry of the lattice inner solve: a tile owns T x T interior columns of its
+// lattice, T = kLatSide - 4k for k exact sweeps per round (a ghost zone of 2k columns on
+// every side), so that the columns its first half-sweep updates are exactly 32 x 32.
+constexpr int kLatSide = 34;
+inline int lattice_tile_side(int k) { return kLatSide - 4 * k; }
 // Refill the value-dependent parts of a packed grid (merged weights, grounded
 // parts, capacitances, 1/L) from a netlist with the same topology.
 pg_status refill_values(const pg_netlist* nl, Packed* P, std::string* why);

@@ -254,7 +254,7 @@ __device__ __forceinline__ double term_volt(const DevGrid& g, const double* v, i
 // and the neighbour values.
 constexpr int kWarpsPerBlock = 8;
 constexpr int kCacheSlices = 32;    // descriptors cached per warp
-constexpr int kCachePool = 384;     // diagonal offsets cached per warp
+constexpr int kCachePool = 192;     // diagonal offsets cached per warp (32 slices x 6)
 
 struct SliceDesc {
     long long off;   // element offset of the slice's slot 0
@@ -758,19 +758,28 @@ __device__ double sweep_colour_tma(const DevGrid& g, const WarpCache* wc, TmaWar
 // spectral radius that the in-plane sweep has to overcome.  With one layer a
 // block is a node and this is the point red-black SOR of Eq. 16-17.
 //
-// The relaxation runs on 32 x 32-column regions of all layers held in shared
-// memory: the region is its tile of (32 - 2H)^2 columns plus a ghost zone of
-// H = 2k columns, and k exact sweeps (2k half-sweeps) are applied to the
+// The relaxation runs on regions of kLatSide x kLatSide = 34 x 34 columns of all
+// layers held in shared memory: a tile of T^2 columns, T = 34 - 2H, plus a ghost
+// zone of H = 2k columns, and k exact sweeps (2k half-sweeps) are applied to the
 // region: half-sweep j (1-based) updates the columns at distance >= j from the
 // region edge, after which every such column holds the exact value (it reads
 // only neighbours at distance >= j - 1, updated by every earlier half-sweep), so
 // the tile interior (distance >= 2k) equals k global block sweeps.  Tiles read the previous round's corrections
 // and write the next buffer: one device barrier per k sweeps, every branch
 // weight stored once (E, N, U per node).
-constexpr int kLatR = 32;                          // region side (columns)
+//
+// The side 34 makes the columns of the first half-sweep (distance >= 1) exactly
+// 32 x 32, one per thread slot (16 column pairs x 2 rows per warp, 2 rows per
+// thread).  A region starts at an even column (T and H are even); its rows are
+// staged from the 16-byte boundary at or below that column (a lead of 0 or 2
+// columns), so that on lattices whose width is a multiple of 4 every row copies
+// in aligned 16-byte pieces.  Shared-memory rows hold kLatW = 36 floats, which
+// keeps the two half-warps (adjacent rows, opposite colours) on disjoint banks.
+constexpr int kLatW = 36;                          // shared-memory row stride (floats)
 constexpr int kLatMaxL = 3;                        // layers held per region
-constexpr int kLatPlane = kLatR * kLatR;
+constexpr int kLatPlane = kLatSide * kLatW;
 constexpr int kLatArrays = 7;                      // delta, r, wE, wN, wU, Thomas m, 1/pivot
+static_assert(kLatSide - 2 == 32, "the first half-sweep covers 32 x 32 thread slots");
 
 __host__ __device__ constexpr int lattice_smem_bytes() {
     return kLatArrays * kLatMaxL * kLatPlane * (int)sizeof(float);
@@ -797,7 +806,7 @@ template <int NL>
 __device__ float lattice_tile(const DevGrid& g, int off, int nx, int ny, int tile, const float* __restrict__ dold,
                               float* __restrict__ dnew, const float* __restrict__ r, float omega, int k,
                               unsigned char* smem) {
-    const int H = 2 * k, T = kLatR - 2 * H;
+    const int H = 2 * k, T = kLatSide - 2 * H;
     const int tiles_x = (nx + T - 1) / T;
     constexpr int A = kLatMaxL * kLatPlane;           // floats per array
     float* sd = reinterpret_cast<float*>(smem);
@@ -808,39 +817,45 @@ __device__ float lattice_tile(const DevGrid& g, int off, int nx, int ny, int til
     float* sm = sd + 5 * A;
     float* sp = sd + 6 * A;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int pair = lane & 15;                        // columns 2 pair, 2 pair + 1
+    const int pair = lane & 15;                        // columns 2 pair, 2 pair + 1 of the slot grid
     const int rsub = lane >> 4;                        // half-warps take adjacent rows (no bank conflicts)
     const long long plane = (long long)nx * ny;
-    const bool vec16 = (nx & 3) == 0 && (off & 3) == 0 && (H & 3) == 0 && (T & 3) == 0;   // aligned rows
+    // region: columns [x0, x0 + 34), rows [y0, y0 + 34); shared column c holds x0 - lead + c
     const int x0 = (tile % tiles_x) * T - H, y0 = (tile / tiles_x) * T - H;
+    const int lead = x0 & 3;                           // 0 or 2: x0 is even
+    const int xa = x0 - lead;
     auto src_of = [&](int arr) -> const float* {       // by value: no local array
         return arr == 0 ? dold : arr == 1 ? r : arr == 2 ? g.lwE : arr == 3 ? g.lwN : arr == 4 ? g.lwU
              : arr == 5 ? g.lm : g.lip;
     };
-    if (vec16) {
-        const int ry = threadIdx.x >> 3, cx = threadIdx.x & 7;   // one 16-byte chunk per plane
-        const int xx = x0 + 4 * cx, yy = y0 + ry;
-        const bool in = yy >= 0 && yy < ny && xx >= 0 && xx < nx;
-        const long long o = in ? off + (long long)yy * nx + xx : 0;
-        const int sa = ry * kLatR + 4 * cx;
-#pragma unroll
-        for (int arr = 0; arr < kLatArrays; ++arr)
-#pragma unroll
-            for (int l = 0; l < NL; ++l)
-                cp_async16(sd + arr * A + l * kLatPlane + sa, src_of(arr) + (in ? o + l * plane : 0), in ? 16u : 0u);
-    } else {
-        const int rx = threadIdx.x & 31;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int ry = (threadIdx.x >> 5) + 8 * q, yy = y0 + ry, xx = x0 + rx;
+    if ((nx & 3) == 0 && (off & 3) == 0) {
+        // rows of 16-byte pieces: a piece (xa + 4c, ..., +3) is wholly inside the lattice or
+        // wholly outside; the (piece, array) pairs are spread over the threads
+        constexpr int kChunks = kLatW / 4;
+        constexpr int kPieces = kLatSide * kChunks;
+        for (int q = threadIdx.x; q < kPieces * kLatArrays; q += blockDim.x) {
+            const int arr = q / kPieces, pos = q - arr * kPieces;
+            const int ry = pos / kChunks, c4 = 4 * (pos - ry * kChunks);
+            const int xx = xa + c4, yy = y0 + ry;
             const bool in = yy >= 0 && yy < ny && xx >= 0 && xx < nx;
             const long long o = in ? off + (long long)yy * nx + xx : 0;
-            const int sa = ry * kLatR + rx;
+            const float* src = src_of(arr);
+            float* dst = sd + arr * A + ry * kLatW + c4;
+#pragma unroll
+            for (int l = 0; l < NL; ++l)
+                cp_async16(dst + l * kLatPlane, src + (in ? o + l * plane : 0), in ? 16u : 0u);
+        }
+    } else {
+        for (int q = threadIdx.x; q < kLatPlane; q += blockDim.x) {
+            const int ry = q / kLatW, c = q - ry * kLatW;
+            const int xx = xa + c, yy = y0 + ry;
+            const bool in = yy >= 0 && yy < ny && xx >= 0 && xx < nx;
+            const long long o = in ? off + (long long)yy * nx + xx : 0;
 #pragma unroll
             for (int arr = 0; arr < kLatArrays; ++arr)
 #pragma unroll
                 for (int l = 0; l < NL; ++l)
-                    cp_async4(sd + arr * A + l * kLatPlane + sa, src_of(arr) + (in ? o + l * plane : 0), in ? 4u : 0u);
+                    cp_async4(sd + arr * A + l * kLatPlane + q, src_of(arr) + (in ? o + l * plane : 0), in ? 4u : 0u);
         }
     }
     cp_async_wait_all();
@@ -850,50 +865,47 @@ __device__ float lattice_tile(const DevGrid& g, int off, int nx, int ny, int til
         const bool last = hs >= 2 * k - 2;
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            const int ry = 2 * (warp + 8 * j) + rsub, y = y0 + ry;
-            const int rx = 2 * pair + ((hs + x0 + y) & 1);      // the column of this colour in the pair
-            const int x = x0 + rx;
-            const int edge = min(min(rx, ry), min(kLatR - 1 - rx, kLatR - 1 - ry));
+            const int ry = 1 + 2 * (warp + 8 * j) + rsub, y = y0 + ry;
+            const int cx = 1 + 2 * pair + ((hs + x0 + 1 + y) & 1);   // the column of this colour in the pair
+            const int x = x0 + cx;
+            const int edge = min(min(cx, ry), min(kLatSide - 1 - cx, kLatSide - 1 - ry));
             // half-sweep hs only matters at distance > hs from the region edge: what it
             // would change nearer the edge cannot reach the interior by the last one
             if (edge <= hs || x < 0 || x >= nx || y < 0 || y >= ny) continue;
-            const int a0 = ry * kLatR + rx;
-            float f[NL], xs[NL];
+            const int a0 = ry * kLatW + cx + lead;
+            float f[NL], xv[NL];
 #pragma unroll
             for (int l = 0; l < NL; ++l) {
                 const int a = a0 + l * kLatPlane;
-                f[l] = sr[a] + se[a] * sd[a + 1] + se[a - 1] * sd[a - 1] + sn[a] * sd[a + kLatR] +
-                       sn[a - kLatR] * sd[a - kLatR];
+                f[l] = sr[a] + se[a] * sd[a + 1] + se[a - 1] * sd[a - 1] + sn[a] * sd[a + kLatW] +
+                       sn[a - kLatW] * sd[a - kLatW];
             }
 #pragma unroll
             for (int l = 1; l < NL; ++l) f[l] = fmaf(sm[a0 + l * kLatPlane], f[l - 1], f[l]);
-            xs[NL - 1] = f[NL - 1] * sp[a0 + (NL - 1) * kLatPlane];
+            xv[NL - 1] = f[NL - 1] * sp[a0 + (NL - 1) * kLatPlane];
 #pragma unroll
             for (int l = NL - 2; l >= 0; --l)
-                xs[l] = fmaf(su[a0 + l * kLatPlane], xs[l + 1], f[l]) * sp[a0 + l * kLatPlane];
+                xv[l] = fmaf(su[a0 + l * kLatPlane], xv[l + 1], f[l]) * sp[a0 + l * kLatPlane];
             const bool interior = edge >= H;
 #pragma unroll
             for (int l = 0; l < NL; ++l) {
                 const int a = a0 + l * kLatPlane;
                 const float dv = sd[a];
-                const float upd = xs[l] - dv;
+                const float upd = xv[l] - dv;
                 sd[a] = fmaf(omega, upd, dv);
                 if (last && interior) mon = nanmaxf(mon, fabsf(upd));
             }
         }
         __syncthreads();
     }
-    {
-        const int rx = threadIdx.x & 31;
+    for (int q = threadIdx.x; q < T * T; q += blockDim.x) {
+        const int iy = q / T, ix = q - iy * T;
+        const int x = x0 + H + ix, y = y0 + H + iy;
+        if (x >= nx || y >= ny) continue;
+        const long long b = off + (long long)y * nx + x;
+        const int a = (H + iy) * kLatW + H + ix + lead;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int ry = (threadIdx.x >> 5) + 8 * q, y = y0 + ry, x = x0 + rx;
-            const int edge = min(min(rx, ry), min(kLatR - 1 - rx, kLatR - 1 - ry));
-            if (edge < H || x < 0 || x >= nx || y < 0 || y >= ny) continue;
-            const long long b = off + (long long)y * nx + x;
-#pragma unroll
-            for (int l = 0; l < NL; ++l) dnew[b + l * plane] = sd[l * kLatPlane + ry * kLatR + rx];
-        }
+        for (int l = 0; l < NL; ++l) dnew[b + l * plane] = sd[l * kLatPlane + a];
     }
     __syncthreads();   // the next tile overwrites the region
     return mon;
@@ -922,7 +934,7 @@ __device__ double lattice_round(const DevGrid& g, const float* dold, float* dnew
         if (latR && __longlong_as_double((long long)latR[L]) <= target) {
             // converged lattice (uniform across the block: no barrier divergence)
             if (first) {
-                const int H = 2 * k, T = kLatR - 2 * H, tiles_x = (nx + T - 1) / T;
+                const int H = 2 * k, T = kLatSide - 2 * H, tiles_x = (nx + T - 1) / T;
                 const int tx0 = (tile % tiles_x) * T, ty0 = (tile / tiles_x) * T;
                 const long long plane = (long long)nx * ny;
                 for (int q = threadIdx.x; q < T * T; q += blockDim.x) {
@@ -1666,10 +1678,9 @@ __global__ void __launch_bounds__(256) adjoint_lgrad_kernel(DevGrid g, const dou
 
 // Dynamic shared memory of the persistent kernel: the TMA stages of the FP32 sweep, or
 // (same bytes) the region of the lattice inner solve.
-static_assert(lattice_smem_bytes() <= kWarpsPerBlock * tma_warp_bytes(sizeof(float)),
-              "the lattice region must fit in the TMA stage memory");
 static size_t persistent_smem(bool mixed) {
-    return mixed ? (size_t)kWarpsPerBlock * tma_warp_bytes(sizeof(float)) : 0;
+    const int stages = kWarpsPerBlock * tma_warp_bytes(sizeof(float));
+    return mixed ? (size_t)(stages > lattice_smem_bytes() ? stages : lattice_smem_bytes()) : 0;
 }
 
 cudaError_t launch_persistent(bool mixed, const DevGrid& g, const DevState& st, const DevCtl& ctl,

@@ -4,9 +4,9 @@
 // (Section IV leaves omega and the sweep order open), and the best choice
 // depends on the grid: its size and layer count decide whether the column-block
 // inner solve pays for its ghost zones, how far the FP32 inner solve should
-// reduce the defect before the next FP64 residual pass, and whether a slightly
-// under-relaxed omega beats Young's value when the Jacobi radius is only
-// estimated.  Every candidate runs under the same certified stopping rule, so
+// reduce the defect before the next FP64 residual pass, and whether omega a
+// little above or below the automatic value (Young's, taken 1 % high) does
+// better on this grid's transient.  Every candidate runs under the same certified stopping rule, so
 // any candidate that converges meets the tolerance and the search only compares
 // time.
 
@@ -19,7 +19,7 @@
 namespace {
 
 constexpr double kInnerReductions[] = {1e-3, 1e-2, 1e-1};
-constexpr double kOmegaScales[] = {1.0, 0.97, 0.94};   // applied to omega - 1
+constexpr double kOmegaScales[] = {1.0, 1.01, 0.98};   // applied to omega - 1
 
 }  // namespace
 
@@ -62,7 +62,7 @@ extern "C" pg_status pg_autotune(const pg_netlist* nl, const pg_options* base, d
                 for (double sc : kOmegaScales) {
                     if (fixed_omega && sc != 1.0) continue;
                     g->opt.inner_reduction = red;
-                    g->omega = 1.0 + (w0 - 1.0) * sc;
+                    g->omega = std::min(1.0 + (w0 - 1.0) * sc, 0.5 * (w0 + 2.0));   // stays below 2
                     double t = INFINITY;
                     int32_t msw = 0;
                     for (int rep = 0; rep < 2 && !s; ++rep) {   // first run warms caches and clocks

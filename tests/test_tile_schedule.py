@@ -1,0 +1,152 @@
+"""The ghost-zone tile schedule of the lattice inner solve, modelled on the host.
+
+The FP32 lattice solve (block red-black SOR over (x, y) columns, Eq. 16-17 with
+the via couplings inside the column blocks) runs k exact sweeps per device
+barrier.  Each tile does this:
+- it loads a 34 x 34-column region;
+- it applies 2k half-sweeps;
+- it stores its (34 - 4k)^2 interior.
+Half-sweep hs updates only the columns farther than hs from the region edge.
+The columns are assigned as in the kernel: each of the 256 threads has 16
+column pairs and two rows per half-sweep, and the half-warps take adjacent
+rows.
+
+Rows are staged from the 16-byte boundary at or below the region's first
+column.
+
+This model replays that index arithmetic in FP64 and checks three things:
+- every shared-memory index stays inside the staged rows;
+- on widths that are a multiple of 4, every 16-byte piece is wholly inside or wholly outside the lattice;
+- every column is stored by exactly one tile, and the stored interior equals k
+  global red-black block sweeps exactly, with the same operations in the same
+  order.
+"""
+import numpy as np
+import pytest
+
+SIDE = 34          # region side in columns
+W = 36             # shared-memory row stride (the region plus a lead of 0 or 2 columns)
+THREADS = 256
+
+
+def _column_update(f, m, p, u, NL):
+    """Thomas elimination of one column block with precomputed factors."""
+    for l in range(1, NL):
+        f[l] = m[l] * f[l - 1] + f[l]
+    x = [0.0] * NL
+    x[NL - 1] = f[NL - 1] * p[NL - 1]
+    for l in range(NL - 2, -1, -1):
+        x[l] = (u[l] * x[l + 1] + f[l]) * p[l]
+    return x
+
+
+def tile_round(nx, ny, NL, k, arrs, dold, omega):
+    H = 2 * k
+    T = SIDE - 2 * H
+    tiles_x, tiles_y = -(-nx // T), -(-ny // T)
+    plane = nx * ny
+    srcs = [dold] + arrs                        # d, r, wE, wN, wU, m, 1/pivot
+    dnew = np.full_like(dold, np.nan)
+    stored = np.zeros(dold.shape, int)
+    for tile in range(tiles_x * tiles_y):
+        x0, y0 = (tile % tiles_x) * T - H, (tile // tiles_x) * T - H
+        assert x0 % 2 == 0
+        lead = x0 & 3
+        xa = x0 - lead
+        assert xa % 4 == 0 and lead in (0, 2)
+        sm = np.zeros((7, NL, SIDE * W))
+        if nx % 4 == 0:
+            chunks = W // 4
+            pieces = SIDE * chunks
+            for q in range(pieces * 7):
+                a, pos = divmod(q, pieces)
+                ry, c4 = pos // chunks, 4 * (pos % chunks)
+                xx, yy = xa + c4, y0 + ry
+                inside = 0 <= yy < ny and 0 <= xx < nx
+                assert inside == (0 <= yy < ny and 0 <= xx + 3 < nx)
+                sa = ry * W + c4
+                assert 0 <= sa and sa + 3 < SIDE * W
+                if inside:
+                    for l in range(NL):
+                        o = yy * nx + xx + l * plane
+                        sm[a, l, sa:sa + 4] = srcs[a].ravel()[o:o + 4]
+        else:
+            for q in range(SIDE * W):
+                ry, c = divmod(q, W)
+                xx, yy = xa + c, y0 + ry
+                if 0 <= yy < ny and 0 <= xx < nx:
+                    for a in range(7):
+                        for l in range(NL):
+                            sm[a, l, q] = srcs[a].ravel()[yy * nx + xx + l * plane]
+        sd, sr, se, sn, su, smm, sp = sm
+        for hs in range(2 * k):
+            touched = set()
+            for t in range(THREADS):
+                lane, warp = t & 31, t >> 5
+                pair, rsub = lane & 15, lane >> 4
+                for j in range(2):
+                    ry = 1 + 2 * (warp + 8 * j) + rsub
+                    y = y0 + ry
+                    cx = 1 + 2 * pair + ((hs + x0 + 1 + y) & 1)
+                    x = x0 + cx
+                    assert (x + y) % 2 == hs % 2               # this half-sweep's colour
+                    edge = min(cx, ry, SIDE - 1 - cx, SIDE - 1 - ry)
+                    if edge <= hs or not (0 <= x < nx and 0 <= y < ny):
+                        continue
+                    a0 = ry * W + cx + lead
+                    assert 1 <= cx <= SIDE - 2 and 1 <= ry <= SIDE - 2 and cx + lead + 1 < W
+                    assert a0 not in touched
+                    touched.add(a0)
+                    f = [sr[l, a0] + se[l, a0] * sd[l, a0 + 1] + se[l, a0 - 1] * sd[l, a0 - 1]
+                         + sn[l, a0] * sd[l, a0 + W] + sn[l, a0 - W] * sd[l, a0 - W]
+                         for l in range(NL)]
+                    xv = _column_update(f, smm[:, a0], sp[:, a0], su[:, a0], NL)
+                    for l in range(NL):
+                        dv = sd[l, a0]
+                        sd[l, a0] = omega * (xv[l] - dv) + dv
+        for q in range(T * T):
+            iy, ix = divmod(q, T)
+            x, y = x0 + H + ix, y0 + H + iy
+            if x >= nx or y >= ny:
+                continue
+            for l in range(NL):
+                dnew[l, y, x] = sd[l, (H + iy) * W + H + ix + lead]
+                stored[l, y, x] += 1
+    assert (stored == 1).all()
+    return dnew
+
+
+def global_sweeps(nx, ny, NL, k, arrs, d, omega):
+    r, wE, wN, wU, m, p = arrs
+    d = d.copy()
+    for hs in range(2 * k):
+        new = d.copy()
+        for y in range(ny):
+            for x in range(nx):
+                if (x + y) % 2 != hs % 2:
+                    continue
+                f = []
+                for l in range(NL):
+                    s = r[l, y, x]
+                    s += wE[l, y, x] * (d[l, y, x + 1] if x + 1 < nx else 0.0)
+                    s += wE[l, y, x - 1] * d[l, y, x - 1] if x > 0 else 0.0
+                    s += wN[l, y, x] * (d[l, y + 1, x] if y + 1 < ny else 0.0)
+                    s += wN[l, y - 1, x] * d[l, y - 1, x] if y > 0 else 0.0
+                    f.append(s)
+                xv = _column_update(f, m[:, y, x], p[:, y, x], wU[:, y, x], NL)
+                for l in range(NL):
+                    new[l, y, x] = omega * (xv[l] - d[l, y, x]) + d[l, y, x]
+        d = new
+    return d
+
+
+@pytest.mark.parametrize("nx,ny,NL,k", [(32, 28, 3, 2), (61, 37, 2, 2), (52, 60, 1, 1),
+                                        (27, 27, 3, 3), (8, 6, 2, 2), (72, 34, 3, 2),
+                                        (70, 30, 2, 2), (48, 40, 1, 3)])
+def test_tile_round_is_k_global_block_sweeps(nx, ny, NL, k):
+    rng = np.random.default_rng(nx * 1000 + ny)
+    arrs = [rng.uniform(-1, 1, (NL, ny, nx))] + [rng.uniform(0.05, 0.2, (NL, ny, nx)) for _ in range(5)]
+    d = rng.uniform(-1, 1, (NL, ny, nx))
+    got = tile_round(nx, ny, NL, k, arrs, d, 1.3)
+    want = global_sweeps(nx, ny, NL, k, arrs, d, 1.3)
+    assert np.array_equal(got, want)
