@@ -541,6 +541,10 @@ constexpr double kOmegaOver = 1.01;
 pg_status prepare_h(pg_grid* g, double h) {
     if (g->h == h) return PG_OK;
     if (!(h > 0.0) || !std::isfinite(h)) { g_last_error = "h must be > 0"; return PG_ERR_INVALID_ARG; }
+    // A state carried into a new system (another h, or new element values): its accumulated
+    // error bound under the old system becomes the starting error of the new series.
+    if (g->has_state && g->series_bound > 0.0)
+        g->series_bound = std::isfinite(g->kacc) && g->kacc > 0.0 ? g->series_bound * g->kacc : INFINITY;
     pg_status s = assemble_h(g, h);
     if (s) return s;
     g->h = h;
