@@ -180,6 +180,36 @@ def cpu_baseline_entry(n_full: int, unit_steps: bool = True) -> dict:
                        f"rate scaled by n_sample/n_full (optimistic for a direct solver)")}
 
 
+def sor_baseline_entry(n_full: int, timeout: float = 900.0) -> dict:
+    """The paper's red-black SOR (Eq. 16-17) on all host cores (OpenMP, FP64,
+    ``oracle/rbsor``) under the same certified stopping rule, on a sample of the
+    workload recipe in a fresh process.  Setup (the bounds' direct solves, the DC
+    point) is excluded from the timed step loop."""
+    nx = int(os.environ.get("PG_SOR_SAMPLE_NX", "256"))
+    nsteps = int(os.environ.get("PG_SOR_SAMPLE_STEPS", "60"))
+    code = f"""
+import sys, json
+sys.path.insert(0, {ROOT!r})
+import pgsynth
+from oracle import rbsor
+net = pgsynth.config1(nx={nx}, ny={nx})
+_, st = rbsor.transient(net, net.meta["h"], {nsteps}, keep=False)
+print(json.dumps({{k: float(v) for k, v in st.items()}}))
+"""
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=timeout)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    rate = nsteps / d["run_s"]
+    return {"value": rate * d["n"] / n_full, "unit": "steps/s", "cores": int(d["threads"]),
+            "kind": "red-black SOR of Eq. 16-17, OpenMP, FP64, certified stopping rule",
+            "node_sweeps_per_s": d["sweeps"] * d["n"] / d["run_s"],
+            "sweeps_per_step": d["sweeps"] / nsteps,
+            "sample": (f"config-1 recipe at {nx}x{nx}x3 ({int(d['n'])} nodes), {nsteps} BE steps from the DC "
+                       f"point (setup {d['setup_s']:.1f} s excluded), point red-black SOR with omega "
+                       f"{d['omega']:.4f}; rate scaled by n_sample/n_full")}
+
+
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
@@ -336,6 +366,12 @@ def main():
             cpu = cpu_baseline_entry(n)
         except Exception as exc:  # keep the GPU line even if the oracle sample fails
             cpu = {"value": None, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
+    cpu_sor = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            cpu_sor = sor_baseline_entry(n)
+        except Exception as exc:
+            cpu_sor = {"value": None, "unit": "steps/s", "kind": "red-black SOR, OpenMP", "sample": f"failed: {exc}"}
 
     if rank == 0:
         line = {
@@ -359,6 +395,7 @@ def main():
             "transient_ms": {"best": min(ms), "median": float(sorted(ms)[len(ms) // 2]), "mean": sum(ms) / len(ms)},
             "roofline": roof,
             "cpu_baseline": cpu,
+            "cpu_sor_baseline": cpu_sor,
             "e2e": e2e,
             "gpu_launches": 2 * args.steps,
             "clocks": clk.summary(),

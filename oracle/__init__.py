@@ -18,6 +18,9 @@ Modules
 ``bounds``     ||M^-1||_inf and the step-to-step error gain q used by the
                stopping rule, computed by direct solves
 ``adjoint``    discrete adjoint of the RC transient (not in the paper)
+``rbsor``      the multicore CPU baseline: red-black SOR (Eq. 16-17) in C with
+               OpenMP under the certified stopping rule, timed by the benchmark
+               (not used for parity)
 
 Sign conventions are those of Eq. 4-7 with the source-term signs fixed so
 that they agree with KVL (Eq. 7): the RHS of a BE step is

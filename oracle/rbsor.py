@@ -1,0 +1,175 @@
+"""Multicore CPU baseline: red-black SOR of the paper's node update on all host cores.
+
+TEST AND BENCHMARK INFRASTRUCTURE ONLY.  This is the paper's relaxation
+(Eq. 16 with the SOR blend of Eq. 17; Algorithm 1's step loop) run on the CPU.
+The sweep is in C with OpenMP (``rbsor.c``).  It solves the same
+backward-Euler steps as the GPU library, under the same certified stopping
+rule, and is timed beside it.  It shares no code with the CUDA library.
+Parity tests use the direct solves of ``transient``, not this module.
+
+Stopping rule: ``M`` is an M-matrix (Lemma 1), so the error of a step is at
+most ``kappa max_i |r_i| / D_i`` with ``kappa = ||M^-1 D||_inf``.  Step errors
+accumulate by at most ``kacc = ||1 + G^-1 (C/h) 1||_inf`` (RC).  Each step
+stops once ``kappa R <= 0.9 tol / kacc``.  ``kappa`` and ``kacc`` come from
+the direct solves of ``bounds`` (setup, not timed).
+
+Ordering and relaxation factor: the nodes are 2-coloured by a breadth-first
+search over the couplings; lattice grids, vias included, are bipartite.  The
+relaxation factor is Young's, from a power-iteration estimate of the Jacobi
+radius, with ``omega - 1`` taken 1 % high.  This is the same rule as the GPU
+library, stated here independently.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import time
+
+import numpy as np
+import scipy.sparse as sp
+from scipy.sparse.csgraph import breadth_first_order
+
+from . import bounds
+from .matrices import nodal_matrices
+from .transient import dc_operating_point, load_current, source_terms
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "rbsor.c")
+LIB = os.path.join(HERE, "_build", "librbsor.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``rbsor.c`` with gcc and OpenMP (in-tree, ``oracle/_build``)."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        os.makedirs(os.path.dirname(LIB), exist_ok=True)
+        tmp = LIB + f".{os.getpid()}.tmp"
+        subprocess.run(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", SRC, "-o", tmp, "-lm"], check=True)
+        os.replace(tmp, LIB)
+    return LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        P = C.POINTER
+        _lib.rbsor_step.restype = C.c_int
+        _lib.rbsor_step.argtypes = [C.c_int, P(C.c_int), P(C.c_int), P(C.c_double), P(C.c_double), P(C.c_int),
+                                    C.c_int, P(C.c_double), P(C.c_double), C.c_double, C.c_double, C.c_int,
+                                    C.c_int, P(C.c_double)]
+        _lib.rbsor_threads.restype = C.c_int
+        _lib.rbsor_set_threads.argtypes = [C.c_int]
+    return _lib
+
+
+def set_threads(t: int) -> None:
+    """OpenMP threads of the sweeps (the default is every core the process may use)."""
+    lib().rbsor_set_threads(int(t))
+
+
+def two_colouring(W: sp.csr_matrix) -> np.ndarray:
+    """Colour 0/1 per node with no coupling inside a colour (breadth-first search
+    over every connected part); raises ValueError if the couplings are not bipartite."""
+    n = W.shape[0]
+    colour = np.full(n, -1, np.int8)
+    for root in range(n):
+        if colour[root] >= 0:
+            continue
+        order, pred = breadth_first_order(W, root, directed=False, return_predecessors=True)
+        colour[root] = 0
+        for v in order[1:]:
+            colour[v] = 1 - colour[pred[v]]
+    rows, cols = W.nonzero()
+    if np.any(colour[rows] == colour[cols]):
+        raise ValueError("the coupling graph is not bipartite: red-black ordering does not apply")
+    return colour
+
+
+def jacobi_radius(D: np.ndarray, W: sp.csr_matrix, iters: int = 300, seed: int = 0) -> float:
+    """Rayleigh-quotient estimate (a lower bound) of rho(D^-1 W), from power iteration
+    on the shifted symmetric form (I + D^-1/2 W D^-1/2) / 2; the shift keeps the -rho
+    eigenvalue of a bipartite graph from cancelling the +rho one."""
+    s = 1.0 / np.sqrt(D)
+    S = sp.diags(s) @ W @ sp.diags(s)
+    x = np.random.default_rng(seed).uniform(0.5, 1.0, D.size)
+    x /= np.linalg.norm(x)
+    mu = 0.0
+    for _ in range(iters):
+        y = 0.5 * (x + S @ x)
+        mu = float(x @ y)
+        x = y / np.linalg.norm(y)
+    return 2.0 * mu - 1.0
+
+
+class StepSystem:
+    """One h: the CSR couplings, diagonal, colour order and relaxation factor."""
+
+    def __init__(self, net, h: float, mats=None):
+        self.mats = mats or nodal_matrices(net)
+        M = self.mats.system_matrix(h).tocsr()
+        self.D = M.diagonal().copy()
+        W = (sp.diags(self.D) - M).tocsr()
+        W.eliminate_zeros()
+        W.sort_indices()
+        self.W = W
+        colour = two_colouring(W)
+        self.order = np.concatenate([np.nonzero(colour == 0)[0], np.nonzero(colour == 1)[0]]).astype(np.int32)
+        self.n_first = int(np.sum(colour == 0))
+        self.rowptr = W.indptr.astype(np.int32)
+        self.col = W.indices.astype(np.int32)
+        self.w = W.data.astype(np.float64)
+        self.rho = min(jacobi_radius(self.D, W), 1.0 - 1e-12)
+        young = 2.0 / (1.0 + np.sqrt(1.0 - self.rho ** 2))
+        self.omega = min(1.0 + 1.01 * (young - 1.0), 0.5 * (young + 2.0))
+
+    def solve(self, b: np.ndarray, x: np.ndarray, target: float, max_sweeps: int = 20000,
+              check_every: int = 4) -> int:
+        """Relax ``x`` in place until ``max |r| / D <= target``; returns the sweeps used."""
+        P = C.POINTER
+        R = C.c_double(0.0)
+        k = lib().rbsor_step(self.D.size, self.rowptr.ctypes.data_as(P(C.c_int)),
+                             self.col.ctypes.data_as(P(C.c_int)), self.w.ctypes.data_as(P(C.c_double)),
+                             self.D.ctypes.data_as(P(C.c_double)), self.order.ctypes.data_as(P(C.c_int)),
+                             self.n_first, b.ctypes.data_as(P(C.c_double)), x.ctypes.data_as(P(C.c_double)),
+                             float(self.omega), float(target), int(max_sweeps), int(check_every), C.byref(R))
+        if k < 0:
+            raise RuntimeError(f"red-black SOR did not converge (status {k}, residual {R.value:.3e})")
+        return k
+
+
+def transient(net, h: float, nsteps: int, tol: float = 1e-6, keep: bool = True, mats=None):
+    """Backward-Euler RC transient from the DC point by red-black SOR on all host cores.
+
+    Returns ``(V, stats)``, where ``V[s]`` for ``s = 0..nsteps`` is ``None`` unless
+    ``keep`` is set.  ``stats`` holds the sweeps, the timed seconds of the step
+    loop, the threads used and the per-step target."""
+    mats = mats or nodal_matrices(net)
+    if mats.A_l.shape[0]:
+        raise ValueError("the CPU baseline covers RC grids")
+    t0 = time.perf_counter()
+    sysm = StepSystem(net, h, mats)
+    kappa = bounds.scaled_minv_inf_norm(net, h, mats)
+    kacc = bounds.accumulation_gain(net, h, mats)
+    step_tol = 0.9 * tol / kacc
+    target = step_tol / kappa - 1e-13
+    v = dc_operating_point(net, mats)
+    Ch = mats.C.diagonal() / h
+    const = source_terms(mats, h)
+    setup_s = time.perf_counter() - t0
+    V = [v.copy()] if keep else None
+    v_prev = v.copy()
+    sweeps = 0
+    t1 = time.perf_counter()
+    for s in range(1, nsteps + 1):
+        b = Ch * v - load_current(net, mats, s * h) + const
+        x = 2.0 * v - v_prev if s > 1 else v.copy()      # linear extrapolation warm start
+        sweeps += sysm.solve(b, x, target)
+        v_prev, v = v, x
+        if keep:
+            V.append(v.copy())
+    run_s = time.perf_counter() - t1
+    stats = dict(sweeps=sweeps, run_s=run_s, setup_s=setup_s, threads=lib().rbsor_threads(), n=net.n_nodes,
+                 omega=sysm.omega, kappa=kappa, kacc=kacc, step_tol=step_tol)
+    return (np.stack(V) if keep else None), stats

@@ -1,0 +1,57 @@
+"""The multicore red-black SOR baseline (``oracle/rbsor``) against the direct
+solves of the oracle, on the CPU.
+
+The baseline runs the paper's relaxation (Eq. 16-17, red-black order) under the
+certified stopping rule.  Its trajectory must stay within the accumulated bound,
+``0.9 tol``, of the exact backward-Euler trajectory at every step.  Red-black
+order makes each colour's updates independent, so the result must not depend on
+the thread count.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import pgsynth
+from oracle import rbsor, transient
+
+TOL = 1e-6
+
+
+@pytest.mark.parametrize("make,steps", [(lambda: pgsynth.config0(nx=30, ny=25), 40),
+                                        (lambda: pgsynth.config1(nx=24, ny=20), 40)])
+def test_rbsor_transient_within_certified_bound(make, steps):
+    net = make()
+    h = net.meta["h"]
+    Vo, _ = transient.transient(net, h, steps)
+    V, st = rbsor.transient(net, h, steps, tol=TOL)
+    err = np.max(np.abs(V - Vo))
+    assert err <= 0.9 * TOL, err
+    assert st["sweeps"] > 0 and 1.0 < st["omega"] < 2.0 and st["kacc"] >= 1.0
+
+
+def test_rbsor_is_independent_of_the_thread_count():
+    net = pgsynth.config1(nx=18, ny=14)
+    h = net.meta["h"]
+    out = []
+    for t in (1, 3):
+        rbsor.set_threads(t)
+        V, st = rbsor.transient(net, h, 15, tol=TOL)
+        out.append((V, st["sweeps"], st["threads"]))
+    rbsor.set_threads(0)
+    assert out[0][2] == 1 and out[1][2] == 3
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+
+
+def test_two_colouring():
+    # a 3 x 3 lattice is bipartite; a triangle is not
+    n = 9
+    e = [(y * 3 + x, y * 3 + x + 1) for y in range(3) for x in range(2)] + \
+        [(y * 3 + x, (y + 1) * 3 + x) for y in range(2) for x in range(3)]
+    a, b = np.array(e).T
+    W = sp.csr_matrix((np.ones(2 * len(e)), (np.r_[a, b], np.r_[b, a])), shape=(n, n))
+    colour = rbsor.two_colouring(W)
+    assert np.all(colour[a] != colour[b])
+    assert np.array_equal(colour, np.array([(i % 3 + i // 3) % 2 for i in range(n)]) ^ colour[0])
+    T = sp.csr_matrix((np.ones(6), ([0, 1, 1, 2, 2, 0], [1, 0, 2, 1, 0, 2])), shape=(3, 3))
+    with pytest.raises(ValueError):
+        rbsor.two_colouring(T)
