@@ -1033,7 +1033,11 @@ pg_status pg_transient(pg_grid* g, double h, int32_t nsteps, const pg_output* ou
             }
             if (cudaMalloc((void**)&probes_perm, pr.size() * sizeof(int32_t)) != cudaSuccess) { cleanup(); return PG_ERR_OOM; }
             tmp.push_back(probes_perm);
-            cudaMemcpy(probes_perm, pr.data(), pr.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+            if (cudaError_t e = cudaMemcpy(probes_perm, pr.data(), pr.size() * sizeof(int32_t),
+                                           cudaMemcpyHostToDevice)) {
+                cleanup();
+                return cuda_fail(e, "probe upload");
+            }
             rp.n_probes = out->n_probes;
             rp.probes_perm = probes_perm;
             rp.probe_v = (double*)stage(out->probe_v, (size_t)nsteps * out->n_probes * sizeof(double));
@@ -1057,9 +1061,12 @@ pg_status pg_transient(pg_grid* g, double h, int32_t nsteps, const pg_output* ou
     }
     g->step += done;
     if (done > 0) g->have_prev = true;
+    cudaError_t copy_err = cudaSuccess;   // the first failed copy-back, reported if the run succeeded
     if (host && out) {
         auto back = [&](void* user, void* dev, size_t bytes) {
-            if (user && dev && bytes) cudaMemcpy(user, dev, bytes, cudaMemcpyDeviceToHost);
+            if (!user || !dev || !bytes) return;
+            const cudaError_t e = cudaMemcpy(user, dev, bytes, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess && copy_err == cudaSuccess) copy_err = e;
         };
         back(out->v_all, rp.v_all, (size_t)done * P.n * sizeof(double));
         back(out->il_all, rp.il_all, (size_t)done * P.n_l * sizeof(double));
@@ -1070,6 +1077,7 @@ pg_status pg_transient(pg_grid* g, double h, int32_t nsteps, const pg_output* ou
     }
     cleanup();
     fill_stats(g, st, ms, stats, prior);
+    if (s == PG_OK && copy_err != cudaSuccess) return cuda_fail(copy_err, "output copy to the host");
     return s;
 }
 
