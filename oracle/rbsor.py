@@ -18,6 +18,12 @@ search over the couplings; lattice grids, vias included, are bipartite.  The
 relaxation factor is Young's, from a power-iteration estimate of the Jacobi
 radius, with ``omega - 1`` taken 1 % high.  This is the same rule as the GPU
 library, stated here independently.
+
+On lattice netlists the column-block form (``block=True``) relaxes whole
+``(x, y)`` columns.  Each column's layers, coupled by the vias, are solved
+exactly, with columns coloured by the parity of ``x + y``.  That is the
+algorithm of the GPU's lattice inner solve, so the two can be compared on the
+same iteration.
 """
 from __future__ import annotations
 
@@ -59,6 +65,9 @@ def lib():
         _lib.rbsor_step.argtypes = [C.c_int, P(C.c_int), P(C.c_int), P(C.c_double), P(C.c_double), P(C.c_int),
                                     C.c_int, P(C.c_double), P(C.c_double), C.c_double, C.c_double, C.c_int,
                                     C.c_int, P(C.c_double)]
+        _lib.rbsor_block_step.restype = C.c_int
+        _lib.rbsor_block_step.argtypes = [C.c_int, C.c_int, C.c_int] + [P(C.c_double)] * 8 + \
+            [C.c_double, C.c_double, C.c_int, C.c_int, P(C.c_double)]
         _lib.rbsor_threads.restype = C.c_int
         _lib.rbsor_set_threads.argtypes = [C.c_int]
     return _lib
@@ -139,19 +148,118 @@ class StepSystem:
         return k
 
 
-def transient(net, h: float, nsteps: int, tol: float = 1e-6, keep: bool = True, mats=None):
-    """Backward-Euler RC transient from the DC point by red-black SOR on all host cores.
+class LatticeSystem:
+    """One h on a lattice netlist, for the column-block form: the couplings by direction
+    (+x, +y, +l), the diagonal, each column block's elimination factors and omega.
 
-    Returns ``(V, stats)``, where ``V[s]`` for ``s = 0..nsteps`` is ``None`` unless
-    ``keep`` is set.  ``stats`` holds the sweeps, the timed seconds of the step
-    loop, the threads used and the per-step target."""
+    A column block is the tridiagonal system of one (x, y) column's layers (the vias).
+    Its elimination uses pivots ``p_0 = D_0`` and ``p_l = D_l - wU_(l-1) m_l``, with
+    multipliers ``m_l = wU_(l-1) / p_(l-1)``."""
+
+    def __init__(self, net, h: float, mats=None):
+        if net.lattice is None:
+            raise ValueError("the column-block form needs a lattice netlist")
+        nx, ny, nl = net.lattice
+        self.nx, self.ny, self.nl = nx, ny, nl
+        plane, n = nx * ny, nx * ny * nl
+        self.mats = mats or nodal_matrices(net)
+        M = self.mats.system_matrix(h).tocoo()
+        self.D = np.zeros(n)
+        self.D[M.row[M.row == M.col]] = M.data[M.row == M.col]
+        up = M.col > M.row
+        r, c, w = M.row[up], M.col[up], -M.data[up]
+        d = c - r
+        east = (d == 1) & (r % nx != nx - 1)
+        north = (d == nx) & ((r // nx) % ny != ny - 1)
+        via = d == plane
+        if not np.all(east | north | via):
+            raise ValueError("a coupling joins nodes that are not lattice neighbours")
+        self.wE, self.wN, self.wU = np.zeros(n), np.zeros(n), np.zeros(n)
+        self.wE[r[east]] = w[east]
+        self.wN[r[north]] = w[north]
+        self.wU[r[via]] = w[via]
+        Dl, Ul = self.D.reshape(nl, plane), self.wU.reshape(nl, plane)
+        piv = Dl.copy()
+        Tm = np.zeros((nl, plane))
+        for l in range(1, nl):
+            Tm[l] = Ul[l - 1] / piv[l - 1]
+            piv[l] = Dl[l] - Ul[l - 1] * Tm[l]
+        self.Tm, self.Tip = Tm.ravel(), (1.0 / piv).ravel()
+        self.rho = min(self._block_jacobi_radius(), 1.0 - 1e-12)
+        young = 2.0 / (1.0 + np.sqrt(1.0 - self.rho ** 2))
+        self.omega = min(1.0 + 1.01 * (young - 1.0), 0.5 * (young + 2.0))
+
+    def _in_plane(self, x):
+        """(W x)_i: the in-plane neighbours' couplings (the part outside the blocks)."""
+        nx = self.nx
+        y = self.wE * np.roll(x, -1)          # wE is 0 on the last column: the wrap adds nothing
+        y[1:] += self.wE[:-1] * x[:-1]
+        y += self.wN * np.roll(x, -nx)        # likewise wN on the last row of each layer
+        y[nx:] += self.wN[:-nx] * x[:-nx]
+        return y
+
+    def _block_solve(self, f):
+        nl, plane = self.nl, self.nx * self.ny
+        g = f.reshape(nl, plane).copy()
+        Tm, Tip, U = self.Tm.reshape(nl, plane), self.Tip.reshape(nl, plane), self.wU.reshape(nl, plane)
+        for l in range(1, nl):
+            g[l] += Tm[l] * g[l - 1]
+        z = np.empty_like(g)
+        z[nl - 1] = g[nl - 1] * Tip[nl - 1]
+        for l in range(nl - 2, -1, -1):
+            z[l] = (U[l] * z[l + 1] + g[l]) * Tip[l]
+        return z.ravel()
+
+    def _block_apply(self, x):
+        """(B x)_i: the diagonal and the via couplings inside the column blocks."""
+        plane = self.nx * self.ny
+        y = self.D * x
+        y[:-plane] -= self.wU[:-plane] * x[plane:]
+        y[plane:] -= self.wU[:-plane] * x[:-plane]
+        return y
+
+    def _block_jacobi_radius(self, iters: int = 300, seed: int = 0) -> float:
+        """Rayleigh quotient x.Wx / x.Bx (a lower bound of rho(B^-1 W)) after power
+        iteration on (I + B^-1 W) / 2; the shift keeps -rho from cancelling +rho."""
+        x = np.random.default_rng(seed).uniform(0.5, 1.0, self.D.size)
+        mu = 0.0
+        for _ in range(iters):
+            wx = self._in_plane(x)
+            mu = float(x @ wx) / float(x @ self._block_apply(x))
+            x = 0.5 * (x + self._block_solve(wx))
+            x /= np.max(np.abs(x))
+        return mu
+
+    def solve(self, b: np.ndarray, x: np.ndarray, target: float, max_sweeps: int = 20000,
+              check_every: int = 4) -> int:
+        """Relax ``x`` in place until ``max |r| / D <= target``; returns the sweeps used."""
+        P = C.POINTER
+        R = C.c_double(0.0)
+        arr = [a.ctypes.data_as(P(C.c_double)) for a in (self.wE, self.wN, self.wU, self.D, self.Tm, self.Tip, b, x)]
+        k = lib().rbsor_block_step(self.nx, self.ny, self.nl, *arr, float(self.omega), float(target),
+                                   int(max_sweeps), int(check_every), C.byref(R))
+        if k < 0:
+            raise RuntimeError(f"column-block SOR did not converge (status {k}, residual {R.value:.3e})")
+        return k
+
+
+def transient(net, h: float, nsteps: int, tol: float = 1e-6, keep: bool = True, mats=None,
+              block: bool = False, consts=None):
+    """Backward-Euler RC transient from the DC point by red-black SOR on all host cores:
+    point updates (Eq. 16-17), or with ``block`` the column-block form on a lattice.
+
+    Returns ``(V, stats)``, where ``V`` is ``None`` unless ``keep`` is set; then
+    ``V[s]`` holds step ``s = 0..nsteps``.  ``stats`` holds the sweeps, the timed
+    seconds of the step loop, the threads used and the per-step target.
+    ``consts`` may pass ``(kappa, kacc)`` already computed for this ``h``."""
     mats = mats or nodal_matrices(net)
     if mats.A_l.shape[0]:
         raise ValueError("the CPU baseline covers RC grids")
     t0 = time.perf_counter()
-    sysm = StepSystem(net, h, mats)
-    kappa = bounds.scaled_minv_inf_norm(net, h, mats)
-    kacc = bounds.accumulation_gain(net, h, mats)
+    sysm = LatticeSystem(net, h, mats) if block else StepSystem(net, h, mats)
+    if consts is None:
+        consts = (bounds.scaled_minv_inf_norm(net, h, mats), bounds.accumulation_gain(net, h, mats))
+    kappa, kacc = consts
     step_tol = 0.9 * tol / kacc
     target = step_tol / kappa - 1e-13
     v = dc_operating_point(net, mats)

@@ -17,29 +17,48 @@ from oracle import rbsor, transient
 TOL = 1e-6
 
 
+@pytest.mark.parametrize("block", [False, True])
 @pytest.mark.parametrize("make,steps", [(lambda: pgsynth.config0(nx=30, ny=25), 40),
-                                        (lambda: pgsynth.config1(nx=24, ny=20), 40)])
-def test_rbsor_transient_within_certified_bound(make, steps):
+                                        (lambda: pgsynth.config1(nx=24, ny=20), 40),
+                                        (lambda: pgsynth.config1(nx=13, ny=9, nl=2), 30)])
+def test_rbsor_transient_within_certified_bound(make, steps, block):
     net = make()
     h = net.meta["h"]
     Vo, _ = transient.transient(net, h, steps)
-    V, st = rbsor.transient(net, h, steps, tol=TOL)
+    V, st = rbsor.transient(net, h, steps, tol=TOL, block=block)
     err = np.max(np.abs(V - Vo))
     assert err <= 0.9 * TOL, err
     assert st["sweeps"] > 0 and 1.0 < st["omega"] < 2.0 and st["kacc"] >= 1.0
 
 
-def test_rbsor_is_independent_of_the_thread_count():
+def test_column_blocks_take_fewer_sweeps_on_layered_grids():
+    """With stiff vias inside the blocks, block SOR needs far fewer sweeps than point SOR."""
+    net = pgsynth.config1(nx=24, ny=20)
+    h = net.meta["h"]
+    _, pt = rbsor.transient(net, h, 20, keep=False)
+    _, bl = rbsor.transient(net, h, 20, keep=False, block=True)
+    assert bl["sweeps"] < 0.6 * pt["sweeps"]
+
+
+@pytest.mark.parametrize("block", [False, True])
+def test_rbsor_is_independent_of_the_thread_count(block):
     net = pgsynth.config1(nx=18, ny=14)
     h = net.meta["h"]
     out = []
     for t in (1, 3):
         rbsor.set_threads(t)
-        V, st = rbsor.transient(net, h, 15, tol=TOL)
+        V, st = rbsor.transient(net, h, 15, tol=TOL, block=block)
         out.append((V, st["sweeps"], st["threads"]))
     rbsor.set_threads(0)
     assert out[0][2] == 1 and out[1][2] == 3
     assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+
+
+def test_column_blocks_need_a_lattice():
+    from pgsynth import GROUND, make_netlist, source_terminal as S
+    net = make_netlist(2, [1.0], R=[(0, S(0), 1.0), (0, 1, 2.0)], C=[(1, GROUND, 1e-15)])
+    with pytest.raises(ValueError):
+        rbsor.LatticeSystem(net, 1e-12)
 
 
 def test_two_colouring():
