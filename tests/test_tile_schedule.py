@@ -12,14 +12,19 @@ column pairs and two rows per half-sweep, and the half-warps take adjacent
 rows.
 
 Rows are staged from the 16-byte boundary at or below the region's first
-column.
+column.  A batch of lattices is one flat tile range: each tile's lattice comes
+from a binary search over the first-tile table.  A lattice that has already
+converged is skipped, and its correction is zeroed on the first round.
 
-This model replays that index arithmetic in FP64 and checks three things:
+This model replays that index arithmetic in FP64 and checks four things:
 - every shared-memory index stays inside the staged rows;
 - on widths that are a multiple of 4, every 16-byte piece is wholly inside or wholly outside the lattice;
 - every column is stored by exactly one tile, and the stored interior equals k
   global red-black block sweeps exactly, with the same operations in the same
-  order.
+  order;
+- in a batch, lattices at any offset behave like that independently (16-byte
+  staging where the offset and the width allow it, 4-byte otherwise), and
+  skipped lattices end with a zero correction.
 """
 import numpy as np
 import pytest
@@ -40,80 +45,121 @@ def _column_update(f, m, p, u, NL):
     return x
 
 
-def tile_round(nx, ny, NL, k, arrs, dold, omega):
+def tile_apply(off, nx, ny, NL, k, tile, srcs, dnew, stored, omega):
+    """One tile of the lattice at global offset ``off``; ``srcs`` are the flat global
+    arrays (d, r, wE, wN, wU, m, 1/pivot) and ``dnew`` the flat output."""
     H = 2 * k
     T = SIDE - 2 * H
-    tiles_x, tiles_y = -(-nx // T), -(-ny // T)
+    tiles_x = -(-nx // T)
     plane = nx * ny
-    srcs = [dold] + arrs                        # d, r, wE, wN, wU, m, 1/pivot
-    dnew = np.full_like(dold, np.nan)
-    stored = np.zeros(dold.shape, int)
-    for tile in range(tiles_x * tiles_y):
-        x0, y0 = (tile % tiles_x) * T - H, (tile // tiles_x) * T - H
-        assert x0 % 2 == 0
-        lead = x0 & 3
-        xa = x0 - lead
-        assert xa % 4 == 0 and lead in (0, 2)
-        sm = np.zeros((7, NL, SIDE * W))
-        if nx % 4 == 0:
-            chunks = W // 4
-            pieces = SIDE * chunks
-            for q in range(pieces * 7):
-                a, pos = divmod(q, pieces)
-                ry, c4 = pos // chunks, 4 * (pos % chunks)
-                xx, yy = xa + c4, y0 + ry
-                inside = 0 <= yy < ny and 0 <= xx < nx
-                assert inside == (0 <= yy < ny and 0 <= xx + 3 < nx)
-                sa = ry * W + c4
-                assert 0 <= sa and sa + 3 < SIDE * W
-                if inside:
+    x0, y0 = (tile % tiles_x) * T - H, (tile // tiles_x) * T - H
+    assert x0 % 2 == 0
+    lead = x0 & 3
+    xa = x0 - lead
+    assert xa % 4 == 0 and lead in (0, 2)
+    sm = np.zeros((7, NL, SIDE * W))
+    if nx % 4 == 0 and off % 4 == 0:
+        chunks = W // 4
+        pieces = SIDE * chunks
+        for q in range(pieces * 7):
+            a, pos = divmod(q, pieces)
+            ry, c4 = pos // chunks, 4 * (pos % chunks)
+            xx, yy = xa + c4, y0 + ry
+            inside = 0 <= yy < ny and 0 <= xx < nx
+            assert inside == (0 <= yy < ny and 0 <= xx + 3 < nx)
+            sa = ry * W + c4
+            assert 0 <= sa and sa + 3 < SIDE * W
+            if inside:
+                for l in range(NL):
+                    o = off + yy * nx + xx + l * plane
+                    assert o % 4 == 0                       # a 16-byte aligned source
+                    sm[a, l, sa:sa + 4] = srcs[a][o:o + 4]
+    else:
+        for q in range(SIDE * W):
+            ry, c = divmod(q, W)
+            xx, yy = xa + c, y0 + ry
+            if 0 <= yy < ny and 0 <= xx < nx:
+                for a in range(7):
                     for l in range(NL):
-                        o = yy * nx + xx + l * plane
-                        sm[a, l, sa:sa + 4] = srcs[a].ravel()[o:o + 4]
-        else:
-            for q in range(SIDE * W):
-                ry, c = divmod(q, W)
-                xx, yy = xa + c, y0 + ry
-                if 0 <= yy < ny and 0 <= xx < nx:
-                    for a in range(7):
-                        for l in range(NL):
-                            sm[a, l, q] = srcs[a].ravel()[yy * nx + xx + l * plane]
-        sd, sr, se, sn, su, smm, sp = sm
-        for hs in range(2 * k):
-            touched = set()
-            for t in range(THREADS):
-                lane, warp = t & 31, t >> 5
-                pair, rsub = lane & 15, lane >> 4
-                for j in range(2):
-                    ry = 1 + 2 * (warp + 8 * j) + rsub
-                    y = y0 + ry
-                    cx = 1 + 2 * pair + ((hs + x0 + 1 + y) & 1)
-                    x = x0 + cx
-                    assert (x + y) % 2 == hs % 2               # this half-sweep's colour
-                    edge = min(cx, ry, SIDE - 1 - cx, SIDE - 1 - ry)
-                    if edge <= hs or not (0 <= x < nx and 0 <= y < ny):
-                        continue
-                    a0 = ry * W + cx + lead
-                    assert 1 <= cx <= SIDE - 2 and 1 <= ry <= SIDE - 2 and cx + lead + 1 < W
-                    assert a0 not in touched
-                    touched.add(a0)
-                    f = [sr[l, a0] + se[l, a0] * sd[l, a0 + 1] + se[l, a0 - 1] * sd[l, a0 - 1]
-                         + sn[l, a0] * sd[l, a0 + W] + sn[l, a0 - W] * sd[l, a0 - W]
-                         for l in range(NL)]
-                    xv = _column_update(f, smm[:, a0], sp[:, a0], su[:, a0], NL)
-                    for l in range(NL):
-                        dv = sd[l, a0]
-                        sd[l, a0] = omega * (xv[l] - dv) + dv
-        for q in range(T * T):
-            iy, ix = divmod(q, T)
-            x, y = x0 + H + ix, y0 + H + iy
-            if x >= nx or y >= ny:
-                continue
-            for l in range(NL):
-                dnew[l, y, x] = sd[l, (H + iy) * W + H + ix + lead]
-                stored[l, y, x] += 1
-    assert (stored == 1).all()
+                        sm[a, l, q] = srcs[a][off + yy * nx + xx + l * plane]
+    sd, sr, se, sn, su, smm, sp = sm
+    for hs in range(2 * k):
+        touched = set()
+        for t in range(THREADS):
+            lane, warp = t & 31, t >> 5
+            pair, rsub = lane & 15, lane >> 4
+            for j in range(2):
+                ry = 1 + 2 * (warp + 8 * j) + rsub
+                y = y0 + ry
+                cx = 1 + 2 * pair + ((hs + x0 + 1 + y) & 1)
+                x = x0 + cx
+                assert (x + y) % 2 == hs % 2               # this half-sweep's colour
+                edge = min(cx, ry, SIDE - 1 - cx, SIDE - 1 - ry)
+                if edge <= hs or not (0 <= x < nx and 0 <= y < ny):
+                    continue
+                a0 = ry * W + cx + lead
+                assert 1 <= cx <= SIDE - 2 and 1 <= ry <= SIDE - 2 and cx + lead + 1 < W
+                assert a0 not in touched
+                touched.add(a0)
+                f = [sr[l, a0] + se[l, a0] * sd[l, a0 + 1] + se[l, a0 - 1] * sd[l, a0 - 1]
+                     + sn[l, a0] * sd[l, a0 + W] + sn[l, a0 - W] * sd[l, a0 - W]
+                     for l in range(NL)]
+                xv = _column_update(f, smm[:, a0], sp[:, a0], su[:, a0], NL)
+                for l in range(NL):
+                    dv = sd[l, a0]
+                    sd[l, a0] = omega * (xv[l] - dv) + dv
+    for q in range(T * T):
+        iy, ix = divmod(q, T)
+        x, y = x0 + H + ix, y0 + H + iy
+        if x >= nx or y >= ny:
+            continue
+        for l in range(NL):
+            o = off + l * plane + y * nx + x
+            dnew[o] = sd[l, (H + iy) * W + H + ix + lead]
+            stored[o] += 1
+
+
+def lattice_round(lats, k, srcs, omega, converged=(), first=True):
+    """One round over every lattice of a batch, as the kernel schedules it: a flat
+    tile index, its lattice found by binary search over the first-tile table, and
+    converged lattices skipped (their correction zeroed on the first round)."""
+    T = SIDE - 4 * k
+    tile0 = [0]
+    for (off, nx, ny, nl) in lats:
+        tile0.append(tile0[-1] + (-(-nx // T)) * (-(-ny // T)))
+    dnew = np.full_like(srcs[0], np.nan)
+    stored = np.zeros(srcs[0].size, int)
+    for t in range(tile0[-1]):
+        lo, hi = 0, len(lats)
+        while hi - lo > 1:
+            mid = (lo + hi) >> 1
+            if tile0[mid] <= t:
+                lo = mid
+            else:
+                hi = mid
+        assert tile0[lo] <= t < tile0[lo + 1]
+        off, nx, ny, nl = lats[lo]
+        tile = t - tile0[lo]
+        if lo in converged:
+            if first:
+                tiles_x = -(-nx // T)
+                tx0, ty0 = (tile % tiles_x) * T, (tile // tiles_x) * T
+                for q in range(T * T):
+                    x, y = tx0 + q % T, ty0 + q // T
+                    if x < nx and y < ny:
+                        for l in range(nl):
+                            o = off + l * nx * ny + y * nx + x
+                            dnew[o] = 0.0
+                            stored[o] += 1
+            continue
+        tile_apply(off, nx, ny, nl, k, tile, srcs, dnew, stored, omega)
+    assert (stored == 1).all(), "every node of the batch written exactly once"
     return dnew
+
+
+def tile_round(nx, ny, NL, k, arrs, dold, omega):
+    srcs = [dold.ravel()] + [a.ravel() for a in arrs]
+    return lattice_round([(0, nx, ny, NL)], k, srcs, omega).reshape(dold.shape)
 
 
 def global_sweeps(nx, ny, NL, k, arrs, d, omega):
@@ -150,3 +196,30 @@ def test_tile_round_is_k_global_block_sweeps(nx, ny, NL, k):
     got = tile_round(nx, ny, NL, k, arrs, d, 1.3)
     want = global_sweeps(nx, ny, NL, k, arrs, d, 1.3)
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("lats_shape,k,converged", [
+    ([(5, 3, 3), (30, 27, 3), (2, 7, 1)], 2, ()),          # odd offsets: 4-byte staging
+    ([(8, 4, 1), (12, 8, 2), (36, 20, 3)], 2, ()),         # offsets and widths multiples of 4
+    ([(8, 4, 1), (12, 8, 2), (36, 20, 3)], 3, (1,)),       # a converged lattice is skipped
+    ([(26, 26, 2), (27, 5, 1)], 1, (0,)),
+])
+def test_batched_round(lats_shape, k, converged):
+    rng = np.random.default_rng(len(lats_shape) * 10 + k)
+    lats, off = [], 0
+    for (nx, ny, nl) in lats_shape:
+        lats.append((off, nx, ny, nl))
+        off += nx * ny * nl
+    N = off
+    d = rng.uniform(-1, 1, N)
+    arrs = [rng.uniform(-1, 1, N)] + [rng.uniform(0.05, 0.2, N) for _ in range(5)]
+    got = lattice_round(lats, k, [d] + arrs, 1.3, converged=converged)
+    for L, (o, nx, ny, nl) in enumerate(lats):
+        sl = slice(o, o + nx * ny * nl)
+        if L in converged:
+            assert not got[sl].any()
+            continue
+        shape = (nl, ny, nx)
+        want = global_sweeps(nx, ny, nl, k, [a[sl].reshape(shape) for a in arrs], d[sl].reshape(shape), 1.3)
+        assert np.array_equal(got[sl].reshape(shape), want), f"lattice {L}"
+
