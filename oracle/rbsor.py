@@ -244,14 +244,19 @@ class LatticeSystem:
 
 
 def transient(net, h: float, nsteps: int, tol: float = 1e-6, keep: bool = True, mats=None,
-              block: bool = False, consts=None):
+              block: bool = False, consts=None, theta: float = 1.0, theta_static=None, check_every: int = 4):
     """Backward-Euler RC transient from the DC point by red-black SOR on all host cores:
     point updates (Eq. 16-17), or with ``block`` the column-block form on a lattice.
 
     Returns ``(V, stats)``, where ``V`` is ``None`` unless ``keep`` is set; then
     ``V[s]`` holds step ``s = 0..nsteps``.  ``stats`` holds the sweeps, the timed
     seconds of the step loop, the threads used and the per-step target.
-    ``consts`` may pass ``(kappa, kacc)`` already computed for this ``h``."""
+    ``consts`` may pass ``(kappa, kacc)`` already computed for this ``h``.
+
+    Warm start: ``v(s-1) + theta (v(s-1) - v(s-2))``.  The default ``theta = 1`` is
+    the GPU library's linear extrapolation.  With ``theta_static`` set, that value
+    replaces ``theta`` on steps where no load current changed over the last two
+    intervals.  ``check_every``: sweeps between residual checks."""
     mats = mats or nodal_matrices(net)
     if mats.A_l.shape[0]:
         raise ValueError("the CPU baseline covers RC grids")
@@ -269,11 +274,17 @@ def transient(net, h: float, nsteps: int, tol: float = 1e-6, keep: bool = True, 
     V = [v.copy()] if keep else None
     v_prev = v.copy()
     sweeps = 0
+    i_hist = [load_current(net, mats, 0.0)] * 2           # A_i^T I at the last two step times
     t1 = time.perf_counter()
     for s in range(1, nsteps + 1):
-        b = Ch * v - load_current(net, mats, s * h) + const
-        x = 2.0 * v - v_prev if s > 1 else v.copy()      # linear extrapolation warm start
-        sweeps += sysm.solve(b, x, target)
+        i_now = load_current(net, mats, s * h)
+        b = Ch * v - i_now + const
+        th = theta
+        if theta_static is not None and np.array_equal(i_now, i_hist[-1]) and np.array_equal(i_hist[-1], i_hist[-2]):
+            th = theta_static
+        i_hist = [i_hist[-1], i_now]
+        x = v + th * (v - v_prev) if s > 1 else v.copy()   # extrapolated warm start
+        sweeps += sysm.solve(b, x, target, check_every=check_every)
         v_prev, v = v, x
         if keep:
             V.append(v.copy())

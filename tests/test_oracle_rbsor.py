@@ -74,3 +74,15 @@ def test_two_colouring():
     T = sp.csr_matrix((np.ones(6), ([0, 1, 1, 2, 2, 0], [1, 0, 2, 1, 0, 2])), shape=(3, 3))
     with pytest.raises(ValueError):
         rbsor.two_colouring(T)
+
+
+def test_damped_predictor_stays_within_bound():
+    """The warm start only changes where the iteration starts: any predictor meets the
+    same certified bound."""
+    net = pgsynth.config1(nx=20, ny=16)
+    h = net.meta["h"]
+    Vo, _ = transient.transient(net, h, 60)
+    for kw in (dict(theta=0.5), dict(theta=1.0, theta_static=0.5), dict(theta=0.0)):
+        V, _ = rbsor.transient(net, h, 60, tol=TOL, block=True, **kw)
+        assert np.max(np.abs(V - Vo)) <= 0.9 * TOL, kw
+
