@@ -369,6 +369,40 @@ def test_generator_multilayer_counts():
     assert r["L"] == 32 * 32 + 4  # every via and every pad
 
 
+def test_generator_config4_counts():
+    """The 2048 x 2048 single-layer mesh: 2 * 2048 * 2047 segments, pads where x and y
+    are multiples of 10 (205 x 205), a capacitor on every node, loads on 20 % of them."""
+    net = pgsynth.config4()
+    c = net.counts()
+    n = 2048 * 2048
+    assert c["n"] == n and c["L"] == 0 and c["C"] == n
+    seg = net.r_b >= 0
+    assert int(seg.sum()) == 2 * 2048 * 2047 == 8_384_512
+    assert int((~seg).sum()) == 205 * 205 == 42_025
+    assert c["I"] == round(0.2 * n) == 838_861
+    assert net.meta["h"] == 10e-12 and net.meta["nsteps"] == 500
+
+
+def test_generator_config3_structure():
+    """Batched grids: each part is a lattice of side 64..512 with 1 or 2 layers, drawn from
+    its own child seed; parts sit back to back; 2-layer parts have one via per column."""
+    parts = pgsynth.config3_parts(n_grids=8)
+    off = 0
+    for o, p in parts:
+        nx, ny, nl = p.lattice
+        assert o == off and nx == ny and 64 <= nx <= 512 and nl in (1, 2)
+        c = p.counts()
+        assert c["n"] == nx * ny * nl
+        seg = nl * 2 * nx * (nx - 1)
+        pads = len(range(0, nx, 10)) ** 2
+        assert c["R"] == seg + (nx * nx if nl == 2 else 0) + pads
+        assert c["C"] == nx * nx and c["I"] == round(0.2 * nx * nx)
+        off += c["n"]
+    # the batch is the parts side by side
+    net = pgsynth.config3(n_grids=8)
+    assert net.n_nodes == off and [l[0] for l in net.lattices] == [o for o, _ in parts]
+
+
 # ---------------------------------------------------------------- adjoint (not in the paper)
 
 def _adjoint_case():
