@@ -85,18 +85,31 @@ def certified_max_solution(A, rhs, rtol: float = 1e-9, maxiter: int = 20000) -> 
     pre = sla.LinearOperator(A.shape, matvec=lambda x: x / d)
     z, info = sla.cg(A, rhs, rtol=rtol, maxiter=maxiter, M=pre)
     z = np.maximum(z, 0.0)
-    absA = abs(A)
-    eps = 2.0 ** -52
     scale = 1.0
     for _ in range(60):
         zz = z * scale
-        lhs = A @ zz - rhs
-        err = 2 * 16 * eps * (absA @ zz + rhs)
-        if np.all(lhs >= err):
+        if is_super_solution(A, rhs, zz):
             return float(np.max(zz))
+        err = _ROUND_TERMS * _EPS * (abs(A) @ zz + rhs)
         worst = np.max((rhs + err - A @ z * scale) / np.maximum(rhs, 1e-300))
         scale *= 1.0 + max(2.0 * worst, 1e-12)
     raise RuntimeError("could not certify a super-solution")
+
+
+_EPS = 2.0 ** -52
+_ROUND_TERMS = 2 * 16      # 2 n_i eps |A||z| with at most 16 terms per row (rows here have <= 8)
+
+
+def is_super_solution(A, rhs, z) -> bool:
+    """True when ``A z >= rhs`` holds componentwise even after the rounding of the
+    FP64 product is charged against it, i.e. ``fl(A z) - rhs >= 2 n_i eps (|A| |z| + rhs)``.
+    For an M-matrix ``A`` this makes ``z >= A^-1 rhs`` (``A^-1 >= 0``, Lemma 1), which
+    also implies ``z >= 0`` when ``rhs > 0``."""
+    A = A.tocsr()
+    z = np.asarray(z, dtype=np.float64)
+    lhs = A @ z - rhs
+    err = _ROUND_TERMS * _EPS * (abs(A) @ z + rhs)
+    return bool(np.all(lhs >= err))
 
 
 def certified_bounds(net, h: float, tau: float = 1e-6) -> dict:

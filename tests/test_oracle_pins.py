@@ -51,6 +51,107 @@ def test_single_node_bounds_closed_form():
     assert bounds.step_gain(net, h) == pytest.approx((C / h) / (C / h + g0), rel=1e-14)
 
 
+def test_scaled_minv_inf_norm_single_node_is_one():
+    """With one node M = D, so ||M^-1 D||_inf = 1 whatever C, G0 and h are."""
+    for C, g0, h in ((50e-15, 10.0, 10e-12), (1e-12, 0.1, 1e-9), (0.0, 3.0, 1e-12)):
+        net = make_netlist(1, [1.0], R=[(0, S(0), g0)], C=[(0, GROUND, C)] if C else [])
+        assert bounds.scaled_minv_inf_norm(net, h) == pytest.approx(1.0, rel=1e-15)
+
+
+def _two_node_system(fx):
+    """The two-node circuit of ``two_node_rc.json`` written out by hand: node 0 has the pad
+    G0 and no capacitor, node 1 has C1; the segment g joins them (Eq. 12 with Eq. 2)."""
+    g0, g, C1, h = fx["G0"], fx["g"], fx["C1"], fx["h"]
+    M = np.array([[g0 + g, -g], [-g, g + C1 / h]])
+    G = np.array([[g0 + g, -g], [-g, g]])          # M - C/h: the pad stays on the diagonal
+    net = make_netlist(2, [fx["Vdd"]], R=[(0, S(0), g0), (0, 1, g)], C=[(1, GROUND, C1)])
+    return net, M, G
+
+
+def _cramer(A, b):
+    det = A[0, 0] * A[1, 1] - A[0, 1] * A[1, 0]
+    return np.array([(b[0] * A[1, 1] - A[0, 1] * b[1]) / det, (A[0, 0] * b[1] - b[0] * A[1, 0]) / det])
+
+
+def test_bounds_of_two_node_circuit_by_cramer():
+    """kappa = max (M^-1 D 1), q = max (M^-1 (C/h) 1) and the accumulation gain
+    1 + max (G^-1 (C/h) 1) of the hand circuit, each by Cramer's rule.  Written out:
+    M^-1 D 1 = [(g + C1/h)(G0 + 2g), (G0 + g)(2g + C1/h)] / det M, and
+    G^-1 (C/h) 1 = [C1/(h G0), (G0 + g) C1 / (h G0 g)]."""
+    fx = _load("two_node_rc.json")
+    net, M, G = _two_node_system(fx)
+    h, g0, g, C1 = fx["h"], fx["G0"], fx["g"], fx["C1"]
+    detM = M[0, 0] * M[1, 1] - M[0, 1] ** 2
+    kappa = max((g + C1 / h) * (g0 + 2 * g), (g0 + g) * (2 * g + C1 / h)) / detM
+    np.testing.assert_allclose(_cramer(M, np.diag(M)), [(g + C1 / h) * (g0 + 2 * g) / detM,
+                                                        (g0 + g) * (2 * g + C1 / h) / detM], rtol=1e-15)
+    assert bounds.scaled_minv_inf_norm(net, h) == pytest.approx(kappa, rel=1e-13)
+    assert bounds.step_gain(net, h) == pytest.approx(np.max(_cramer(M, [0.0, C1 / h])), rel=1e-13)
+    gain = 1.0 + max(C1 / (h * g0), (g0 + g) * C1 / (h * g0 * g))
+    assert bounds.accumulation_gain(net, h) == pytest.approx(gain, rel=1e-13)
+
+
+def test_certified_bounds_of_two_node_circuit():
+    """The certified (factorisation-free) bounds enclose the hand values from above and
+    stay within the CG tolerance of them: kappa_upper >= max(M^-1 D 1), and gain_upper >=
+    1 + max(G^-1 (C/h 1 + tau diag G)), the right-hand side with its stated lift."""
+    fx = _load("two_node_rc.json")
+    net, M, G = _two_node_system(fx)
+    h, tau = fx["h"], 1e-6
+    cb = bounds.certified_bounds(net, h, tau=tau)
+    kappa = np.max(_cramer(M, np.diag(M)))
+    lifted = 1.0 + np.max(_cramer(G, np.array([0.0, fx["C1"] / h]) + tau * np.diag(G)))
+    assert kappa <= cb["kappa_upper"] <= kappa * (1 + 1e-8)
+    assert lifted <= cb["gain_upper"] <= lifted * (1 + 1e-8)
+    assert cb["tau"] == tau
+
+
+@pytest.mark.parametrize("recipe", ["config0_40x30", "config1_24x20x3", "config0_64x64"])
+def test_certified_bounds_enclose_direct_solves(recipe):
+    """On grids small enough for the direct solver the certified bounds must lie above
+    the exact constants (a sub-solution accepted by the check would fall below) and
+    close to them: kappa within the CG tolerance (1e-7 relative), and the gain within
+    the lift tau ||G^-1 diag G||_inf it adds on purpose plus 1e-5 relative.  The
+    accumulation gain itself is pinned by the error-propagation test below."""
+    from oracle.transient import DirectSolver
+    net = {"config0_40x30": lambda: pgsynth.config0(nx=40, ny=30),
+           "config1_24x20x3": lambda: pgsynth.config1(nx=24, ny=20),
+           "config0_64x64": lambda: pgsynth.config0(nx=64, ny=64)}[recipe]()
+    h = net.meta["h"]
+    mats = matrices.nodal_matrices(net)
+    kappa = bounds.scaled_minv_inf_norm(net, h, mats)
+    gain = bounds.accumulation_gain(net, h, mats)
+    cb = bounds.certified_bounds(net, h)
+    assert kappa <= cb["kappa_upper"] <= kappa * (1 + 1e-7)
+    G = mats.G.tocsc()
+    lift = cb["tau"] * np.max(DirectSolver(G).solve(G.diagonal()))
+    assert gain <= cb["gain_upper"] <= gain + lift + 1e-5 * gain
+    assert cb["gain_upper"] - gain >= 0.5 * lift        # the lift is on the right-hand side, not removed
+
+
+def test_super_solution_check_direction():
+    """The check that makes the certified bounds rigorous: with x = M^-1 D 1 exact, a
+    vector 1e-8 above x passes and one 1e-8 below fails, as does a copy of x lowered at a
+    single node.  Raised by 3e-11 only, x has a computed residual M z - D 1 that is
+    positive in every row yet inside the rounding of the FP64 product, so the check must
+    refuse it: the rounding margin is charged."""
+    from oracle.transient import DirectSolver
+    net = pgsynth.config1(nx=24, ny=20)
+    h = net.meta["h"]
+    M = matrices.nodal_matrices(net).system_matrix(h).tocsr()
+    rhs = M.diagonal()
+    x = DirectSolver(M.tocsc()).solve(rhs)
+    assert bounds.is_super_solution(M, rhs, x * (1 + 1e-8))
+    assert not bounds.is_super_solution(M, rhs, x * (1 - 1e-8))
+    low = x * (1 + 1e-8)
+    k = int(np.argmax(x))
+    low[k] = x[k] * (1 - 1e-6)
+    assert not bounds.is_super_solution(M, rhs, low)
+    thin = x * (1 + 3e-11)
+    assert np.all(M @ thin - rhs > 0)
+    assert not bounds.is_super_solution(M, rhs, thin)
+
+
 def test_accumulation_gain_bounds_error_propagation():
     """Per-step errors eta_k with |eta_k| <= 1 propagate through e_s = T e_{s-1} + eta_s,
     T = M^-1 C/h; the accumulation gain bounds |e_s| for every sign pattern, is
