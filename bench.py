@@ -38,8 +38,13 @@ def parse():
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=1024)
     ap.add_argument("--nsteps", type=int, default=1000, help="BE steps per transient")
+    ap.add_argument("--warm-start", type=int, default=-1,
+                    help="pg_options.warm_start: -1 automatic (the default), 0 previous value, 1 linear "
+                         "extrapolation, 2 load-aware")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-per-config", action="store_true", help="skip the configs 0, 2, 3, 4 object")
+    ap.add_argument("--per-config-only", action="store_true", help="print only the per-config object")
     ap.add_argument("--case", action="store_true",
                     help="profiling case: set up the grid, run one transient of --nsteps steps, exit")
     return ap.parse_args()
@@ -105,9 +110,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ncu capture of `bench.py --case --nsteps 2` on the 1024x1024x3 grid (the persistent
-# kernel's 2-step launch): its DRAM bytes and the work that launch did
-NCU_CAPTURE = {"dram_bytes": 7.41e9, "total_sweeps": 216, "total_outer": 4, "lattice_sweeps": 3}
+# ncu capture of the persistent kernel's launch on the 1024x1024x3 grid: its DRAM bytes,
+# the work that launch did, and the SHA-256 (first 16 hex digits) of the kernel source it
+# was taken on.  The bench reports `traffic` only while the source still matches.
+NCU_CAPTURE = {"dram_bytes": 7.41e9, "total_sweeps": 216, "total_outer": 4, "lattice_sweeps": 3, "nsteps": 2,
+               "kernel_sha16": None}
+KERNEL_SRC = os.path.join(ROOT, "paper_1409_7166_gb300", "csrc", "pg_kernels.cu")
+
+
+def kernel_sha16() -> str:
+    import hashlib
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def survey_bytes(st, n, mn, n_src, mixed: bool, nsteps: int) -> float:
+    """Algorithmic bytes of the recorded work by the per-unit figures of the method:
+
+    per node-sweep:            FP32 16 + 4 m/n, FP64 32 + 8 m/n  (each branch weight once,
+                               the correction read and written, the residual and 1/D read)
+    per node, FP64 residual pass (each outer pass):  24 + 8 m/n  (v, r, 1/D read, each weight
+                               once; the reduction is fused, nothing written)
+    per step:                  24 B per node + 36 B per PWL source  (right-hand side of Eq. 2)
+    """
+    sweep_b = (16 + 4 * mn) if mixed else (32 + 8 * mn)
+    return (st["total_sweeps"] * sweep_b * n + st["total_outer"] * (24 + 8 * mn) * n
+            + nsteps * (24 * n + 36 * n_src))
 
 
 def algorithmic_bytes(st, n, mn, n_src, mixed: bool, nsteps: int, extrap: bool = True) -> float:
@@ -174,8 +202,8 @@ def cpu_baseline_entry(n_full: int, unit_steps: bool = True) -> dict:
     d = oracle_sample_rate(nx, nx, nsteps)
     rate_sample = d["steps"] / d["steps_s"]                    # BE steps/s on the sample
     value = rate_sample * d["n"] / n_full                      # scaled to the full grid (linear in n)
-    return {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
-            "sample": (f"config-1 recipe at {nx}x{nx}x3 ({d['n']} nodes), {d['steps']} BE steps after the "
+    return {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle", "extrapolated": True,
+            "sample": (f"extrapolated: config-1 recipe at {nx}x{nx}x3 ({d['n']} nodes), {d['steps']} BE steps after the "
                        f"factorisation ({d['setup_s']:.1f} s, excluded), FP64 sparse LU solves, 1 thread; "
                        f"rate scaled by n_sample/n_full (optimistic for a direct solver)")}
 
@@ -251,6 +279,196 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ the other workloads
+
+C2_CHECK_STEPS = 100          # config 2: steps compared with the oracle field by field
+
+
+def _c3_sample(shapes):
+    """Grids of config 3 compared with the oracle: the smallest single-layer grid, the
+    smallest two-layer grid and the single-layer grid whose side is nearest 256."""
+    one = [k for k, (s, l) in enumerate(shapes) if l == 1]
+    two = [k for k, (s, l) in enumerate(shapes) if l == 2]
+    a = min(one, key=lambda k: shapes[k][0])
+    b = min(two, key=lambda k: shapes[k][0])
+    c = min((k for k in one if k != a), key=lambda k: abs(shapes[k][0] - 256))
+    return sorted({a, b, c})
+
+
+ORACLE_JOBS = f"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, {ROOT!r})
+import pgsynth
+from oracle import transient
+out = sys.argv[1]
+t = time.perf_counter()
+net = pgsynth.config0()
+V, _ = transient.transient(net, net.meta["h"], net.meta["nsteps"])
+np.save(out + "/c0.npy", V[1:])
+net = pgsynth.config2()
+V, IL = transient.transient(net, net.meta["h"], {C2_CHECK_STEPS})
+np.save(out + "/c2_v.npy", V[1:]); np.save(out + "/c2_il.npy", IL[1:])
+for k in json.loads(sys.argv[2]):
+    off, part = pgsynth.config3_part(k)
+    V, _ = transient.transient(part, 10e-12, 500)
+    np.save(out + f"/c3_{{k}}.npy", V[1:])
+print(json.dumps({{"oracle_s": time.perf_counter() - t}}))
+"""
+
+
+def per_config_entries(B, torch, warm_start: int) -> dict:
+    """Steps/s, node-sweeps/s, sweeps, the certified bound and the measured max-abs error
+    against the FP64 oracle for the other four workloads: config 0 in full; config 2 on its
+    first steps; config 3 on three of its grids, in both precisions (the mixed form against
+    plain FP64); config 4 by its certified bound (its oracle does not fit the bench's time).
+    Each transient is timed once (CUDA events of its launch) after a short warm-up."""
+    import tempfile
+
+    import numpy as np
+
+    import pgsynth
+
+    tmp = tempfile.mkdtemp(prefix="pg_oracle_")
+    shapes = pgsynth.config3_shapes()
+    pick = _c3_sample(shapes)
+    env = dict(os.environ, OMP_NUM_THREADS="4", OPENBLAS_NUM_THREADS="4")
+    orc = subprocess.Popen([sys.executable, "-c", ORACLE_JOBS, tmp, json.dumps(pick)], stdout=subprocess.PIPE,
+                           stderr=subprocess.PIPE, text=True, env=env)
+    stream = torch.cuda.current_stream()
+
+    def run(grid, h, nsteps, **out):
+        B.pg_reset(grid.handle)
+        B.pg_transient(grid.handle, h, min(nsteps, 5))          # warm-up (and per-h setup)
+        B.pg_reset(grid.handle)
+        st = B.pg_transient(grid.handle, h, nsteps, **out)
+        torch.cuda.synchronize()
+        return st
+
+    def entry(net, st, nsteps, prec):
+        t = st.device_ms / 1e3
+        return {"precision": prec, "nodes": int(net.n_nodes), "be_steps": nsteps, "steps_per_s": nsteps / t,
+                "node_sweeps_per_s": st.total_sweeps * net.n_nodes / t, "sweeps": int(st.total_sweeps),
+                "outer_passes": int(st.total_outer), "transient_ms": st.device_ms,
+                "certified_err_bound_V": None if st.err_bound != st.err_bound else st.err_bound,
+                "max_step_bound_V": st.max_step_bound, "lattice_sweeps": int(st.lattice_sweeps)}
+
+    res = {}
+    # config 0: 100x100 RC mesh, FP64 (its own precision), every node of every step
+    net = pgsynth.config0()
+    h, S = net.meta["h"], net.meta["nsteps"]
+    V0 = {}
+    for prec, name in ((B.PG_PREC_FP64, "fp64"), (B.PG_PREC_MIXED, "mixed")):
+        with B.Grid(net, precision=prec, warm_start=warm_start) as g:
+            B.pg_set_stream(g.handle, stream.cuda_stream)
+            v = torch.empty((S, net.n_nodes), dtype=torch.float64, device="cuda")
+            res[f"config0_{name}"] = entry(net, run(g, h, S, v_all=v), S, name)
+            V0[name] = v.cpu().numpy()
+    # config 2: 512x512x2 RLC, FP64; the first steps field by field in a separate run
+    net = pgsynth.config2()
+    h, S = net.meta["h"], net.meta["nsteps"]
+    V2 = {}
+    for prec, name in ((B.PG_PREC_FP64, "fp64"), (B.PG_PREC_MIXED, "mixed")):
+        with B.Grid(net, precision=prec, warm_start=warm_start) as g:
+            B.pg_set_stream(g.handle, stream.cuda_stream)
+            res[f"config2_{name}"] = entry(net, run(g, h, S), S, name)
+            v = torch.empty((C2_CHECK_STEPS, net.n_nodes), dtype=torch.float64, device="cuda")
+            il = torch.empty((C2_CHECK_STEPS, len(net.l_val)), dtype=torch.float64, device="cuda")
+            B.pg_reset(g.handle)
+            B.pg_transient(g.handle, h, C2_CHECK_STEPS, v_all=v, il_all=il)
+            V2[name] = (v.cpu().numpy(), il.cpu().numpy())
+    del net
+    # config 3: 256 grids in one launch, mixed and plain FP64; three grids sampled by probes
+    net = pgsynth.config3()
+    h, S = net.meta["h"], net.meta["nsteps"]
+    offs, sizes = net.meta["grid_offsets"], net.meta["grid_sizes"]
+    probes = np.concatenate([np.arange(offs[k], offs[k] + sizes[k], dtype=np.int32) for k in pick])
+    P3 = {}
+    for prec, name in ((B.PG_PREC_MIXED, "mixed"), (B.PG_PREC_FP64, "fp64")):
+        with B.Grid(net, precision=prec, warm_start=warm_start) as g:
+            B.pg_set_stream(g.handle, stream.cuda_stream)
+            pr = torch.tensor(probes, device="cuda")
+            pv = torch.empty((S, probes.size), dtype=torch.float64, device="cuda")
+            res[f"config3_{name}"] = entry(net, run(g, h, S, probes=pr, probe_v=pv), S, name)
+            P3[name] = pv.cpu().numpy()
+            del pv
+    res["config3_mixed"]["vs_fp64_steps_per_s"] = (res["config3_mixed"]["steps_per_s"] /
+                                                    res["config3_fp64"]["steps_per_s"])
+    del net
+    # config 4: 2048x2048 RC mesh, mixed precision
+    net = pgsynth.config4()
+    h, S = net.meta["h"], net.meta["nsteps"]
+    with B.Grid(net, precision=B.PG_PREC_MIXED, warm_start=warm_start) as g:
+        B.pg_set_stream(g.handle, stream.cuda_stream)
+        res["config4_mixed"] = entry(net, run(g, h, S), S, "mixed")
+    res["config4_mixed"]["max_abs_err_V"] = None
+    res["config4_mixed"]["err_note"] = ("oracle too large for the bench; the certified bound covers it, and the "
+                                        "full-size test recomputes that certificate from the oracle's assembly")
+    del net
+
+    # load scenarios of config 0: S copies of the grid in one launch (each copy its own
+    # weights) against S right-hand sides of one grid (one copy of the weights)
+    from paper_1409_7166_gb300 import batch
+    net = pgsynth.config0()
+    h, S = net.meta["h"], net.meta["nsteps"]
+    rng = np.random.default_rng(5)
+    scen = {}
+    for ns in (16, 64, 256):
+        loads = [np.asarray(net.i_v) * np.repeat(rng.uniform(0.0, 2.0, len(net.i_a)), np.diff(net.i_ptr))
+                 for _ in range(ns)]
+        cat = batch.concat(batch.scenario_copies(net, loads))
+        with B.Grid(cat, precision=B.PG_PREC_MIXED, warm_start=warm_start) as g:
+            B.pg_set_stream(g.handle, stream.cuda_stream)
+            stc = run(g, h, S)
+        iv = torch.tensor(np.stack(loads), device="cuda")
+        with B.Grid(net, precision=B.PG_PREC_MIXED, lattice_sweeps=-1, warm_start=warm_start) as g:
+            B.pg_set_stream(g.handle, stream.cuda_stream)
+            B.pg_transient_scenarios(g.handle, h, 5, iv)               # warm-up (and per-h setup)
+            sts = B.pg_transient_scenarios(g.handle, h, S, iv)
+            torch.cuda.synchronize()
+        scen[str(ns)] = {"copies_scenario_steps_per_s": ns * S / (stc.device_ms / 1e3),
+                         "shared_scenario_steps_per_s": ns * S / (sts.device_ms / 1e3),
+                         "copies_sweeps": int(stc.total_sweeps), "shared_sweeps": int(sts.total_sweeps),
+                         "shared_certified_err_bound_V": sts.err_bound, "copies_certified_err_bound_V": stc.err_bound}
+        scen[str(ns)]["shared_vs_copies"] = (scen[str(ns)]["shared_scenario_steps_per_s"] /
+                                             scen[str(ns)]["copies_scenario_steps_per_s"])
+    res["config0_scenarios"] = scen
+    del net
+
+    try:
+        out, err = orc.communicate(timeout=1200)
+        if orc.returncode != 0:
+            raise RuntimeError(err[-1500:])
+        oracle_s = json.loads(out.strip().splitlines()[-1])["oracle_s"]
+        Vo = np.load(tmp + "/c0.npy")
+        for name in ("fp64", "mixed"):
+            res[f"config0_{name}"]["max_abs_err_V"] = float(np.max(np.abs(V0[name] - Vo)))
+            res[f"config0_{name}"]["err_sample"] = "every node, all 100 steps"
+        Vo, ILo = np.load(tmp + "/c2_v.npy"), np.load(tmp + "/c2_il.npy")
+        for name in ("fp64", "mixed"):
+            v, il = V2[name]
+            res[f"config2_{name}"]["max_abs_err_V"] = float(np.max(np.abs(v - Vo)))
+            res[f"config2_{name}"]["il_max_rel_err"] = float(np.max(np.abs(il - ILo)) / np.max(np.abs(ILo)))
+            res[f"config2_{name}"]["err_sample"] = f"every node and inductor, steps 1-{C2_CHECK_STEPS}"
+        for name in ("mixed", "fp64"):
+            col, worst = 0, 0.0
+            for k in pick:
+                Vo = np.load(tmp + f"/c3_{k}.npy")
+                worst = max(worst, float(np.max(np.abs(P3[name][:, col:col + sizes[k]] - Vo))))
+                col += sizes[k]
+            res[f"config3_{name}"]["max_abs_err_V"] = worst
+            res[f"config3_{name}"]["err_sample"] = (
+                "every node of grids " + ", ".join(f"{k} ({shapes[k][0]}^2 x {shapes[k][1]})" for k in pick)
+                + ", all 500 steps")
+        res["oracle_s"] = oracle_s
+    except Exception as exc:       # the timings stand without the comparison
+        res["oracle_error"] = str(exc)[-500:]
+    finally:
+        import shutil
+        shutil.rmtree(tmp, ignore_errors=True)
+    return res
+
+
 # ------------------------------------------------------------------ our arm
 
 def main():
@@ -280,6 +498,10 @@ def main():
         dist.barrier()
     B.lib()
 
+    if args.per_config_only:
+        print(json.dumps({"per_config": per_config_entries(B, torch, args.warm_start)}), flush=True)
+        return
+
     net = pgsynth.config1(nx=args.nx, ny=args.ny)
     h = net.meta["h"]
     n = net.n_nodes
@@ -287,7 +509,7 @@ def main():
     n_src = len(net.i_a)
     nsteps = args.nsteps
     t0 = time.time()
-    grid = B.Grid(net, precision=B.PG_PREC_MIXED)
+    grid = B.Grid(net, precision=B.PG_PREC_MIXED, warm_start=args.warm_start)
     stream = torch.cuda.Stream()
     B.pg_set_stream(grid.handle, stream.cuda_stream)
     vmin = torch.empty(nsteps, dtype=torch.float64, device="cuda")
@@ -336,21 +558,35 @@ def main():
     node_sweeps = world * sweeps * n / t_max
     dev_ms = [s["device_ms"] for s in stats]
 
-    # roofline of the persistent kernel (the only kernel of consequence in the timed region)
+    # roofline of the persistent kernel (the only kernel of consequence in the timed region):
+    # the method's algorithmic bytes per launch over the launch's CUDA-event time
     peak, peak_kind = load_peaks()
-    alg = [algorithmic_bytes(s, n, mn, n_src, True, nsteps) for s in stats]
-    achieved = sum(alg) / (sum(dev_ms) / 1e3) / 1e9
-    # DRAM traffic per launch: ncu's dram__bytes_read.sum + dram__bytes_write.sum on a 2-step
-    # launch of this grid (the full 1000-step launch is too long to capture), scaled to the
-    # timed launch by the ratio of algorithmic bytes.  Valid for the kernel as captured.
-    cap = NCU_CAPTURE
-    captured = algorithmic_bytes(cap, n, mn, n_src, True, 2)
-    traffic_ratio = cap["dram_bytes"] / captured if (args.nx, args.ny) == (1024, 1024) else None
+    t_dev = sum(dev_ms) / 1e3
+    alg = [survey_bytes(s, n, mn, n_src, True, nsteps) for s in stats]
+    own = [algorithmic_bytes(s, n, mn, n_src, True, nsteps) for s in stats]
+    achieved = sum(alg) / t_dev / 1e9
     bpl = sum(alg) / len(alg)
+    # DRAM traffic per launch from the ncu capture, scaled to the timed launch by the ratio of
+    # algorithmic bytes when the capture was a shorter launch; null once the kernel changed
+    cap = NCU_CAPTURE
+    traffic = None
+    if (args.nx, args.ny) == (1024, 1024) and cap.get("kernel_sha16") == kernel_sha16():
+        traffic = bpl * cap["dram_bytes"] / survey_bytes(cap, n, mn, n_src, True, cap["nsteps"])
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": bpl * traffic_ratio if traffic_ratio else None,
-            "traffic_note": "ncu DRAM bytes of a 2-step launch of the same grid, scaled by algorithmic bytes",
-            "peak_kind": peak_kind, "bytes_per_launch": bpl, "kernel": "persistent_kernel<true>"}
+            "traffic": traffic, "peak_kind": peak_kind, "bytes_per_launch": bpl, "kernel": "persistent_kernel<true, 34>",
+            "byte_model": "16 + 4 m/n per FP32 node-sweep, 24 + 8 m/n per node per FP64 residual pass, "
+                          "24 B/node + 36 B/source per step",
+            "units_per_launch": {"node_sweeps": sweeps / args.steps * n,
+                                 "outer_passes": sum(s["total_outer"] for s in stats) / args.steps,
+                                 "steps": nsteps, "nodes": n, "sources": n_src, "m_over_n": mn},
+            "dram_achieved": traffic / (t_dev / len(stats)) / 1e9 if traffic else None,
+            "dram_frac": traffic / (t_dev / len(stats)) / 1e9 / peak if traffic else None,
+            "traffic_note": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of a {cap['nsteps']}-step launch "
+                             "of the same grid, scaled by algorithmic bytes" if traffic else
+                             "no ncu capture of the current kernel source"),
+            "implementation_bytes": {"achieved": sum(own) / t_dev / 1e9, "frac": sum(own) / t_dev / 1e9 / peak,
+                                     "note": "the implementation's own byte count: two Thomas factors per column, "
+                                             "the carried M d, the incremental step start and the outputs"}}
 
     # end to end: new load scenario from pinned host memory, outputs back to host, every step
     e2e = None
@@ -373,6 +609,14 @@ def main():
         e2e = {"value": world * nsteps * len(te) / sum(te), "unit": "steps/s",
                "h2d_bytes_per_step": int(it_h.numel() * 8 + iv_h.numel() * 8),
                "d2h_bytes_per_step": int(nsteps * (8 + 4))}
+
+    per_config = None
+    if rank == 0 and world == 1 and not args.no_per_config:
+        grid.close()
+        try:
+            per_config = per_config_entries(B, torch, args.warm_start)
+        except Exception as exc:   # keep the line for the bench workload
+            per_config = {"error": str(exc)[-500:]}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -399,6 +643,10 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "node_sweeps_per_s": node_sweeps,
             "sweeps_per_transient": sweeps / args.steps,
+            "outer_passes_per_transient": sum(s["total_outer"] for s in stats) / args.steps,
+            "phase_ms": {k: sum(s["phase_ms"][i] for s in stats) / args.steps
+                         for i, k in enumerate(("step_start", "inner_solves", "outer_passes", "step_end"))},
+            "warm_start": args.warm_start,
             "max_step_bound_V": max(s["max_step_bound"] for s in stats),
             "err_bound_V": max(s["err_bound"] for s in stats),
             "omega": stats[0]["omega"], "kappa": stats[0]["kappa"], "q": stats[0]["q"],
@@ -409,6 +657,7 @@ def main():
             "setup_s": setup_s,
             "transient_ms": {"best": min(ms), "median": float(sorted(ms)[len(ms) // 2]), "mean": sum(ms) / len(ms)},
             "roofline": roof,
+            "per_config": per_config,
             "cpu_baseline": cpu,
             "cpu_sor_baseline": cpu_sor["point"],
             "cpu_block_sor_baseline": cpu_sor["column_block"],

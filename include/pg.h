@@ -105,7 +105,13 @@ typedef struct pg_options {
     double step_tol;          /* per-step solve target, V; 0 -> derived from tol: RC grids use
                                  0.9 tol / kacc (see pg_run_stats), grids with inductors 1e-4 tol */
     int32_t max_sweeps;       /* cap on relaxation sweeps per step (0 -> 20000) */
-    int32_t warm_start;       /* 0: V(s-1) as in Algorithm 1; 1: linear extrapolation (default) */
+    int32_t warm_start;       /* 0: V(s-1) as in Algorithm 1; 1: linear extrapolation;
+                                 2: linear extrapolation while the load currents change, damped to
+                                 V(s-1) + (V(s-1) - V(s-2)) / 2 once they have been constant for
+                                 two steps (explicit form; the three-level form extrapolates fully);
+                                 -1 (default): 2 for grids without inductors, 1 with inductors
+                                 (an RC grid relaxes monotonically once its loads are quiet; an
+                                 RLC grid keeps ringing, and full extrapolation follows it) */
     double inner_reduction;   /* PG_PREC_MIXED: residual reduction asked of one FP32 inner solve;
                                  0 (default) -> 1e-1 for netlists of more than 8 lattices (a batch:
                                  more frequent FP64 passes let converged grids drop out sooner), else
@@ -131,7 +137,22 @@ typedef struct pg_options {
                                  state's inductor currents; pg_initial_conditions gives the paper's two
                                  levels instead.  No il_all output; step errors add up over the steps
                                  instead of decaying, so err_bound is NaN */
+    int32_t colouring;        /* update order of the neighbour-list (point) sweeps, which Section IV-A
+                                 leaves open (any order converges, Theorem 1):
+                                 PG_COLOUR_AUTO (0, default): red-black where the netlist is
+                                 bipartite, else greedy multicolour; PG_COLOUR_RED_BLACK: the same,
+                                 named; PG_COLOUR_FOUR: on lattice netlists four colours
+                                 ((x + l) mod 2) + 2 (y mod 2), swept in that order (omega as for
+                                 red-black), elsewhere greedy multicolour.  The lattice inner solve
+                                 keeps its column red-black order whatever this says */
+    int32_t tile_rows;        /* rows of the lattice inner solve's shared-memory region: 0 (default)
+                                 or 34 (34 x 34 columns), or 66 (34 columns x 66 rows, one block per
+                                 SM: twice the interior per region load) */
 } pg_options;
+
+#define PG_COLOUR_AUTO 0
+#define PG_COLOUR_RED_BLACK 1
+#define PG_COLOUR_FOUR 2
 
 #define PG_FORM_EXPLICIT 0
 #define PG_FORM_THREE_LEVEL 1
@@ -255,7 +276,9 @@ pg_status pg_transient(pg_grid* g, double h, int32_t nsteps, const pg_output* ou
  * Option search by timed trials (the paper leaves omega and the sweep schedule
  * open, Section IV).  Builds the netlist once per structural candidate (lattice
  * block sweeps per barrier k in {off, 1, 2, 3} when the netlist describes
- * lattices and the precision is mixed; blocks per SM in {as many as fit, 1})
+ * lattices and the precision is mixed; with k > 0 region rows in {34, 66}, with
+ * the point sweeps colouring in {automatic, four colours} on lattice netlists;
+ * blocks per SM in {as many as fit, 1})
  * and, on each, times trial_steps transient steps from the DC point (best of
  * two runs, CUDA events) for every runtime candidate (inner reduction in {1e-3,
  * 1e-2, 1e-1} when mixed; omega - 1 of the automatic value scaled by {1, 1.01,
@@ -263,7 +286,7 @@ pg_status pg_transient(pg_grid* g, double h, int32_t nsteps, const pg_output* ou
  * at most 4x the winner's sweeps per step.  Every trial runs under the certified
  * stopping rule of `base` (tol), so only time is compared.  `base` (NULL ->
  * defaults) supplies every other field.  On success *best is `base` with
- * lattice_sweeps, blocks_per_sm, inner_reduction, jacobi and omega (0 = the automatic value;
+ * lattice_sweeps, tile_rows, colouring, blocks_per_sm, inner_reduction, jacobi and omega (0 = the automatic value;
  * a scaled value is tied to this h) set to the fastest candidate and *best_ms
  * (may be NULL) to its trial time.  stream: cudaStream_t for the trials or
  * NULL.  Errors: PG_ERR_INVALID_ARG, or the last failure when no candidate ran.
@@ -382,16 +405,19 @@ pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* o
  * errors as pg_solve, with these differences:
  *   - All scratch (permuted right-hand side, iterate, residuals, corrections,
  *     barrier and reduction words, statistics) lives in one file-scope device
- *     array of 32 MiB inside the library; every GPU that loads the library
- *     holds it until the process exits.  Grids whose scratch would not fit
- *     (about 830k padded nodes in FP64, 930k in mixed precision) are rejected
- *     with PG_ERR_INVALID_ARG and a message naming the limit.
+ *     array of 32 MiB inside the library.  CUDA loads the array's module, and
+ *     reserves its memory on a device, when its address is first looked up on
+ *     that device (cudaGetSymbolAddress, with the device current).  The first
+ *     pg_create_grid on each device makes that lookup, so the reservation
+ *     belongs to grid creation; the device then holds the array until the
+ *     process exits.  If the lookup failed there, this call returns
+ *     PG_ERR_CUDA naming the cause, and never retries it.  Grids whose scratch
+ *     would not fit (about 830k padded nodes in FP64, 930k in mixed precision)
+ *     are rejected with PG_ERR_INVALID_ARG and a message naming the limit.
  *   - The coefficients for h must already be assembled (one earlier pg_solve
  *     or pg_transient with the same h); otherwise PG_ERR_INVALID_ARG.  The
- *     call itself allocates no device memory and calls no allocating routine.
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current); make that first call
- *     before any stream capture.
+ *     call itself allocates no device memory, loads no module and calls no
+ *     allocating routine.  Its statistics are filled exactly as pg_solve's.
  *   - Every call shares the one array and it keeps the last call's contents;
  *     the call clears what must start at zero.  Calls that overlap on the GPU
  *     (other streams, other threads, other grids) race on it: serialise them.
@@ -399,6 +425,74 @@ pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* o
  */
 pg_status pg_solve_noalloc(pg_grid* g, double h, const double* b, double* x, double tol,
                            pg_run_stats* stats);
+
+/* Outputs of pg_transient_scenarios (each may be NULL). */
+typedef struct pg_scenario_output {
+    int32_t on_host;          /* 1: the pointers below are host memory, 0: device memory */
+    double* v_all;            /* [nsteps][n_scen][n_nodes] every scenario's node voltages */
+    double* vmin;             /* [nsteps][n_scen] every scenario's smallest node voltage */
+} pg_scenario_output;
+
+/*
+ * Many load scenarios of one RC grid in one persistent launch: n_scen right-hand
+ * sides of the same backward-Euler system (Eq. 2, M = C/h + G + G0), relaxed
+ * together (Eq. 16-17) so that every coefficient is read once for all of them.
+ * Scenario k's load currents are the grid's PWL sources with the breakpoint times
+ * of the netlist and the breakpoint values i_v[k * n_points .. (k + 1) * n_points)
+ * (n_points = the netlist's i_ptr[n_i]; host or device memory, found by address).
+ * Every scenario starts at v = Vdd, the DC point of a grid with one supply level, no
+ * resistor to ground and no load current at t = 0, and runs nsteps steps of length h
+ * with the grid's precision, tolerance and stopping rule; a step ends when the
+ * certified bound of its worst scenario meets the step target, so stats (the work
+ * of all scenarios together; err_bound covers every scenario) reads as for
+ * pg_transient.  The grid's own transient state is reset.  The paper solves one
+ * right-hand side per step; sharing the matrix across load patterns has no
+ * counterpart there.  Errors: PG_ERR_INVALID_ARG; PG_ERR_UNSUPPORTED for grids with
+ * inductors, the three-level form, grids built for the lattice inner solve (create
+ * them with lattice_sweeps = -1), or a start other than v = Vdd; PG_ERR_OOM;
+ * PG_ERR_NOT_CONVERGED; PG_ERR_TIMEOUT; PG_ERR_CUDA.
+ */
+pg_status pg_transient_scenarios(pg_grid* g, double h, int32_t nsteps, int32_t n_scen, const double* i_v,
+                                 const pg_scenario_output* out, pg_run_stats* stats);
+
+/*
+ * Row-block domain decomposition of one lattice grid (the device half).  The node
+ * update of Eq. 16-17 reads only the node and its neighbours, so a grid cut along y
+ * into blocks of rows (all layers of each column kept together) can be relaxed
+ * block by block: each block holds its rows plus one halo row on each side, and
+ * the halos are refreshed from the neighbouring blocks between half-sweeps.  The
+ * red-black order puts the colours in separate half-sweeps, so the decomposed
+ * iteration makes exactly the updates of the undecomposed one (a single block
+ * holding every row).  Layout: node (x, local row k, layer l) at (l*R + k)*nx + x,
+ * with R the row count of the array.  All pointers are device memory owned by the
+ * caller, FP64.
+ */
+typedef struct pg_row_block {
+    int32_t nx, rows, nl;     /* the block: rows [y0, y0 + rows) of an nx-wide lattice, nl layers */
+    int32_t y0;               /* its first global row: colours are the parity of x + y + l */
+    const double* w_e;        /* [nl][rows][nx] conductance to (x + 1, y, l); 0 on the last column */
+    const double* w_n;        /* [nl][rows + 1][nx] row k couples local rows k and k + 1 (row 0: the
+                                 halo below and the first row; row rows: the last row and the halo
+                                 above); 0 across the grid's outer edges */
+    const double* w_u;        /* [nl][rows][nx] conductance to layer l + 1; 0 on the top layer */
+    const double* inv_d;      /* [nl][rows][nx] 1 / D of Eq. 14 */
+    const double* rhs;        /* [nl][rows][nx] right-hand side */
+    double* x;                /* [nl][rows + 2][nx] iterate; local rows 0 and rows + 1 are the halos
+                                 (zero at the grid's outer edges) */
+} pg_row_block;
+
+/*
+ * One colour half-sweep (Eq. 16-17) over a block: every node of the colour (x + y + l
+ * of that parity) in rows 1..rows is over-relaxed with factor omega in (0, 2); the
+ * neighbour sum is formed in a fixed order.  *max_update (device, a non-negative
+ * double the caller zeroes) receives the largest unrelaxed update |(rhs + sum)/D - x|
+ * merged by max.  Stream-ordered on `stream` (a cudaStream_t, or NULL).  The paper
+ * has no multi-GPU schedule: this is the device step of the decomposition that
+ * Eq. 16-17's locality allows.  Errors: PG_ERR_INVALID_ARG (null array, empty
+ * block, colour not 0 or 1, omega outside (0, 2)), PG_ERR_CUDA (launch).
+ */
+pg_status pg_block_half_sweep(const pg_row_block* blk, int32_t colour, double omega, double* max_update,
+                              void* stream);
 
 #ifdef __cplusplus
 }

@@ -23,6 +23,7 @@ STATUS = {0: "PG_OK", 1: "PG_ERR_INVALID_ARG", 2: "PG_ERR_FLOATING_NODE", 3: "PG
  PG_ERR_TIMEOUT, PG_ERR_UNSUPPORTED) = range(8)
 PG_PREC_FP64, PG_PREC_MIXED = 0, 1
 PG_FORM_EXPLICIT, PG_FORM_THREE_LEVEL = 0, 1
+PG_COLOUR_AUTO, PG_COLOUR_RED_BLACK, PG_COLOUR_FOUR = 0, 1, 2
 PG_DEBUG_SKIP_ARRIVAL = 1
 
 _i32p = C.POINTER(C.c_int32)
@@ -47,7 +48,17 @@ class pg_options(C.Structure):
                 ("inner_reduction", C.c_double), ("threads_per_block", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("barrier_timeout_s", C.c_double),
                 ("debug_flags", C.c_int32), ("lattice_sweeps", C.c_int32), ("jacobi", C.c_int32),
-                ("form", C.c_int32)]
+                ("form", C.c_int32), ("colouring", C.c_int32), ("tile_rows", C.c_int32)]
+
+
+class pg_row_block(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("rows", C.c_int32), ("nl", C.c_int32), ("y0", C.c_int32),
+                ("w_e", C.c_void_p), ("w_n", C.c_void_p), ("w_u", C.c_void_p), ("inv_d", C.c_void_p),
+                ("rhs", C.c_void_p), ("x", C.c_void_p)]
+
+
+class pg_scenario_output(C.Structure):
+    _fields_ = [("on_host", C.c_int32), ("v_all", C.c_void_p), ("vmin", C.c_void_p)]
 
 
 class pg_output(C.Structure):
@@ -122,10 +133,13 @@ def lib(path: Optional[str] = None) -> C.CDLL:
     L.pg_async_stats.argtypes = [vp, vp, C.POINTER(pg_run_stats)]
     L.pg_autotune.argtypes = [C.POINTER(pg_netlist), C.POINTER(pg_options), C.c_double, C.c_int32, vp,
                               C.POINTER(pg_options), _f64p]
+    L.pg_block_half_sweep.argtypes = [C.POINTER(pg_row_block), C.c_int32, C.c_double, vp, vp]
+    L.pg_transient_scenarios.argtypes = [vp, C.c_double, C.c_int32, C.c_int32, vp, C.POINTER(pg_scenario_output),
+                                         C.POINTER(pg_run_stats)]
     for name in ("pg_create_grid", "pg_set_stream", "pg_grid_info", "pg_set_state", "pg_get_state",
                  "pg_reset", "pg_update_sources", "pg_transient", "pg_step", "pg_solve", "pg_solve_noalloc",
                  "pg_update_values", "pg_adjoint", "pg_transient_async", "pg_async_stats", "pg_autotune", "pg_grid_components",
-                 "pg_initial_conditions"):
+                 "pg_initial_conditions", "pg_block_half_sweep", "pg_transient_scenarios"):
         getattr(L, name).restype = C.c_int
     if path is None:
         _LIB = L
@@ -372,3 +386,30 @@ class Grid:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def pg_block_half_sweep(nx: int, rows: int, nl: int, y0: int, w_e, w_n, w_u, inv_d, rhs, x, colour: int,
+                        omega: float, max_update, stream: int = 0) -> None:
+    """One colour half-sweep over a row block (device FP64 tensors, see ``pg_row_block``);
+    ``max_update`` is a device float64 scalar the caller zeroes (max-merged)."""
+    for name, t in (("w_e", w_e), ("w_n", w_n), ("w_u", w_u), ("inv_d", inv_d), ("rhs", rhs), ("x", x),
+                    ("max_update", max_update)):
+        if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
+            raise TypeError(f"pg_block_half_sweep: {name} must be a contiguous CUDA tensor")
+    blk = pg_row_block(int(nx), int(rows), int(nl), int(y0), _ptr(w_e), _ptr(w_n), _ptr(w_u), _ptr(inv_d),
+                       _ptr(rhs), _ptr(x))
+    _check(lib().pg_block_half_sweep(C.byref(blk), int(colour), float(omega), _ptr(max_update),
+                                     C.c_void_p(stream)), "pg_block_half_sweep")
+
+
+def pg_transient_scenarios(h, step_h: float, nsteps: int, i_v, v_all=None, vmin=None) -> pg_run_stats:
+    """``i_v``: ``[n_scen, n_points]`` PWL breakpoint values of each scenario (host or
+    device); outputs ``v_all`` ``[nsteps, n_scen, n_nodes]`` and ``vmin`` ``[nsteps, n_scen]``."""
+    n_scen = int(i_v.shape[0])
+    out = pg_scenario_output()
+    out.on_host = _on_host(v_all, vmin)
+    out.v_all = _ptr(v_all); out.vmin = _ptr(vmin)
+    st = pg_run_stats()
+    _check(lib().pg_transient_scenarios(h, float(step_h), int(nsteps), n_scen, _ptr(i_v), C.byref(out), C.byref(st)),
+           "pg_transient_scenarios")
+    return st

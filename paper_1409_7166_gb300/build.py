@@ -15,8 +15,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libpg.so")
-SOURCES = ["pg_kernels.cu", "pg_api.cpp", "pg_build.cpp", "pg_noalloc.cu", "pg_tune.cpp", "pg_init.cpp"]
-HEADERS = [os.path.join(CSRC, "pg_internal.h"), os.path.join(CSRC, "pg_grid.h"), os.path.join(ROOT, "include", "pg.h")]
+SOURCES = ["pg_kernels.cu", "pg_api.cpp", "pg_build.cpp", "pg_noalloc.cu", "pg_tune.cpp", "pg_init.cpp",
+           "pg_domain.cu", "pg_scenarios.cu"]
+HEADERS = [os.path.join(CSRC, "pg_internal.h"), os.path.join(CSRC, "pg_grid.h"), os.path.join(CSRC, "pg_device.cuh"),
+           os.path.join(ROOT, "include", "pg.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

@@ -124,14 +124,17 @@ pg_status alloc_device(pg_grid* g) {
         float* lw[5];
         for (auto& q : lw) if (!(q = g->alloc<float>(P.n))) return PG_ERR_OOM;
         d.lwE = lw[0]; d.lwN = lw[1]; d.lwU = lw[2]; d.lm = lw[3]; d.lip = lw[4];
-        // tiles of T^2 interior columns per lattice, and columns per lattice
-        const int nlat = (int)P.lats.size() / 4, T = lattice_tile_side(lat_k);
+        // tiles of T x TY interior columns per lattice, and columns per lattice
+        const int rows = g->opt.tile_rows > 0 ? g->opt.tile_rows : kLatSide;
+        const int nlat = (int)P.lats.size() / 4, T = lattice_tile_side(lat_k), TY = lattice_tile_rows(lat_k, rows);
+        d.lat_rows = rows;
+        d.lat_astride = P.lat_maxnl * rows * kLatW;
         lat_info = P.lats;
         lat_tile0.assign(nlat + 1, 0);
         lat_col0.assign(nlat + 1, 0);
         for (int L = 0; L < nlat; ++L) {
             const int nx = P.lats[4 * L + 1], ny = P.lats[4 * L + 2];
-            lat_tile0[L + 1] = lat_tile0[L] + ((nx + T - 1) / T) * ((ny + T - 1) / T);
+            lat_tile0[L + 1] = lat_tile0[L] + ((nx + T - 1) / T) * ((ny + TY - 1) / TY);
             lat_col0[L + 1] = lat_col0[L] + (int64_t)nx * ny;
         }
         int32_t* li = g->alloc<int32_t>(lat_info.size());
@@ -189,8 +192,28 @@ pg_status alloc_device(pg_grid* g) {
     st.md = g->alloc<double>(np);
     if (!st.md) return PG_ERR_OOM;
     d.n_src = (int32_t)(P.pwl_ptr.size() - 1);
-    st.isrc = g->alloc<double>(2 * (size_t)std::max(d.n_src, 1));
-    if (!st.isrc) return PG_ERR_OOM;
+    {
+        // per-node load currents: a node with one load takes its source's value directly, a
+        // node with several sums them (CSR order, deterministic)
+        std::vector<int32_t> na(std::max(d.n_src, 1), kLoadNone), nb(std::max(d.n_src, 1), kLoadNone), multi;
+        for (int i = 0; i < np; ++i) {
+            const int cnt = P.ld_ptr[i + 1] - P.ld_ptr[i];
+            if (cnt >= 2) multi.push_back(i);
+            for (int q = P.ld_ptr[i]; q < P.ld_ptr[i + 1]; ++q) {
+                const int sid = P.ld_idx[q];
+                const int e = (sid > 0 ? sid : -sid) - 1;
+                (sid > 0 ? na : nb)[e] = cnt == 1 ? i : kLoadMulti;
+            }
+        }
+        int32_t* sa = g->alloc<int32_t>(na.size());
+        int32_t* sb = g->alloc<int32_t>(nb.size());
+        int32_t* mn = g->alloc<int32_t>(std::max<size_t>(multi.size(), 1));
+        st.inode = g->alloc<double>(2 * (size_t)np);
+        if (!sa || !sb || !mn || !st.inode) return PG_ERR_OOM;
+        if ((s = upload(g, sa, na)) || (s = upload(g, sb, nb)) || (s = upload(g, mn, multi))) return s;
+        CK(cudaMemsetAsync(st.inode, 0, 2 * (size_t)np * sizeof(double), g->stream));
+        d.src_na = sa; d.src_nb = sb; d.n_multi = (int32_t)multi.size(); d.multi_node = mn;
+    }
     st.r64 = g->alloc<double>(np);
     if (!st.il || !st.r64) return PG_ERR_OOM;
     CK(cudaMemsetAsync(st.il, 0, std::max(1, P.n_l) * sizeof(double), g->stream));
@@ -212,8 +235,9 @@ pg_status alloc_device(pg_grid* g) {
     if (!g->d_x) return PG_ERR_OOM;
 
     // launch shape: every warp gets the same number of slices per colour sweep
+    g->smem = persistent_smem_bytes(g->mixed, d.lat_rows, d.lwE ? P.lat_maxnl : 0);
     int bps = 0;
-    CK(persistent_occupancy(g->mixed, g->threads, &bps));
+    CK(persistent_occupancy(g->mixed, d.lat_rows, g->threads, g->smem, &bps));
     if (g->opt.blocks_per_sm > 0) bps = std::min(bps, g->opt.blocks_per_sm);
     if (bps < 1) { g_last_error = "kernel does not fit on an SM"; return PG_ERR_CUDA; }
     const int wpb = g->threads / 32;
@@ -234,6 +258,7 @@ pg_status alloc_device(pg_grid* g) {
     c.stats = g->alloc<double>(kStatCount);
     if (!c.bar_count || !c.bar_gen || !c.err || !c.red || !c.blk_min || !c.blk_arg || !c.stats) return PG_ERR_OOM;
     if (d.lwE && !(c.lat_R = g->alloc<unsigned long long>(2 * (size_t)d.n_lats))) return PG_ERR_OOM;
+    if (!(c.ld_flags = g->alloc<unsigned>(4))) return PG_ERR_OOM;
     CK(cudaMemsetAsync(c.bar_gen, 0, sizeof(unsigned), g->stream));
     CK(cudaEventCreate(&g->ev0));
     CK(cudaEventCreate(&g->ev1));
@@ -324,6 +349,11 @@ pg_status assemble_h(pg_grid* g, double h) {
 
 }  // namespace
 
+// warm_start = 2: extrapolation weight once the loads have been static for two intervals
+// (full extrapolation there carries the previous steps' iteration errors forward, up to
+// three times the per-step target)
+constexpr double kThetaStatic = 0.5;
+
 RunParams pg::base_params(const pg_grid* g) {
     RunParams rp{};
     rp.mixed = g->mixed;
@@ -337,7 +367,11 @@ RunParams pg::base_params(const pg_grid* g) {
     rp.timeout_ns = (long long)(g->opt.barrier_timeout_s * 1e9);
     rp.debug_flags = g->opt.debug_flags;
     rp.cur = g->vL; rp.prev = g->vP;
-    rp.warm_extrap = g->opt.warm_start;
+    // automatic warm start: damped once the loads are quiet on RC grids, full extrapolation
+    // on grids with inductors (their LC response keeps moving after the loads stop)
+    const int ws = g->opt.warm_start < 0 ? (g->P.n_l == 0 ? 2 : 1) : g->opt.warm_start;
+    rp.warm_extrap = ws != 0;
+    rp.warm_theta_static = ws == 2 ? kThetaStatic : 1.0;
     rp.lat_k = g->dg.lwE ? g->lat_k : 0;
     rp.three_level = g->opt.form == PG_FORM_THREE_LEVEL;
     rp.jacobi = g->opt.jacobi;
@@ -363,7 +397,7 @@ pg_status run(pg_grid* g, const RunParams& rp, double* stats, float* ms) {
     pg_status s0 = clear_ctl(g);
     if (s0) return s0;
     CK(cudaEventRecord(g->ev0, g->stream));
-    CK(launch_persistent(g->mixed, g->dg, g->ds, g->dc, rp, g->blocks, g->threads, g->stream));
+    CK(launch_persistent(g->mixed, g->dg, g->ds, g->dc, rp, g->blocks, g->threads, g->smem, g->stream));
     CK(cudaEventRecord(g->ev1, g->stream));
     int32_t err = 0;
     CK(cudaMemcpyAsync(&err, g->dc.err, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
@@ -561,7 +595,9 @@ pg_status prepare_h(pg_grid* g, double h) {
         // are too): Young's optimum, taken 1 % high in omega - 1.  The SOR radius falls
         // steeply up to the optimum and rises with slope 1 past it, so an omega from an
         // estimated rho errs upward.  Other colourings use Gauss-Seidel.
-        if (g->P.ncol == 2 || g->dg.lwE) {
+        // (the four-colour lattice order takes the red-black value too: a heuristic that
+        // pg_autotune scales up and down)
+        if (g->P.ncol == 2 || g->dg.lwE || (g->opt.colouring == PG_COLOUR_FOUR && g->P.lattice)) {
             const double young = 2.0 / (1.0 + std::sqrt(1.0 - r * r));
             g->omega = std::min(1.0 + kOmegaOver * (young - 1.0), 0.5 * (young + 2.0));
         } else {
@@ -709,7 +745,16 @@ pg_status create_impl(const pg_netlist* nl, const pg_options* opt, std::unique_p
     if (o.barrier_timeout_s <= 0.0) o.barrier_timeout_s = 2.0;
     if (o.lattice_sweeps > 7) { g_last_error = "lattice_sweeps must be <= 7"; return PG_ERR_INVALID_ARG; }
     if (o.jacobi != 0 && o.jacobi != 1) { g_last_error = "jacobi must be 0 or 1"; return PG_ERR_INVALID_ARG; }
+    if (o.warm_start < -1 || o.warm_start > 2) { g_last_error = "warm_start must be -1, 0, 1 or 2"; return PG_ERR_INVALID_ARG; }
     if (o.jacobi && o.omega > 1.0) { g_last_error = "damped Jacobi needs omega <= 1"; return PG_ERR_INVALID_ARG; }
+    if (o.colouring < PG_COLOUR_AUTO || o.colouring > PG_COLOUR_FOUR) {
+        g_last_error = "colouring must be PG_COLOUR_AUTO, PG_COLOUR_RED_BLACK or PG_COLOUR_FOUR";
+        return PG_ERR_INVALID_ARG;
+    }
+    if (o.tile_rows != 0 && o.tile_rows != 34 && o.tile_rows != 66) {
+        g_last_error = "tile_rows must be 0, 34 or 66";
+        return PG_ERR_INVALID_ARG;
+    }
     if (o.form != PG_FORM_EXPLICIT && o.form != PG_FORM_THREE_LEVEL) {
         g_last_error = "form must be PG_FORM_EXPLICIT or PG_FORM_THREE_LEVEL";
         return PG_ERR_INVALID_ARG;
@@ -717,7 +762,7 @@ pg_status create_impl(const pg_netlist* nl, const pg_options* opt, std::unique_p
     g->threads = o.threads_per_block;
     g->mixed = o.precision == PG_PREC_MIXED;
     std::string why;
-    pg_status s = build_packed(nl, &g->P, &why, g->mixed && !o.jacobi ? o.lattice_sweeps : INT32_MIN);
+    pg_status s = build_packed(nl, &g->P, &why, g->mixed && !o.jacobi ? o.lattice_sweeps : INT32_MIN, o.colouring);
     if (s) { g_last_error = why; return s; }
     g->nc.from(nl);
     compute_dc_trivial(g.get());
@@ -726,6 +771,7 @@ pg_status create_impl(const pg_netlist* nl, const pg_options* opt, std::unique_p
     int coop = 0;
     CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device));
     if (!coop) { g_last_error = "device lacks cooperative launch"; return PG_ERR_CUDA; }
+    pg::noalloc_bind_device(g->device);
     if ((s = alloc_device(g.get()))) return s;
     out = std::move(g);
     return PG_OK;
@@ -734,6 +780,12 @@ pg_status create_impl(const pg_netlist* nl, const pg_options* opt, std::unique_p
 // `prior`: the largest per-step bound of the series before this run (the start state's
 // error and earlier runs continued by this one); the accumulated bound covers both.
 pg_status fill_stats(pg_grid* g, const double* st, float ms, pg_run_stats* out, double prior) {
+    return pg::fill_run_stats(g, st, ms, out, prior);
+}
+
+}  // namespace
+
+pg_status pg::fill_run_stats(pg_grid* g, const double* st, float ms, pg_run_stats* out, double prior) {
     if (!out) return PG_OK;
     std::memset(out, 0, sizeof(*out));
     out->steps_done = (int64_t)st[kStatSteps];
@@ -758,8 +810,6 @@ pg_status fill_stats(pg_grid* g, const double* st, float ms, pg_run_stats* out, 
     return PG_OK;
 }
 
-}  // namespace
-
 extern "C" {
 
 void pg_default_options(pg_options* o) {
@@ -770,7 +820,7 @@ void pg_default_options(pg_options* o) {
     o->tol = 1e-6;
     o->step_tol = 0.0;
     o->max_sweeps = 20000;
-    o->warm_start = 1;
+    o->warm_start = -1;
     o->inner_reduction = 0.0;
     o->threads_per_block = 256;
     o->blocks_per_sm = 0;
@@ -1139,7 +1189,7 @@ pg_status pg_transient_async(pg_grid* g, double h, int32_t nsteps, const double*
     }
     g->has_state = false;          // the host does not follow the device state of this launch
     if ((s = clear_ctl(g))) return s;
-    CK(launch_persistent(g->mixed, g->dg, g->ds, g->dc, rp, g->blocks, g->threads, g->stream));
+    CK(launch_persistent(g->mixed, g->dg, g->ds, g->dc, rp, g->blocks, g->threads, g->smem, g->stream));
     if (dstats) {
         CK(cudaMemcpyAsync(dstats, g->dc.stats, kStatCount * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
         CK(cudaMemcpyAsync(static_cast<char*>(dstats) + kStatCount * sizeof(double), g->dc.err, sizeof(int32_t),

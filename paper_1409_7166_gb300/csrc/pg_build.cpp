@@ -31,7 +31,7 @@ inline bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 }  // namespace
 
-pg_status build_packed(const pg_netlist* nl, Packed* P, std::string* why, int32_t lattice_policy) {
+pg_status build_packed(const pg_netlist* nl, Packed* P, std::string* why, int32_t lattice_policy, int32_t colouring) {
     auto fail = [&](pg_status s, const std::string& m) { if (why) *why = m; return s; };
     if (!nl || !P) return fail(PG_ERR_INVALID_ARG, "null netlist");
     const int32_t n = nl->n_nodes, p = nl->n_sources;
@@ -247,11 +247,34 @@ pg_status build_packed(const pg_netlist* nl, Packed* P, std::string* why, int32_
         }
     }
     int ncol = natural ? 1 : 2;
+    // four colours on a lattice: ((x + l) mod 2) + 2 (y mod 2) differs across every x, y and via
+    // neighbour pair, so each class is independent; another valid Gauss-Seidel order
+    const bool four = !natural && colouring == PG_COLOUR_FOUR && P->lattice;
     if (natural) {
         // one colour
-    } else if (!bipartite) {
+    } else if (four) {
+        for (size_t L = 0; L < P->lats.size() / 4; ++L) {
+            const int32_t off = P->lats[4 * L], lnx = P->lats[4 * L + 1], lny = P->lats[4 * L + 2],
+                          lnl = P->lats[4 * L + 3];
+            for (int32_t l = 0; l < lnl; ++l)
+                for (int32_t y = 0; y < lny; ++y)
+                    for (int32_t x = 0; x < lnx; ++x)
+                        colour[off + ((int64_t)l * lny + y) * lnx + x] = ((x + l) & 1) + 2 * (y & 1);
+        }
+        ncol = 0;
+        for (int i = 0; i < n; ++i) ncol = std::max(ncol, colour[i] + 1);
+        // a class no node fell into (a lattice one column or row wide) is dropped
+        std::vector<int32_t> remap(4, -1);
+        int m = 0;
+        for (int c = 0; c < ncol; ++c)
+            for (int i = 0; i < n; ++i)
+                if (colour[i] == c) { remap[c] = m++; break; }
+        for (int i = 0; i < n; ++i) colour[i] = remap[colour[i]];
+        ncol = m;
+    } else if (!bipartite || colouring == PG_COLOUR_FOUR) {
         std::fill(colour.begin(), colour.end(), -1);
         ncol = 0;
+        bipartite = false;
         std::vector<int32_t> seen(kMaxColours + 1, -1);
         for (int i = 0; i < n; ++i) {
             for (int64_t k = P->adj_ptr[i]; k < P->adj_ptr[i + 1]; ++k) {

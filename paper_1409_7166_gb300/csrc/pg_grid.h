@@ -74,6 +74,7 @@ struct pg_grid {
     cudaStream_t stream = nullptr;
     int n_sm = 0;
     int blocks = 1, threads = 256;
+    size_t smem = 0;               // dynamic shared memory of the persistent launch
     bool mixed = false;
     int lat_k = 0;                 // lattice inner solve: block sweeps per device barrier (0 = off)
     std::vector<void*> allocs;
@@ -128,4 +129,14 @@ pg_status paper_initial_levels(const NetCopy& nc, double h, double tol, void* st
                                std::vector<double>& il1);
 // Record the detail message returned by pg_last_error().
 void set_last_error(const std::string& msg);
+// Run statistics of one launch in the public form (shared by every solve entry point):
+// `st` the device statistics record, `ms` its event time, `prior` the largest per-step
+// bound of the series before the launch.
+pg_status fill_run_stats(pg_grid* g, const double* st, float ms, pg_run_stats* out, double prior);
+// Look up, once per device and with that device current, the device address of the fixed
+// scratch array of pg_solve_noalloc (pg_noalloc.cu).  The array's module is loaded, and its
+// memory reserved, by this first lookup; pg_create_grid calls it so that the reservation
+// happens at grid creation and never inside pg_solve_noalloc.  A failure is remembered and
+// reported by pg_solve_noalloc; it does not fail the grid's creation.
+void noalloc_bind_device(int device);
 }  // namespace pg

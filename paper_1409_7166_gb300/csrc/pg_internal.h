@@ -75,7 +75,9 @@ struct Packed {
 // Grids that take the lattice inner solve are packed in natural (caller) order with one
 // colour: no point sweep runs on them, and the FP64 passes then read the lattice-ordered
 // corrections contiguously.
-pg_status build_packed(const pg_netlist* nl, Packed* out, std::string* why, int32_t lattice_policy);
+// colouring: PG_COLOUR_* (the order of the neighbour-list sweeps).
+pg_status build_packed(const pg_netlist* nl, Packed* out, std::string* why, int32_t lattice_policy,
+                       int32_t colouring = PG_COLOUR_AUTO);
 
 // Lattice inner solve chosen automatically (lattice_sweeps = 0): k = 3 block sweeps per
 // barrier for lattices of 2-3 layers, and for single-layer lattices small enough that a
@@ -85,11 +87,17 @@ constexpr int32_t kSmallLattice = 200000;
 inline int32_t auto_lattice_k(int32_t lat_maxnl, int32_t n_nodes) {
     return lat_maxnl >= 2 || (lat_maxnl == 1 && n_nodes <= kSmallLattice) ? 3 : 0;
 }
-// Tile geometry of the lattice inner solve: a tile owns T x T interior columns of its
-// lattice, T = kLatSide - 4k for k exact sweeps per round (a ghost zone of 2k columns on
-// every side), so that the columns its first half-sweep updates are exactly 32 x 32.
+// Tile geometry of the lattice inner solve: a region of kLatSide columns by `rows` rows
+// (34 or 66) whose tile owns (kLatSide - 4k) x (rows - 4k) interior columns for k exact
+// sweeps per round (a ghost zone of 2k columns on every side), so that the columns its
+// first half-sweep updates are exactly 32 x (rows - 2), 16 pairs of them per half-warp row.
 constexpr int kLatSide = 34;
+constexpr int kLatW = 36;                          // shared-memory row stride (floats)
+constexpr int kLatArrays = 7;                      // delta, r, wE, wN, wU, Thomas m, 1/pivot
 inline int lattice_tile_side(int k) { return kLatSide - 4 * k; }
+inline int lattice_tile_rows(int k, int rows) { return rows - 4 * k; }
+// Dynamic shared memory of one lattice region: kLatArrays arrays of nl layers of rows x kLatW.
+inline size_t lattice_region_bytes(int rows, int nl) { return (size_t)kLatArrays * nl * rows * kLatW * sizeof(float); }
 // Refill the value-dependent parts of a packed grid (merged weights, grounded
 // parts, capacitances, 1/L) from a netlist with the same topology.
 pg_status refill_values(const pg_netlist* nl, Packed* P, std::string* why);
@@ -119,6 +127,13 @@ struct DevGrid {
     const int32_t* ld_ptr;
     const int32_t* ld_idx;
     int32_t n_src;           // PWL load sources
+    // per source and terminal: the permuted node whose only load this source is (its total
+    // load current is the source's, written directly), kLoadMulti for a node with several
+    // loads (summed per node over ld_ptr / ld_idx), kLoadNone for a terminal that is not a node
+    const int32_t* src_na;   // terminal the current leaves (its node's injection is -I)
+    const int32_t* src_nb;   // terminal the current enters (+I)
+    int32_t n_multi;         // permuted nodes with several loads
+    const int32_t* multi_node;
     const int64_t* pwl_ptr;
     const double* pwl_t;
     const double* pwl_v;
@@ -142,6 +157,8 @@ struct DevGrid {
     const float* lwU;        // weight to (x, y, l+1)
     const float* lm;         // column block (via couplings): Thomas multiplier u_{l-1} / d'_{l-1} (0 for l = 0)
     const float* lip;        // column block: inverse Thomas pivot 1 / d'_l
+    int32_t lat_rows;        // region rows of the lattice solve (34 or 66)
+    int32_t lat_astride;     // floats per staged array in shared memory: max layers x rows x kLatW
     int32_t natural;         // 1: the permutation is the identity on the real nodes (padding after them)
     // connected components (independent sub-circuits, Fig. 1)
     int32_t n_comp;
@@ -149,6 +166,8 @@ struct DevGrid {
 };
 
 enum Mode : int32_t { kModeTransient = 0, kModeSolve = 1 };
+constexpr int32_t kLoadNone = -1;      // src_na / src_nb: the terminal is ground or a source node
+constexpr int32_t kLoadMulti = -2;     // src_na / src_nb: the node has several loads
 
 struct DevState {
     double* v[3];            // rotating node-voltage buffers (permuted)
@@ -158,7 +177,8 @@ struct DevState {
     double* d64[2];          // correction buffers (FP64 sweeps)
     float* d32[2];           // correction buffers (FP32 sweeps)
     const double* rhs;       // kModeSolve: right-hand side (permuted)
-    double* isrc;            // [2 x n_src] load currents I_e(S h), slot S & 1 (transient mode)
+    double* inode;           // [2 x n_pad] total load current drawn from each node, (A_i^T I_s(S h))_i,
+                             // slot S & 1 (transient mode); nodes without loads stay 0
     double* md;              // [n_pad] M (v(s) - v(s-1)) by the end of step s (incremental step start)
 };
 
@@ -171,6 +191,8 @@ struct DevCtl {
     int32_t* blk_arg;               // [2 * nblocks]
     double* stats;                  // device statistics, see kStat*
     unsigned long long* lat_R;      // [2 * n_lats] per-lattice max |r| / D of the latest FP64 pass
+    unsigned int* ld_flags;         // [4] ring: word S & 3 is nonzero if a load current changed
+                                    // between (S-1) h and S h; null disables the damped warm start
 };
 
 enum Stat : int {
@@ -189,6 +211,8 @@ struct RunParams {
     int32_t cur, prev, prev2; // buffer indices of v at launch: current (= step0), previous
     int32_t have_prev;        // previous step exists (for extrapolation)
     int32_t warm_extrap;
+    double warm_theta_static; // extrapolation weight on steps whose last two load intervals are
+                              // static (1: plain linear extrapolation on every step)
     double omega;
     double kappa;             // bound constant ||M^-1 D||_inf
     double target;            // per-step target on max |r_i| / D_i  (= step_tol / kappa)
@@ -227,9 +251,13 @@ struct RunParams {
 #include <cuda_runtime.h>
 
 namespace pg {
+// smem: dynamic shared memory of the launch (persistent_smem_bytes for the grid)
 cudaError_t launch_persistent(bool mixed, const DevGrid& g, const DevState& st, const DevCtl& ctl,
-                              const RunParams& rp, int blocks, int threads, cudaStream_t stream);
-cudaError_t persistent_occupancy(bool mixed, int threads, int* blocks_per_sm);
+                              const RunParams& rp, int blocks, int threads, size_t smem, cudaStream_t stream);
+cudaError_t persistent_occupancy(bool mixed, int rows, int threads, size_t smem, int* blocks_per_sm);
+// Dynamic shared memory the persistent kernel needs: the TMA stages of the FP32 point sweep,
+// or (the same memory) the lattice region of `rows` rows and `nl` layers.
+size_t persistent_smem_bytes(bool mixed, int rows, int nl);
 cudaError_t launch_power_step(const DevGrid& g, const double* x, double* y, const unsigned long long* xmax_prev,
                               double* acc, unsigned long long* ymax, int blocks, cudaStream_t stream);
 cudaError_t launch_lattice_power(const DevGrid& g, const double* x, double* y, const unsigned long long* xmax_prev,

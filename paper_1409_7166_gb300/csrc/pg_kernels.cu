@@ -21,7 +21,7 @@
 #include <algorithm>
 #include <type_traits>
 
-#include "pg_internal.h"
+#include "pg_device.cuh"
 
 // Minimum resident blocks per SM requested from ptxas for the persistent
 // kernel (register budget = 65536 / (256 * PG_MIN_BLOCKS)).
@@ -39,212 +39,6 @@ namespace pg {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ long long global_ns() {
-    long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// ---- 4-wide loads/stores.  ldg*: read-only for the whole launch (nc path);
-//      ld*/st*: state that other blocks write during the launch.
-__device__ __forceinline__ void ldg4(const float* p, float (&x)[4]) {
-    float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
-}
-__device__ __forceinline__ void ldg4(const double* p, double (&x)[4]) {
-    double2 a = __ldg(reinterpret_cast<const double2*>(p));
-    double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
-    x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
-}
-__device__ __forceinline__ void ldg4(const int32_t* p, int (&x)[4]) {
-    int4 v = __ldg(reinterpret_cast<const int4*>(p));
-    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
-}
-__device__ __forceinline__ void ld4(const float* p, float (&x)[4]) {
-    float4 v = *reinterpret_cast<const float4*>(p);
-    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
-}
-__device__ __forceinline__ void ld4(const double* p, double (&x)[4]) {
-    double2 a = reinterpret_cast<const double2*>(p)[0];
-    double2 b = reinterpret_cast<const double2*>(p)[1];
-    x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
-}
-__device__ __forceinline__ void st4(float* p, const float (&x)[4]) {
-    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
-}
-__device__ __forceinline__ void st4(double* p, const double (&x)[4]) {
-    reinterpret_cast<double2*>(p)[0] = make_double2(x[0], x[1]);
-    reinterpret_cast<double2*>(p)[1] = make_double2(x[2], x[3]);
-}
-
-// softplus(u) = log(1 + e^u), evaluated without overflow: max(u, 0) + log1p(e^-|u|)
-__device__ __forceinline__ double softplus_d(double u) { return fmax(u, 0.0) + log1p(exp(-fabs(u))); }
-__device__ __forceinline__ double sigmoid_d(double u) { return 0.5 * (1.0 + tanh(0.5 * u)); }
-
-// max that lets a NaN win, so a diverged iterate is never mistaken for convergence
-__device__ __forceinline__ double nanmax(double a, double b) { return (a > b || a != a) ? a : b; }
-// FP32 version for the FP32 sweeps: GB300's FP64 pipe is a small fraction of its FP32
-// rate, so even a per-node double compare would cost a large share of a sweep.
-__device__ __forceinline__ float nanmaxf(float a, float b) { return (a > b || a != a) ? a : b; }
-template <typename T>
-__device__ __forceinline__ T nanmax_t(T a, T b) { return (a > b || a != a) ? a : b; }
-
-// Per-lattice maxima of val over the lane's 4 nodes (warp-collective): one atomic
-// per warp when the slice lies in one lattice (the common case), else per node.
-// Per-lattice maxima of |r|/D (the FP64 passes feed the lattice solve's skip test).
-// A warp's slices are contiguous and almost always inside one lattice, so the
-// warp keeps a running (lattice, max) pair (warp-uniform) and publishes it with
-// one atomic when the lattice changes and at the end of the pass (lat_flush);
-// a slice that straddles lattices publishes its values directly.
-struct LatAcc {
-    int L = -1;
-    double m = 0.0;
-};
-__device__ __forceinline__ void lat_flush(unsigned long long* latR, LatAcc& acc) {
-    if ((threadIdx.x & 31) == 0 && acc.L >= 0 && acc.m != 0.0)
-        atomicMax(latR + acc.L, (unsigned long long)__double_as_longlong(acc.m));
-    acc.L = -1;
-    acc.m = 0.0;
-}
-__device__ __forceinline__ void lattice_max(const DevGrid& g, unsigned long long* latR, int i0,
-                                            const double (&val)[4], LatAcc& acc) {
-    int L[4];
-    bool same = true;
-    const int L0 = __shfl_sync(0xffffffffu, __ldg(g.node_lat + i0), 0);
-    double m = 0.0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        L[j] = __ldg(g.node_lat + i0 + j);
-        same = same && (L[j] == L0 || L[j] < 0);
-        if (L[j] >= 0) m = nanmax(m, val[j]);
-    }
-    if (__all_sync(0xffffffffu, same)) {
-        for (int o = 16; o; o >>= 1) m = nanmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (L0 < 0) return;
-        if (L0 != acc.L) lat_flush(latR, acc);
-        acc.L = L0;
-        acc.m = nanmax(acc.m, m);
-    } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (L[j] >= 0 && val[j] != 0.0) atomicMax(latR + L[j], (unsigned long long)__double_as_longlong(val[j]));
-    }
-}
-
-// Order-preserving map of a double to an unsigned key (for min reductions).
-__device__ __forceinline__ unsigned long long order_key(double x) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
-__device__ __forceinline__ double key_value(unsigned long long k) {
-    unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
-    return __longlong_as_double((long long)b);
-}
-
-// Device-wide barrier with a time limit, fused with the block's max-reduction.
-//
-// Every block merges `v` (its threads' partial maxima) into the reduction slot
-// `slot` with one atomic, then arrives.  The generation word is cleared by the
-// host before each launch, so barrier number k (counted from 0 in every block)
-// completes when the generation reaches k + 1: no load is needed before
-// arriving.  Arrival is an acq_rel RMW and the wait an acquire load, both at
-// device scope, which publishes the block's writes (ordered before the
-// arrival by __syncthreads) to every block that passes the barrier.  .ok is
-// false for the whole block when an error was recorded (this block's wait
-// timed out, or another block's did); .val is the reduced value, read once
-// by thread 0 after the wait and broadcast.
-struct BarrierResult {
-    bool ok;
-    double val;
-};
-
-__device__ __forceinline__ BarrierResult grid_barrier(const DevCtl& c, unsigned nblocks, unsigned target_gen,
-                                                      long long timeout_ns, bool skip, double v,
-                                                      unsigned long long* slot) {
-    __shared__ double s_part[32];
-    __shared__ int s_ok;
-    __shared__ double s_val;
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (slot) {
-        for (int o = 16; o; o >>= 1) v = nanmax(v, __shfl_xor_sync(kFull, v, o));
-        if (l == 0) s_part[w] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(*c.bar_gen);
-        cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(*c.bar_count);
-        cuda::atomic_ref<int, cuda::thread_scope_device> err(*c.err);
-        if (slot) {
-            double m = s_part[0];
-            for (int q = 1; q < (int)(blockDim.x >> 5); ++q) m = nanmax(m, s_part[q]);
-            if (m != 0.0) atomicMax(slot, (unsigned long long)__double_as_longlong(m));
-        }
-        int ok = 1;
-        // test hook: a skipping block waits without being counted, so the barrier never opens
-        const unsigned arrived = skip ? 0u : cnt.fetch_add(1u, cuda::memory_order_acq_rel);
-        if (!skip && arrived == nblocks - 1) {
-            cnt.store(0u, cuda::memory_order_relaxed);
-            gen.store(target_gen, cuda::memory_order_release);
-        } else {
-            long long t0 = 0;
-            unsigned ns = 0;
-            for (int it = 0; gen.load(cuda::memory_order_acquire) < target_gen; ++it) {
-                if (err.load(cuda::memory_order_relaxed) != 0) { ok = 0; break; }
-                if (it == 64) t0 = global_ns();
-                if (it > 64) {
-                    if (global_ns() - t0 > timeout_ns) {
-                        int z = 0;
-                        err.compare_exchange_strong(z, (int)PG_ERR_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(ns);
-                    ns = ns < 128 ? ns + 16 : 128;
-                }
-            }
-        }
-        s_ok = ok;
-        if (slot) {
-            cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> r(*slot);
-            s_val = __longlong_as_double((long long)r.load(cuda::memory_order_relaxed));
-        }
-    }
-    __syncthreads();
-    return BarrierResult{s_ok != 0, slot ? s_val : 0.0};
-}
-
-// Value of current source e at time t (piecewise linear, held outside the breakpoints).
-__device__ __forceinline__ double pwl_eval(const DevGrid& g, int e, double t) {
-    int64_t lo = g.pwl_ptr[e], hi = g.pwl_ptr[e + 1] - 1;
-    const double* T = g.pwl_t;
-    const double* V = g.pwl_v;
-    if (t <= T[lo]) return V[lo];
-    if (t > T[hi]) return V[hi];
-    while (hi - lo > 1) {            // keep T[lo] < t <= T[hi]
-        int64_t mid = (lo + hi) >> 1;
-        if (t <= T[mid]) hi = mid; else lo = mid;
-    }
-    return V[lo] + (V[hi] - V[lo]) * ((t - T[lo]) / (T[hi] - T[lo]));
-}
-
-// Buffer selection by value (no dynamic indexing of kernel-parameter arrays,
-// which would force them into local memory).
-__device__ __forceinline__ double* vbuf(const DevState& st, int k) {
-    return k == 0 ? st.v[0] : (k == 1 ? st.v[1] : st.v[2]);
-}
-template <typename T>
-__device__ __forceinline__ T* dbuf(const DevState& st, int k);
-template <>
-__device__ __forceinline__ double* dbuf<double>(const DevState& st, int k) { return k ? st.d64[1] : st.d64[0]; }
-template <>
-__device__ __forceinline__ float* dbuf<float>(const DevState& st, int k) { return k ? st.d32[1] : st.d32[0]; }
-
-__device__ __forceinline__ double term_volt(const DevGrid& g, const double* v, int t) {
-    return t >= 0 ? v[t] : (t == PG_GROUND ? 0.0 : g.vdd[-2 - t]);
-}
-
 // ---- slice descriptors
 //
 // A warp owns a contiguous run of slices of every colour (the same run in
@@ -256,12 +50,6 @@ constexpr int kWarpsPerBlock = 8;
 constexpr int kCacheSlices = 32;    // descriptors cached per warp
 constexpr int kCachePool = 192;     // diagonal offsets cached per warp (32 slices x 6)
 
-struct SliceDesc {
-    long long off;   // element offset of the slice's slot 0
-    int K;           // slots per node
-    int dpos;        // >= 0: offsets at pool[dpos]; -1: explicit columns; <= -2: offsets at dia_off[-2 - dpos]
-};
-
 struct WarpCache {
     SliceDesc desc[kCacheSlices];
     int pool[kCachePool];
@@ -269,15 +57,6 @@ struct WarpCache {
     int lo[kMaxColours];         // first slice of colour c owned by the warp
     int cnt[kMaxColours];        // slices of colour c owned by the warp
 };
-
-__device__ __forceinline__ SliceDesc global_desc(const DevGrid& g, int s) {
-    SliceDesc d;
-    d.off = __ldg(g.slice_off + s);
-    d.K = __ldg(g.slice_w + s);
-    const int d0 = __ldg(g.slice_doff + s);
-    d.dpos = __ldg(g.slice_doff + s + 1) > d0 ? -2 - d0 : -1;
-    return d;
-}
 
 // Fill the calling warp's cache (once per launch).  Every lane must call it.
 __device__ void fill_warp_cache(const DevGrid& g, WarpCache& wc, int gwarp, int nwarps) {
@@ -362,7 +141,8 @@ __device__ __forceinline__ void df_acc(float& hi, float& lo, float a_hi, float a
     lo += err + fmaf(a_lo, x, e);
 }
 
-// sum_k w_k x_{col_k} of one slice row as a double-float, weights as FP32 pairs
+// sum_k w_k x_{col_k} of one slice row as a double-float, weights as FP32 pairs; two
+// slots' loads in flight at a time (more would spill in the mixed-precision kernel)
 template <typename Load>
 __device__ __forceinline__ void sell_row_df(const DevGrid& g, const WarpCache* wc, const SliceDesc& d, int s, int lane,
                                             Load xload, float (&hi)[4], float (&lo)[4]) {
@@ -371,6 +151,7 @@ __device__ __forceinline__ void sell_row_df(const DevGrid& g, const WarpCache* w
     const int* offs = d.dpos >= 0 ? wc->pool + d.dpos : (d.dpos <= -2 ? g.dia_off + (-2 - d.dpos) : nullptr);
 #pragma unroll
     for (int j = 0; j < 4; ++j) hi[j] = lo[j] = 0.f;
+#pragma unroll 2
     for (int k = 0; k < d.K; ++k) {
         const long long e = base + (long long)k * kSlice;
         float wh[4], wl[4];
@@ -393,7 +174,7 @@ __device__ __forceinline__ void sell_row_df(const DevGrid& g, const WarpCache* w
 // md = M (x0 - v(s-1)) for a step whose start residual is computed in full: M (v(s-1) -
 // v(s-2)) with the extrapolated warm start, 0 without.
 __device__ __forceinline__ void md_slice(const DevGrid& g, const WarpCache* wc, const SliceDesc& sd, const DevState& st,
-                                         int s, int lane, const double* vl, const double* vp, bool extrap) {
+                                         int s, int lane, const double* vl, const double* vp, bool extrap, float th) {
     const int i0 = s * kSlice + lane * kVec;
     double m[4] = {0.0, 0.0, 0.0, 0.0};
     if (extrap) {
@@ -404,22 +185,33 @@ __device__ __forceinline__ void md_slice(const DevGrid& g, const WarpCache* wc, 
         ld4(vp + i0, p);
 #pragma unroll
         for (int j = 0; j < 4; ++j) m[j] = D[j] * (a[j] - p[j]) - sig[j];
+        if (th != 1.0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) m[j] *= th;       // M (x0 - v(s-1)) = th M (v(s-1) - v(s-2))
+        }
     }
     st4(st.md + i0, m);
 }
 
+// Warm start v(s-1) + th (v(s-1) - v(s-2)); th = 1 keeps the plain form (same rounding).
+__device__ __forceinline__ double warm_value(double a, double p, double th) {
+    return th == 1.0 ? 2.0 * a - p : a + th * (a - p);
+}
+
 // Start of a step: RHS assembly (Eq. 2 / Eq. 10), warm start, FP64 residual.
-template <bool MIXED>
+template <bool MIXED, bool DAMP>
 __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* wc, const SliceDesc& sd,
                                             const DevState& st, const RunParams& rp, int s, int lane, int vL, int vP,
                                             int vF, bool extrap, bool three, bool inc, long long sabs, int dsel,
-                                            unsigned long long* latR, LatAcc& lacc) {
+                                            unsigned long long* latR, LatAcc& lacc, float th_in) {
+    const float th = DAMP ? th_in : 1.0f;
     const int i0 = s * kSlice + lane * kVec;
     const double* vl = vbuf(st, vL);
     const double* vp = vbuf(st, vP);
     double vw[4], b[4], D[4], iD[4];
     ldg4(g.D64 + i0, D);
     ldg4(g.invD64 + i0, iD);
+
     double base[4] = {0.0, 0.0, 0.0, 0.0};       // the residual is taken of M (x0 - base)
     if (rp.mode == kModeSolve) {
         ldg4(st.rhs + i0, b);
@@ -431,21 +223,18 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* w
         //   b - M v(s-1) = (C/h)(v(s-1) - v(s-2)) - A_l^T h L^-1 (A_l v(s-1) + A_ls v_d)
         //                  - A_i^T (I_s(t) - I_s(t-h)),
         // and the residual of x0 is that minus M (x0 - v(s-1)).
-        double pp[4], ch[4];
+        double pp[4], ch[4], Ic[4], Ip[4];
         ld4(vl + i0, base);
         ld4(vp + i0, pp);
         ldg4(g.ch + i0, ch);
+        ld4(st.inode + (sabs & 1) * (long long)g.n_pad + i0, Ic);          // (A_i^T I_s(t))_i
+        ld4(st.inode + ((sabs - 1) & 1) * (long long)g.n_pad + i0, Ip);    // (A_i^T I_s(t - h))_i
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            vw[j] = extrap ? 2.0 * base[j] - pp[j] : base[j];
-            double bj = ch[j] * (base[j] - pp[j]);
+            vw[j] = extrap ? warm_value(base[j], pp[j], th) : base[j];
+            double bj = ch[j] * (base[j] - pp[j]) - (Ic[j] - Ip[j]);
             const int i = i0 + j;
-            for (int q = __ldg(g.ld_ptr + i); q < __ldg(g.ld_ptr + i + 1); ++q) {
-                const int sid = __ldg(g.ld_idx + q);
-                const int e = (sid > 0 ? sid : -sid) - 1;
-                const double dI = st.isrc[(sabs & 1) * g.n_src + e] - st.isrc[((sabs - 1) & 1) * g.n_src + e];
-                bj -= sid > 0 ? dI : -dI;
-            }
+            if (g.n_l > 0)
             for (int q = __ldg(g.ind_ptr + i); q < __ldg(g.ind_ptr + i + 1); ++q) {
                 const int lid = __ldg(g.ind_idx + q);
                 const int e = (lid > 0 ? lid : -lid) - 1;
@@ -456,28 +245,25 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* w
             b[j] = bj;
         }
     } else {
-        double a[4], ch[4], cj[4];
+        double a[4], ch[4], cj[4], Ic[4];
         ld4(vl + i0, a);
         ldg4(g.ch + i0, ch);
         ldg4(g.cinj + i0, cj);
+        ld4(st.inode + (sabs & 1) * (long long)g.n_pad + i0, Ic);          // (A_i^T I_s(t + h))_i
         if (extrap) {
             double pp[4];
             ld4(vp + i0, pp);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) vw[j] = 2.0 * a[j] - pp[j];
+            for (int j = 0; j < 4; ++j) vw[j] = warm_value(a[j], pp[j], th);
         } else {
 #pragma unroll
             for (int j = 0; j < 4; ++j) vw[j] = a[j];
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            double bj = ch[j] * a[j] + cj[j];
+            double bj = ch[j] * a[j] + cj[j] - Ic[j];
             const int i = i0 + j;
-            for (int q = __ldg(g.ld_ptr + i); q < __ldg(g.ld_ptr + i + 1); ++q) {
-                const int sid = __ldg(g.ld_idx + q);
-                const double I = st.isrc[(sabs & 1) * g.n_src + (sid > 0 ? sid : -sid) - 1];
-                bj -= sid > 0 ? I : -I;               // A_i^T I_s(t+h)
-            }
+            if (g.n_l > 0)
             for (int q = __ldg(g.ind_ptr + i); q < __ldg(g.ind_ptr + i + 1); ++q) {
                 const int lid = __ldg(g.ind_idx + q);
                 const double il = st.il[(lid > 0 ? lid : -lid) - 1];
@@ -497,20 +283,28 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* w
         if (extrap) sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return vl[c] - vp[c]; }, sig);
         else sig[0] = sig[1] = sig[2] = sig[3] = 0.0;
     } else if (inc) {
-        // r = r_final(s-1) + increment - M (x0 - v(s-1)), the last term carried in md
+        // r = r_final(s-1) + increment - M (x0 - v(s-1)); md carries M (v(s-1) - v(s-2)), and
+        // M (x0 - v(s-1)) is th times that
         double rp_[4];
         ld4(st.r64 + i0, rp_);
-        if (extrap) ld4(st.md + i0, mdv);
+        if (extrap) {
+            ld4(st.md + i0, mdv);
+            if (th != 1.0) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mdv[j] *= th;
+            }
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) b[j] += rp_[j] - mdv[j];
         sig[0] = sig[1] = sig[2] = sig[3] = 0.0;
     } else if (extrap) {
-        sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return 2.0 * vl[c] - vp[c]; }, sig);
+        sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return warm_value(vl[c], vp[c], th); }, sig);
     } else {
         sell_row<1, double>(g, wc, sd, g.w64, s, lane, [&](int c) { return vl[c]; }, sig);
     }
-    // a full step's md (M (x0 - v(s-1))) is written by md_slice before phase A
-    if (track && inc && !extrap) st4(st.md + i0, mdv);
+    // a full step's md (M (x0 - v(s-1))) is written by md_slice before phase A; an
+    // incremental step stores it here when it differs from the carried value
+    if (track && inc && (!extrap || th != 1.0)) st4(st.md + i0, mdv);
     double r[4], sc[4], mon = 0.0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -518,7 +312,11 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* w
         sc[j] = fabs(r[j]) * iD[j];
         mon = nanmax(mon, sc[j]);
     }
-    if (latR) lattice_max(g, latR, i0, sc, lacc);
+    if (latR) {
+        int Lid[4];
+        ldg4(g.node_lat + i0, Lid);
+        lattice_max(latR, Lid, sc, lacc);
+    }
     st4(vbuf(st, vF) + i0, vw);
     st4(st.r64 + i0, r);
     if (MIXED && rp.lat_k > 0 && !g.natural) {
@@ -768,22 +566,16 @@ __device__ double sweep_colour_tma(const DevGrid& g, const WarpCache* wc, TmaWar
 // and write the next buffer: one device barrier per k sweeps, every branch
 // weight stored once (E, N, U per node).
 //
-// The side 34 makes the columns of the first half-sweep (distance >= 1) exactly
-// 32 x 32, one per thread slot (16 column pairs x 2 rows per warp, 2 rows per
-// thread).  A region starts at an even column (T and H are even); its rows are
-// staged from the 16-byte boundary at or below that column (a lead of 0 or 2
-// columns), so that on lattices whose width is a multiple of 4 every row copies
-// in aligned 16-byte pieces.  Shared-memory rows hold kLatW = 36 floats, which
-// keeps the two half-warps (adjacent rows, opposite colours) on disjoint banks.
-constexpr int kLatW = 36;                          // shared-memory row stride (floats)
-constexpr int kLatMaxL = 3;                        // layers held per region
-constexpr int kLatPlane = kLatSide * kLatW;
-constexpr int kLatArrays = 7;                      // delta, r, wE, wN, wU, Thomas m, 1/pivot
-static_assert(kLatSide - 2 == 32, "the first half-sweep covers 32 x 32 thread slots");
-
-__host__ __device__ constexpr int lattice_smem_bytes() {
-    return kLatArrays * kLatMaxL * kLatPlane * (int)sizeof(float);
-}
+// The width 34 makes the columns of the first half-sweep (distance >= 1) exactly 32
+// wide, 16 column pairs per half-warp row; a region has ROWS = 34 or 66 rows (32 or 64
+// of them in the first half-sweep: two or four rows per thread).  A region starts at an
+// even column (T and H are even); its rows are staged from the 16-byte boundary at or
+// below that column (a lead of 0 or 2 columns), so that on lattices whose width is a
+// multiple of 4 every row copies in aligned 16-byte pieces.  Shared-memory rows hold
+// kLatW = 36 floats, which keeps the two half-warps (adjacent rows, opposite colours) on
+// disjoint banks; each staged array holds lat_astride floats (the grid's largest layer
+// count times ROWS rows).
+static_assert(kLatSide - 2 == 32, "the first half-sweep covers 32 columns, 16 pairs per half-warp row");
 
 // Asynchronous global -> shared copies (no registers held while in flight);
 // src_bytes = 0 fills the destination with zeros.
@@ -802,13 +594,16 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // One tile (region of lattice L): load, 2k half-sweeps, store the interior.
 // Returns the max unrelaxed column update of the last sweep over the interior.
 // NL (layers) is a template parameter: the column solve unrolls completely.
-template <int NL>
+template <int NL, int ROWS>
 __device__ float lattice_tile(const DevGrid& g, int off, int nx, int ny, int tile, const float* __restrict__ dold,
                               float* __restrict__ dnew, const float* __restrict__ r, float omega, int k,
                               unsigned char* smem) {
-    const int H = 2 * k, T = kLatSide - 2 * H;
+    constexpr int kLatPlane = ROWS * kLatW;           // floats per layer of a staged array
+    constexpr int J = (ROWS - 2) / 16;                // rows per thread in a half-sweep
+    static_assert(ROWS == 34 || ROWS == 66, "regions of 34 or 66 rows");
+    const int H = 2 * k, T = kLatSide - 2 * H, TY = ROWS - 2 * H;
     const int tiles_x = (nx + T - 1) / T;
-    constexpr int A = kLatMaxL * kLatPlane;           // floats per array
+    const int A = g.lat_astride;                      // floats per array
     float* sd = reinterpret_cast<float*>(smem);
     float* sr = sd + A;
     float* se = sd + 2 * A;
@@ -821,7 +616,7 @@ __device__ float lattice_tile(const DevGrid& g, int off, int nx, int ny, int til
     const int rsub = lane >> 4;                        // half-warps take adjacent rows (no bank conflicts)
     const long long plane = (long long)nx * ny;
     // region: columns [x0, x0 + 34), rows [y0, y0 + 34); shared column c holds x0 - lead + c
-    const int x0 = (tile % tiles_x) * T - H, y0 = (tile / tiles_x) * T - H;
+    const int x0 = (tile % tiles_x) * T - H, y0 = (tile / tiles_x) * TY - H;
     const int lead = x0 & 3;                           // 0 or 2: x0 is even
     const int xa = x0 - lead;
     auto src_of = [&](int arr) -> const float* {       // by value: no local array
@@ -832,7 +627,7 @@ __device__ float lattice_tile(const DevGrid& g, int off, int nx, int ny, int til
         // rows of 16-byte pieces: a piece (xa + 4c, ..., +3) is wholly inside the lattice or
         // wholly outside; the (piece, array) pairs are spread over the threads
         constexpr int kChunks = kLatW / 4;
-        constexpr int kPieces = kLatSide * kChunks;
+        constexpr int kPieces = ROWS * kChunks;
         for (int q = threadIdx.x; q < kPieces * kLatArrays; q += blockDim.x) {
             const int arr = q / kPieces, pos = q - arr * kPieces;
             const int ry = pos / kChunks, c4 = 4 * (pos - ry * kChunks);
@@ -864,11 +659,11 @@ __device__ float lattice_tile(const DevGrid& g, int off, int nx, int ny, int til
     for (int hs = 0; hs < 2 * k; ++hs) {
         const bool last = hs >= 2 * k - 2;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
+        for (int j = 0; j < J; ++j) {
             const int ry = 1 + 2 * (warp + 8 * j) + rsub, y = y0 + ry;
             const int cx = 1 + 2 * pair + ((hs + x0 + 1 + y) & 1);   // the column of this colour in the pair
             const int x = x0 + cx;
-            const int edge = min(min(cx, ry), min(kLatSide - 1 - cx, kLatSide - 1 - ry));
+            const int edge = min(min(cx, ry), min(kLatSide - 1 - cx, ROWS - 1 - ry));
             // half-sweep hs only matters at distance > hs from the region edge: what it
             // would change nearer the edge cannot reach the interior by the last one
             if (edge <= hs || x < 0 || x >= nx || y < 0 || y >= ny) continue;
@@ -898,7 +693,7 @@ __device__ float lattice_tile(const DevGrid& g, int off, int nx, int ny, int til
         }
         __syncthreads();
     }
-    for (int q = threadIdx.x; q < T * T; q += blockDim.x) {
+    for (int q = threadIdx.x; q < T * TY; q += blockDim.x) {
         const int iy = q / T, ix = q - iy * T;
         const int x = x0 + H + ix, y = y0 + H + iy;
         if (x >= nx || y >= ny) continue;
@@ -917,6 +712,7 @@ __device__ float lattice_tile(const DevGrid& g, int off, int nx, int ny, int til
 // must stay zero in both buffers, which the start buffer is (zeroed by the FP64
 // pass) and which the first round of the inner solve (`first`) writes into the
 // other one; later rounds skip those tiles entirely.
+template <int ROWS>
 __device__ double lattice_round(const DevGrid& g, const float* dold, float* dnew, const float* r, float omega,
                                 int k, unsigned char* smem, const unsigned long long* latR, double target,
                                 bool first) {
@@ -934,10 +730,10 @@ __device__ double lattice_round(const DevGrid& g, const float* dold, float* dnew
         if (latR && __longlong_as_double((long long)latR[L]) <= target) {
             // converged lattice (uniform across the block: no barrier divergence)
             if (first) {
-                const int H = 2 * k, T = kLatSide - 2 * H, tiles_x = (nx + T - 1) / T;
-                const int tx0 = (tile % tiles_x) * T, ty0 = (tile / tiles_x) * T;
+                const int H = 2 * k, T = kLatSide - 2 * H, TY = ROWS - 2 * H, tiles_x = (nx + T - 1) / T;
+                const int tx0 = (tile % tiles_x) * T, ty0 = (tile / tiles_x) * TY;
                 const long long plane = (long long)nx * ny;
-                for (int q = threadIdx.x; q < T * T; q += blockDim.x) {
+                for (int q = threadIdx.x; q < T * TY; q += blockDim.x) {
                     const int x = tx0 + q % T, y = ty0 + q / T;
                     if (x >= nx || y >= ny) continue;
                     for (int l = 0; l < nl; ++l) dnew[off + l * plane + (long long)y * nx + x] = 0.f;
@@ -946,9 +742,9 @@ __device__ double lattice_round(const DevGrid& g, const float* dold, float* dnew
             continue;
         }
         float m;
-        if (nl == 1) m = lattice_tile<1>(g, off, nx, ny, tile, dold, dnew, r, omega, k, smem);
-        else if (nl == 2) m = lattice_tile<2>(g, off, nx, ny, tile, dold, dnew, r, omega, k, smem);
-        else m = lattice_tile<3>(g, off, nx, ny, tile, dold, dnew, r, omega, k, smem);
+        if (nl == 1) m = lattice_tile<1, ROWS>(g, off, nx, ny, tile, dold, dnew, r, omega, k, smem);
+        else if (nl == 2) m = lattice_tile<2, ROWS>(g, off, nx, ny, tile, dold, dnew, r, omega, k, smem);
+        else m = lattice_tile<3, ROWS>(g, off, nx, ny, tile, dold, dnew, r, omega, k, smem);
         mon = nanmaxf(mon, m);
     }
     return (double)mon;
@@ -1019,7 +815,11 @@ __device__ __forceinline__ double outer_slice(const DevGrid& g, const WarpCache*
         sc[j] = fabs(r[j]) * iD[j];
         mon = nanmax(mon, sc[j]);
     }
-    if (latR) lattice_max(g, latR, i0, sc, lacc);
+    if (latR) {
+        int Lid[4];
+        ldg4(g.node_lat + i0, Lid);
+        lattice_max(latR, Lid, sc, lacc);
+    }
     st4(st.r64 + i0, r);
     st4(v + i0, vv);
     if (lat) {
@@ -1043,7 +843,8 @@ __device__ __forceinline__ double outer_slice(const DevGrid& g, const WarpCache*
 
 // ---------------------------------------------------------------- the persistent kernel
 
-template <bool MIXED>
+// ROWS: region rows of the lattice inner solve (34, or 66 for tall regions; mixed precision only).
+template <bool MIXED, int ROWS>
 __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid g, DevState st, DevCtl ctl, RunParams rp) {
     using T = typename std::conditional<MIXED, float, double>::type;
     const unsigned nblocks = gridDim.x;
@@ -1177,22 +978,78 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
             for (int q = threadIdx.x; q < g.n_lats; q += blockDim.x) ctl.lat_R[(size_t)b * g.n_lats + q] = 0ull;
     };
 
-    // load currents of a step, one thread per source (slot S & 1 holds I(S h)); phase A of
-    // step S reads slot S & 1 (and slot (S - 1) & 1 in the three-level form)
-    auto eval_sources = [&](long long S) {
-        double* dst = st.isrc + (S & 1) * g.n_src;
+    // Load currents of step S into the per-node slot S & 1: (A_i^T I_s(S h))_i, the current
+    // drawn from node i by its loads (phase A of step S reads slot S & 1, and slot (S - 1) & 1
+    // in the incremental and three-level forms).  A node with one load is written by its
+    // source's thread, a node with several by a thread of its own that sums them in CSR order;
+    // nodes without loads keep 0.  Each node is always written by the same thread.
+    // With the load-aware warm start, word S & 3 of ctl.ld_flags records whether any node's
+    // load current changed between (S - 1) h and S h (compared with the other slot, written by
+    // the same thread), set at launch for the first two steps as in every post phase, so a run
+    // split over launches takes the same decisions.
+    const bool damp = rp.mode == kModeTransient && rp.warm_extrap && !rp.three_level &&
+                      rp.warm_theta_static < 1.0 && ctl.ld_flags != nullptr;
+    auto eval_sources = [&](long long S, bool flag) {
+        double* dst = st.inode + (S & 1) * (long long)g.n_pad;
+        const double* prev = st.inode + ((S - 1) & 1) * (long long)g.n_pad;
         const double tS = (double)S * rp.h;
-        for (int e = gtid; e < g.n_src; e += nthreads) dst[e] = pwl_eval(g, e, tS);
+        bool changed = false;
+        for (int e = gtid; e < g.n_src; e += nthreads) {
+            const int a = __ldg(g.src_na + e), b = __ldg(g.src_nb + e);
+            if (a < 0 && b < 0) continue;
+            const double I = pwl_eval(g, e, tS);
+            if (a >= 0) {
+                if (flag) changed |= I != prev[a];
+                dst[a] = I;
+            }
+            if (b >= 0) {
+                if (flag) changed |= -I != prev[b];
+                dst[b] = -I;
+            }
+        }
+        for (int k = gtid; k < g.n_multi; k += nthreads) {
+            const int i = __ldg(g.multi_node + k);
+            double sum = 0.0;
+            for (int q = __ldg(g.ld_ptr + i); q < __ldg(g.ld_ptr + i + 1); ++q) {
+                const int sid = __ldg(g.ld_idx + q);
+                const double I = pwl_eval(g, (sid > 0 ? sid : -sid) - 1, tS);
+                sum += sid > 0 ? I : -I;
+            }
+            if (flag) changed |= sum != prev[i];
+            dst[i] = sum;
+        }
+        if (flag && __any_sync(kFull, changed) && lane == 0) atomicOr(ctl.ld_flags + (S & 3), 1u);
     };
-    if (rp.mode == kModeTransient && g.n_src > 0 && rp.nsteps > 0) {
-        eval_sources(rp.step0 + 1);
-        if (rp.three_level || rp.inc_start) eval_sources(rp.step0);   // the load increment I(t) - I(t - h)
+    if (rp.mode == kModeTransient && (g.n_src > 0 || damp) && rp.nsteps > 0) {
+        const long long S0 = rp.step0;
+        if (damp) {                      // with no sources every interval stays static (0)
+            if (gtid == 0) {
+                ctl.ld_flags[S0 & 3] = 0u;
+                ctl.ld_flags[(S0 + 1) & 3] = 0u;
+                ctl.ld_flags[(S0 + 2) & 3] = 0u;
+            }
+            if (g.n_src > 0) eval_sources(S0 - 1, false);
+            if (!barrier(false, 0.0).ok) { publish(-1); return; }
+            if (g.n_src > 0) {
+                eval_sources(S0, true);
+                eval_sources(S0 + 1, true);
+            }
+        } else if (g.n_src > 0) {
+            if (rp.three_level || rp.inc_start) eval_sources(S0, false);   // I(t) - I(t - h)
+            eval_sources(S0 + 1, false);
+        }
         if (!barrier(false, 0.0).ok) { publish(-1); return; }
     }
 
     for (int sl = 0; sl < rp.nsteps; ++sl) {
         const long long sabs = rp.step0 + sl + 1;
         const bool extrap = rp.mode == kModeTransient && rp.warm_extrap && have_prev;
+        // extrapolation weight: damped once no load changed over the last two intervals
+        float th = 1.0f;
+        if (damp && extrap) {
+            const volatile unsigned* f = ctl.ld_flags;
+            if (f[sabs & 3] == 0u && f[(sabs - 1) & 3] == 0u) th = (float)rp.warm_theta_static;
+        }
         // Eq. 11 needs two levels; a step from a single level is an ordinary backward-Euler step
         const bool three = rp.mode == kModeTransient && rp.three_level && have_prev;
         // explicit form: the step start adds the increment to the previous final residual
@@ -1211,7 +1068,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
             for (int c = 0; c < g.ncol; ++c)
                 for (int tt = 0; tt < wc->cnt[c]; ++tt) {
                     const int s = wc->lo[c] + tt;
-                    md_slice(g, wc, warp_desc(g, *wc, c, tt, s), st, s, lane, vlp, vpp, extrap);
+                    md_slice(g, wc, warp_desc(g, *wc, c, tt, s), st, s, lane, vlp, vpp, extrap, th);
                 }
         }
         {
@@ -1220,8 +1077,17 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
             for (int c = 0; c < g.ncol; ++c)
                 for (int tt = 0; tt < wc->cnt[c]; ++tt) {
                     const int s = wc->lo[c] + tt;
-                    mon = nanmax(mon, phase_rhs<MIXED>(g, wc, warp_desc(g, *wc, c, tt, s), st, rp, s, lane, vL, vP,
-                                                       vF, extrap, three, inc, sabs, dsel, lb, lacc));
+                    const SliceDesc d = warp_desc(g, *wc, c, tt, s);
+                    if constexpr (MIXED) {   // keeps the undamped mixed path's registers as they were
+                        mon = nanmax(mon, th != 1.0f
+                                              ? phase_rhs<MIXED, true>(g, wc, d, st, rp, s, lane, vL, vP, vF, extrap,
+                                                                       three, inc, sabs, dsel, lb, lacc, th)
+                                              : phase_rhs<MIXED, false>(g, wc, d, st, rp, s, lane, vL, vP, vF, extrap,
+                                                                        three, inc, sabs, dsel, lb, lacc, 1.0f));
+                    } else {
+                        mon = nanmax(mon, phase_rhs<MIXED, true>(g, wc, d, st, rp, s, lane, vL, vP, vF, extrap, three,
+                                                                 inc, sabs, dsel, lb, lacc, th));
+                    }
                 }
             if (lb) lat_flush(lb, lacc);
         }
@@ -1249,7 +1115,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
                 // lattice rounds: lat_k exact block sweeps per device barrier
                 const float* dold = dbuf<float>(st, dsel);
                 float* dnew = dbuf<float>(st, dsel ^ 1);
-                const double m = lattice_round(g, dold, dnew, st.r32, (float)omega, rp.lat_k, s_dyn,
+                const double m = lattice_round<ROWS>(g, dold, dnew, st.r32, (float)omega, rp.lat_k, s_dyn,
                                                lat_buf(lat_par), target, inner == 0);
                 const BarrierResult be = barrier(true, m);
                 if (!be.ok) { publish(-1); return; }
@@ -1349,7 +1215,12 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
 
         // ---- post: inductor currents (Eq. 10), outputs, the next step's load currents
         lat_clear(lat_par ^ 1);           // the next step's phase A writes there
-        if (rp.mode == kModeTransient && sl + 1 < rp.nsteps) eval_sources(sabs + 1);
+        if (rp.mode == kModeTransient && sl + 1 < rp.nsteps) {
+            // the word of step sabs + 2 is next written by the following post phase; nobody
+            // reads it before then (step sabs + 1 reads the words of sabs + 1 and sabs)
+            if (damp && gtid == 0) ctl.ld_flags[(sabs + 2) & 3] = 0u;
+            eval_sources(sabs + 1, damp);
+        }
         const double* vnew = vbuf(st, vF);
         if (rp.mode == kModeTransient && !three) {
             for (int e = gtid; e < g.n_l; e += nthreads) {
@@ -1363,20 +1234,29 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
         unsigned long long bk = ~0ull;
         int ba = 0x7fffffff;
         double objsum = 0.0;
-        for (int i = gtid; i < g.n_pad; i += nthreads) {
-            if (rp.v_perm_all) rp.v_perm_all[(long long)sl * g.n_pad + i] = vnew[i];
-            const int o = __ldg(g.orig + i);
-            if (o < 0) continue;
-            const double x = vnew[i];
-            if (rp.obj_partials) {
-                const double sp = softplus_d(rp.obj_vref - x - rp.obj_margin);
-                objsum += sp * sp;
-            }
-            if (rp.v_all) rp.v_all[(long long)sl * g.n_real + o] = x;
-            if (rp.solve_out) rp.solve_out[o] = x;
-            if (rp.vmin) {
-                const unsigned long long k = order_key(x);
-                if (k < bk || (k == bk && o < ba)) { bk = k; ba = o; }
+        // four consecutive nodes per thread and iteration (n_pad is a multiple of kSlice):
+        // 128-bit loads, a quarter of the dependent iterations
+        for (int i4 = 4 * gtid; i4 < g.n_pad; i4 += 4 * nthreads) {
+            double x4[4];
+            int o4[4];
+            ld4(vnew + i4, x4);
+            ldg4(g.orig + i4, o4);
+            if (rp.v_perm_all) st4(rp.v_perm_all + (long long)sl * g.n_pad + i4, x4);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int o = o4[j];
+                if (o < 0) continue;
+                const double x = x4[j];
+                if (rp.obj_partials) {
+                    const double sp = softplus_d(rp.obj_vref - x - rp.obj_margin);
+                    objsum += sp * sp;
+                }
+                if (rp.v_all) rp.v_all[(long long)sl * g.n_real + o] = x;
+                if (rp.solve_out) rp.solve_out[o] = x;
+                if (rp.vmin) {
+                    const unsigned long long k = order_key(x);
+                    if (k < bk || (k == bk && o < ba)) { bk = k; ba = o; }
+                }
             }
         }
         if (rp.probe_v)
@@ -1676,23 +1556,26 @@ __global__ void __launch_bounds__(256) adjoint_lgrad_kernel(DevGrid g, const dou
 
 // ---------------------------------------------------------------- host-side launch helpers
 
-// Dynamic shared memory of the persistent kernel: the TMA stages of the FP32 sweep, or
-// (same bytes) the region of the lattice inner solve.
-static size_t persistent_smem(bool mixed) {
-    const int stages = kWarpsPerBlock * tma_warp_bytes(sizeof(float));
-    return mixed ? (size_t)(stages > lattice_smem_bytes() ? stages : lattice_smem_bytes()) : 0;
+size_t persistent_smem_bytes(bool mixed, int rows, int nl) {
+    const size_t stages = (size_t)kWarpsPerBlock * tma_warp_bytes(sizeof(float));
+    const size_t region = nl > 0 ? lattice_region_bytes(rows, nl) : 0;
+    return mixed ? std::max(stages, region) : 0;
+}
+
+static const void* persistent_fn(bool mixed, int rows) {
+    return !mixed ? (const void*)persistent_kernel<false, 34>
+         : rows == 66 ? (const void*)persistent_kernel<true, 66> : (const void*)persistent_kernel<true, 34>;
 }
 
 cudaError_t launch_persistent(bool mixed, const DevGrid& g, const DevState& st, const DevCtl& ctl,
-                              const RunParams& rp, int blocks, int threads, cudaStream_t stream) {
+                              const RunParams& rp, int blocks, int threads, size_t smem, cudaStream_t stream) {
     void* args[] = {(void*)&g, (void*)&st, (void*)&ctl, (void*)&rp};
-    const void* fn = mixed ? (const void*)persistent_kernel<true> : (const void*)persistent_kernel<false>;
-    return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, persistent_smem(mixed), stream);
+    return cudaLaunchCooperativeKernel(persistent_fn(mixed, g.lat_rows), dim3(blocks), dim3(threads), args, smem,
+                                       stream);
 }
 
-cudaError_t persistent_occupancy(bool mixed, int threads, int* blocks_per_sm) {
-    const void* fn = mixed ? (const void*)persistent_kernel<true> : (const void*)persistent_kernel<false>;
-    const size_t smem = persistent_smem(mixed);
+cudaError_t persistent_occupancy(bool mixed, int rows, int threads, size_t smem, int* blocks_per_sm) {
+    const void* fn = persistent_fn(mixed, rows);
     if (smem > 0) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

@@ -21,14 +21,18 @@
 
 namespace {
 
-// Maximum scratch shared by all calls: 32 MiB.  Every GPU that loads the
-// library holds this array until the process exits.
+// Maximum scratch shared by all calls: 32 MiB.  CUDA loads this file's module,
+// and with it reserves the array on a device, at the first lookup of its address
+// on that device, which pg_create_grid makes; from then on the device holds it
+// until the process exits.
 constexpr size_t kScratchBytes = size_t(32) << 20;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_addr_mu;
 void* g_addr[kMaxDevices] = {nullptr};
+bool g_tried[kMaxDevices] = {false};
+std::string g_bind_error[kMaxDevices];
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -63,6 +67,21 @@ pg_status fail(pg_status s, const std::string& m) {
 
 }  // namespace
 
+void pg::noalloc_bind_device(int dev) {
+    if (dev < 0 || dev >= kMaxDevices) return;
+    std::lock_guard<std::mutex> lk(g_addr_mu);
+    if (g_tried[dev]) return;
+    g_tried[dev] = true;
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+        cudaGetLastError();            // the grid does not depend on this array
+        g_bind_error[dev] = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+        return;
+    }
+    g_addr[dev] = p;
+}
+
 extern "C" pg_status pg_solve_noalloc(pg_grid* g, double h, const double* b, double* x, double tol,
                                       pg_run_stats* stats) {
     if (!g || !b || !x || !(tol > 0.0)) return fail(PG_ERR_INVALID_ARG, "null argument or tol <= 0");
@@ -79,20 +98,16 @@ extern "C" pg_status pg_solve_noalloc(pg_grid* g, double h, const double* b, dou
     const double target = tol / g->kappa - 1e-13;
     if (!(target > 0.0)) return fail(PG_ERR_INVALID_ARG, "tol below the rounding floor");
 
-    // Set-up, once per device, with that device current: the device address of the array.
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail(PG_ERR_CUDA, cudaGetErrorString(e));
+    // The array's device address was looked up when the grid was created (with the grid's
+    // device current); this call only reads it, so it never loads a module or reserves memory.
+    const int dev = g->device;
     if (dev < 0 || dev >= kMaxDevices) return fail(PG_ERR_CUDA, "device ordinal out of range");
     unsigned char* base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_addr_mu);
-        if (!g_addr[dev]) {
-            void* p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess) return fail(PG_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            g_addr[dev] = p;
-        }
+        if (!g_addr[dev])
+            return fail(PG_ERR_CUDA, "the fixed scratch array could not be set up when the grid was created" +
+                                         (g_bind_error[dev].empty() ? std::string() : ": " + g_bind_error[dev]));
         base = static_cast<unsigned char*>(g_addr[dev]);
     }
 
@@ -122,6 +137,7 @@ extern "C" pg_status pg_solve_noalloc(pg_grid* g, double h, const double* b, dou
 
     // The array keeps the previous call's contents: clear what must start at zero.
     cudaStream_t s = g->stream;
+    cudaError_t e = cudaSuccess;
     if ((e = cudaMemsetAsync(base + L.ctl, 0, 3 * sizeof(uint32_t), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(base + L.red, 0, pg::kRedSlots * sizeof(unsigned long long), s)) != cudaSuccess)
         return fail(PG_ERR_CUDA, cudaGetErrorString(e));
@@ -139,7 +155,7 @@ extern "C" pg_status pg_solve_noalloc(pg_grid* g, double h, const double* b, dou
     rp.solve_out = x;
     rp.debug_flags = 0;
     if ((e = cudaEventRecord(g->ev0, s)) != cudaSuccess ||
-        (e = pg::launch_persistent(g->mixed, g->dg, st, c, rp, g->blocks, g->threads, s)) != cudaSuccess ||
+        (e = pg::launch_persistent(g->mixed, g->dg, st, c, rp, g->blocks, g->threads, g->smem, s)) != cudaSuccess ||
         (e = cudaEventRecord(g->ev1, s)) != cudaSuccess)
         return fail(PG_ERR_CUDA, cudaGetErrorString(e));
     int32_t err = 0;
@@ -150,24 +166,7 @@ extern "C" pg_status pg_solve_noalloc(pg_grid* g, double h, const double* b, dou
         return fail(PG_ERR_CUDA, cudaGetErrorString(e));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, g->ev0, g->ev1);
-    if (stats) {
-        *stats = pg_run_stats{};
-        stats->steps_done = (int64_t)hs[pg::kStatSteps];
-        stats->total_sweeps = (int64_t)hs[pg::kStatSweeps];
-        stats->max_sweeps_step = (int32_t)hs[pg::kStatMaxSweeps];
-        stats->total_outer = (int64_t)hs[pg::kStatOuter];
-        stats->max_outer_step = (int32_t)hs[pg::kStatMaxOuter];
-        stats->max_step_bound = g->kappa * (hs[pg::kStatMaxBound] + 1e-13);
-        stats->err_bound = stats->max_step_bound;
-        stats->failed_step = (int64_t)hs[pg::kStatFailedStep];
-        stats->omega = g->omega;
-        stats->rho_jacobi = g->rho;
-        stats->kappa = g->kappa;
-        stats->q = g->q;
-        stats->step_tol = tol;
-        stats->device_ms = ms;
-        stats->kacc = 1.0;
-    }
+    pg::fill_run_stats(g, hs, ms, stats, 0.0);     // the same report as pg_solve
     if (err == PG_ERR_TIMEOUT) return fail(PG_ERR_TIMEOUT, "device barrier timed out");
     if (err == PG_ERR_NOT_CONVERGED) return fail(PG_ERR_NOT_CONVERGED, "relaxation did not converge");
     if (err != 0) return fail(PG_ERR_CUDA, "device error");

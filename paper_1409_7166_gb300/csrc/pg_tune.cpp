@@ -3,7 +3,9 @@
 // The paper fixes neither the relaxation factor nor the parallel schedule
 // (Section IV leaves omega and the sweep order open), and the best choice
 // depends on the grid: its size and layer count decide whether the column-block
-// inner solve pays for its ghost zones, how far the FP32 inner solve should
+// inner solve pays for its ghost zones and which region shape (34 x 34 columns,
+// or 34 x 66 at one block per SM) does, which colouring the point sweeps take
+// (red-black, or four colours on a lattice), how far the FP32 inner solve should
 // reduce the defect before the next FP64 residual pass, and whether omega a
 // little above or below the automatic value (Young's, taken 1 % high) does
 // better on this grid's transient.  Every candidate runs under the same certified stopping rule, so
@@ -32,6 +34,20 @@ extern "C" pg_status pg_autotune(const pg_netlist* nl, const pg_options* base, d
     const bool mixed = b0.precision == PG_PREC_MIXED;
     const bool lattice = mixed && (nl->n_lat > 0 || (nl->lat_nx > 0 && nl->lat_ny > 0 && nl->lat_nl > 0));
     std::vector<int32_t> ks = lattice ? std::vector<int32_t>{-1, 1, 2, 3} : std::vector<int32_t>{b0.lattice_sweeps};
+    const bool lat_net = nl->n_lat > 0 || (nl->lat_nx > 0 && nl->lat_ny > 0 && nl->lat_nl > 0);
+    // per inner-solve form, the layout candidates: region rows for the lattice solve,
+    // colourings for the point sweeps (four colours only where the netlist is a lattice)
+    auto layouts = [&](int32_t k) {
+        std::vector<std::pair<int32_t, int32_t>> v;    // (tile_rows, colouring)
+        if (lattice && k > 0) {
+            v.push_back({34, b0.colouring});
+            v.push_back({66, b0.colouring});
+        } else {
+            v.push_back({b0.tile_rows, PG_COLOUR_AUTO});
+            if (lat_net) v.push_back({b0.tile_rows, PG_COLOUR_FOUR});
+        }
+        return v;
+    };
     const std::vector<int32_t> bps = {0, 1};
     std::vector<double> reds;
     if (mixed) reds.assign(std::begin(kInnerReductions), std::end(kInnerReductions));
@@ -42,10 +58,13 @@ extern "C" pg_status pg_autotune(const pg_netlist* nl, const pg_options* base, d
     pg_options win = b0;
     pg_status last = PG_OK;
     for (int32_t k : ks) {
+      for (const auto& lay : layouts(k)) {
         for (int32_t bp : bps) {
             pg_options o = b0;
             o.lattice_sweeps = k;
             o.blocks_per_sm = bp;
+            o.tile_rows = lay.first;
+            o.colouring = lay.second;
             pg_grid* g = nullptr;
             pg_status s = pg_create_grid(nl, &o, &g);
             if (s) { last = s; continue; }
@@ -88,6 +107,7 @@ extern "C" pg_status pg_autotune(const pg_netlist* nl, const pg_options* base, d
             g->omega = w0;
             pg_destroy(g);
         }
+      }
     }
     // damped Jacobi (undamped, omega = 1): allowed 4x the winner's sweeps per step, so a
     // candidate that cannot compete fails fast instead of running to the sweep cap

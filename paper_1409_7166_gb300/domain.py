@@ -18,7 +18,10 @@ residual estimate.
 This module is the host side of that schedule: the partition, the halo
 exchange (torch.distributed point-to-point; gloo on the CPU, NCCL for device
 tensors), and the sweep loop.  The half-sweep over a block is supplied by the
-caller.
+caller; on the GPU it is the library's ``pg_block_half_sweep``.  Several blocks
+of one grid can also be held in one process (``split_blocks``,
+``LocalHaloExchange``, ``red_black_sor_blocks``), their halos refreshed by
+device copies.
 """
 from __future__ import annotations
 
@@ -130,3 +133,76 @@ def gather_rows(x: torch.Tensor, halo: HaloExchange, root: int = 0) -> Optional[
     if halo.rank != root:
         return None
     return torch.cat(parts, dim=1)
+
+
+# ---------------------------------------------------------------------------
+# several row blocks of one grid in one process (device tensors)
+# ---------------------------------------------------------------------------
+
+def split_blocks(w_e: torch.Tensor, w_n: torch.Tensor, w_u: torch.Tensor, inv_d: torch.Tensor,
+                 rhs: torch.Tensor, world: int) -> List[dict]:
+    """Cut full-grid coefficient arrays, each ``[nl, ny, nx]``, into ``world`` row blocks.
+
+    ``w_e``: conductance (x, y, l)-(x + 1, y, l), zero on the last column; ``w_n``:
+    (x, y, l)-(x, y + 1, l), zero on the last row; ``w_u``: (x, y, l)-(x, y, l + 1), zero
+    on the top layer; ``inv_d``: 1 / D (Eq. 14); ``rhs``: the right-hand side.  Each block
+    gets the layout of ``pg_row_block``: its rows of every layer, the north couplings of
+    its rows plus the one from the row below it (``[nl, rows + 1, nx]``), and a zero
+    iterate with one halo row on each side (``[nl, rows + 2, nx]``)."""
+    nl, ny, nx = w_e.shape
+    out = []
+    for (y0, y1) in row_blocks(ny, world):
+        rows = y1 - y0
+        wn = torch.zeros((nl, rows + 1, nx), dtype=w_n.dtype, device=w_n.device)
+        if y0 > 0:
+            wn[:, 0] = w_n[:, y0 - 1]
+        wn[:, 1:] = w_n[:, y0:y1]
+        out.append(dict(nx=nx, rows=rows, nl=nl, y0=y0,
+                        w_e=w_e[:, y0:y1].contiguous(), w_n=wn, w_u=w_u[:, y0:y1].contiguous(),
+                        inv_d=inv_d[:, y0:y1].contiguous(), rhs=rhs[:, y0:y1].contiguous(),
+                        x=torch.zeros((nl, rows + 2, nx), dtype=rhs.dtype, device=rhs.device)))
+    return out
+
+
+class LocalHaloExchange:
+    """The halo exchange between row blocks held in one process: after a half-sweep,
+    each block's first and last rows are copied into the halos of the blocks below
+    and above it (device-to-device copies on the current stream)."""
+
+    def __init__(self, blocks: List[dict]):
+        self.blocks = blocks
+
+    def exchange(self) -> None:
+        for lo, hi in zip(self.blocks[:-1], self.blocks[1:]):
+            lo["x"][:, lo["rows"] + 1].copy_(hi["x"][:, 1])
+            hi["x"][:, 0].copy_(lo["x"][:, lo["rows"]])
+
+
+def red_black_sor_blocks(blocks: List[dict], half_sweep: Callable[[dict, int, torch.Tensor], None],
+                         max_sweeps: int, tol: float, check_every: int = 4) -> Tuple[int, float]:
+    """Red-black SOR over every block of one process, in the schedule of
+    :func:`red_black_sor`: per colour, every block's half-sweep, then the halo exchange;
+    every ``check_every`` sweeps the largest update of the last sweep over all blocks
+    decides the stop.  ``half_sweep(block, colour, max_update)`` max-merges its largest
+    update into the device scalar ``max_update``."""
+    halo = LocalHaloExchange(blocks)
+    dev = blocks[0]["x"].device
+    mx = torch.zeros(1, dtype=torch.float64, device=dev)
+    est = float("inf")
+    halo.exchange()
+    for k in range(1, max_sweeps + 1):
+        mx.zero_()
+        for colour in (0, 1):
+            for blk in blocks:
+                half_sweep(blk, colour, mx)
+            halo.exchange()
+        if k % check_every == 0 or k == max_sweeps:
+            est = float(mx.item())
+            if est <= tol:
+                return k, est
+    return max_sweeps, est
+
+
+def gather_blocks(blocks: List[dict]) -> torch.Tensor:
+    """The full ``[nl, ny, nx]`` field from the blocks' own rows."""
+    return torch.cat([b["x"][:, 1:b["rows"] + 1] for b in blocks], dim=1)

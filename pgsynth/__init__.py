@@ -308,6 +308,29 @@ def config3_parts(seed: int = 3, n_grids: int = 256, side_lo: int = 64, side_hi:
     return parts
 
 
+def config3_part(k: int, seed: int = 3, n_grids: int = 256, side_lo: int = 64, side_hi: int = 512):
+    """Grid ``k`` of :func:`config3` alone, as ``(node offset in the batch, netlist)``:
+    the same draws as :func:`config3_parts` without generating the other grids."""
+    root = np.random.SeedSequence(seed)
+    top = np.random.Generator(np.random.PCG64(root))
+    sides = top.integers(side_lo, side_hi + 1, size=n_grids)
+    layers = top.integers(1, 3, size=n_grids)
+    children = root.spawn(n_grids)
+    off = int(np.sum(sides[:k].astype(np.int64) ** 2 * layers[:k]))
+    spec = LatticeSpec(nx=int(sides[k]), ny=int(sides[k]), nl=int(layers[k]), g_layer=("uniform", 0.5, 2.0),
+                       g_via=("uniform", 5.0, 20.0), pad_pitch=10,
+                       cap_layers=(0,), cap=("uniform", 10e-15, 100e-15), load_frac=0.2)
+    return off, lattice_netlist(spec, np.random.Generator(np.random.PCG64(children[k])))
+
+
+def config3_shapes(seed: int = 3, n_grids: int = 256, side_lo: int = 64, side_hi: int = 512):
+    """(side, layers) of every grid of :func:`config3`, without generating them."""
+    top = np.random.Generator(np.random.PCG64(np.random.SeedSequence(seed)))
+    sides = top.integers(side_lo, side_hi + 1, size=n_grids)
+    layers = top.integers(1, 3, size=n_grids)
+    return [(int(a), int(b)) for a, b in zip(sides, layers)]
+
+
 def config3(seed: int = 3, n_grids: int = 256, side_lo: int = 64, side_hi: int = 512) -> Netlist:
     """256 independent RC grids of uneven size (side U{64..512}, 1-2 layers),
     each drawn like config 0 from its own child seed; 2-layer grids get vias

@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol(B):
 
 def test_default_options_and_status_names(B):
     o = B.pg_default_options()
-    assert (o.precision, o.tol, o.max_sweeps, o.warm_start, o.threads_per_block) == (0, 1e-6, 20000, 1, 256)
+    assert (o.precision, o.tol, o.max_sweeps, o.warm_start, o.threads_per_block) == (0, 1e-6, 20000, -1, 256)
     for code, name in B.STATUS.items():
         assert B.lib().pg_status_str(code).decode() == name
 
@@ -116,3 +116,28 @@ def test_degenerate_netlists(B):
     assert _create_status(B, no_source) == "PG_ERR_FLOATING_NODE"
     cap_only = make_netlist(1, [1.0], C=[(0, GROUND, 1e-15)])
     assert _create_status(B, cap_only) == "PG_ERR_FLOATING_NODE"
+
+
+def test_warm_start_option_validation():
+    """warm_start takes -1 (automatic), 0 (previous value), 1 (linear extrapolation) or 2
+    (load-aware damped extrapolation); anything else is rejected before any device work."""
+    from paper_1409_7166_gb300 import binding as B
+    net = pgsynth.config0(nx=6, ny=5)
+    for bad in (-2, 3):
+        with pytest.raises(B.PGError) as ei:
+            B.pg_create_grid(net, B.pg_default_options(warm_start=bad))
+        assert ei.value.status == B.PG_ERR_INVALID_ARG
+
+
+
+def test_colouring_and_tile_rows_validation():
+    """colouring takes PG_COLOUR_AUTO, _RED_BLACK or _FOUR and tile_rows 0, 34 or 66;
+    anything else is rejected before any device work."""
+    from paper_1409_7166_gb300 import binding as B
+    net = pgsynth.config0(nx=6, ny=5)
+    for bad in (dict(colouring=-1), dict(colouring=3), dict(tile_rows=33), dict(tile_rows=-34)):
+        with pytest.raises(B.PGError) as ei:
+            B.pg_create_grid(net, B.pg_default_options(**bad))
+        assert ei.value.status == B.PG_ERR_INVALID_ARG
+    o = B.pg_default_options()
+    assert (o.colouring, o.tile_rows) == (B.PG_COLOUR_AUTO, 0)

@@ -64,3 +64,30 @@ def test_algorithmic_byte_model():
     assert one == pytest.approx((56 + 8 + 8 * mn) * n + 56 * n_src + 8 * n)
     sixteen = ab({"total_sweeps": 0, "total_outer": 0}, n, mn, n_src, True, 16)
     assert sixteen == pytest.approx((56 + 8 + 8 * mn) * n + 15 * 72 * n + 16 * (56 * n_src + 8 * n))
+
+
+def test_survey_byte_model():
+    """The roofline's byte model, term by term: 16 + 4 m/n per FP32 node-sweep (32 + 8 m/n
+    in FP64), 24 + 8 m/n per node per FP64 residual pass, 24 B per node plus 36 B per
+    source per step.  The column-block form counts as an FP32 sweep."""
+    n, mn, n_src = 1000, 2.5, 30
+    sb = bench.survey_bytes
+    z = {"total_sweeps": 0, "total_outer": 0}
+    assert sb(z, n, mn, n_src, True, 0) == 0.0
+    assert sb({"total_sweeps": 1, "total_outer": 0}, n, mn, n_src, True, 0) == (16 + 4 * mn) * n
+    assert sb({"total_sweeps": 1, "total_outer": 0, "lattice_sweeps": 3}, n, mn, n_src, True, 0) == (16 + 4 * mn) * n
+    assert sb({"total_sweeps": 1, "total_outer": 0}, n, mn, n_src, False, 0) == (32 + 8 * mn) * n
+    assert sb({"total_sweeps": 0, "total_outer": 1}, n, mn, n_src, True, 0) == (24 + 8 * mn) * n
+    assert sb(z, n, mn, n_src, True, 7) == 7 * (24 * n + 36 * n_src)
+
+
+def test_config3_sample_choice():
+    """The per-config bench compares three grids of the batch with the oracle: the smallest
+    single-layer grid, the smallest two-layer grid and the single-layer grid nearest 256."""
+    import pgsynth
+    shapes = pgsynth.config3_shapes()
+    pick = bench._c3_sample(shapes)
+    assert len(pick) == 3
+    one = [s for s, l in shapes if l == 1]
+    assert min(one) in [shapes[k][0] for k in pick if shapes[k][1] == 1]
+    assert any(shapes[k][1] == 2 and shapes[k][0] == min(s for s, l in shapes if l == 2) for k in pick)

@@ -50,6 +50,9 @@ def test_autotune_choice_is_exact(B, case):
     assert ms > 0.0 and opts["precision"] == prec
     assert opts["blocks_per_sm"] in (0, 1)
     assert opts["jacobi"] in (0, 1)
+    assert opts["tile_rows"] in (0, 34, 66) and opts["colouring"] in (0, 2)
+    if opts["colouring"] == 2:
+        assert opts["lattice_sweeps"] <= 0            # a point-sweep order
     if opts["jacobi"]:
         assert opts["lattice_sweeps"] == -1
     elif prec == 1:

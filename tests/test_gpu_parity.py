@@ -298,3 +298,82 @@ def test_lattices_smaller_than_a_tile(B):
     V, _, _, _, st = run_gpu(B, net, tiny.meta["h"], 20, 1, lattice_sweeps=2)
     assert st.lattice_sweeps == 2
     assert np.max(np.abs(V - Vo[1:])) <= TOL_V
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_load_aware_warm_start(B, precision):
+    """warm_start = 2 damps the extrapolation once the loads have been constant for two
+    steps.  It only moves the starting point, so parity holds.  The 3-layer recipe's loads
+    all finish within 1.2 ns (240 steps of 5 ps), so 300 steps include a quiet stretch.
+    There the damped start saves sweeps on the mixed-precision lattice path and costs a
+    few per cent on this small grid's FP64 point path; the sweep ratio is printed and
+    held within 5 %.  A run split over launches takes the same decisions (they depend on
+    absolute time only)."""
+    net = pgsynth.config1(nx=40, ny=30)
+    h, S = net.meta["h"], 300
+    err2, st2 = check_against_oracle(B, net, h, S, precision, warm_start=2)
+    _, st1 = check_against_oracle(B, net, h, S, precision, warm_start=1)
+    print(f"sweeps: warm_start 1 {st1.total_sweeps}, warm_start 2 {st2.total_sweeps} "
+          f"(ratio {st2.total_sweeps / st1.total_sweeps:.4f})")
+    assert st2.total_sweeps <= 1.05 * st1.total_sweeps
+    with B.Grid(net, precision=precision, warm_start=2) as g:
+        B.pg_set_stream(g.handle, torch.cuda.current_stream().cuda_stream)
+        one = torch.empty(S, dtype=torch.float64, device="cuda")
+        B.pg_transient(g.handle, h, S, vmin=one)
+        B.pg_reset(g.handle)
+        parts = []
+        for a in range(0, S, 70):
+            k = min(70, S - a)
+            v = torch.empty(k, dtype=torch.float64, device="cuda")
+            B.pg_transient(g.handle, h, k, vmin=v)
+            parts.append(v)
+        torch.cuda.synchronize()
+        assert torch.equal(torch.cat(parts), one)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("recipe", ["config0_37x29", "config1_33x27x3", "config2_24x19x2"])
+def test_four_colour_order(B, recipe, precision):
+    """PG_COLOUR_FOUR sweeps the neighbour-list path in four colours ((x + l) mod 2 +
+    2 (y mod 2)), a Gauss-Seidel order other than red-black (Section IV-A leaves the order
+    open; Theorem 1 covers any order).  The fixed point is the same: parity with the oracle
+    holds on odd-sided RC, 3-layer and RLC recipes, and the grid reports four colours."""
+    net = {"config0_37x29": lambda: pgsynth.config0(nx=37, ny=29),
+           "config1_33x27x3": lambda: pgsynth.config1(nx=33, ny=27),
+           "config2_24x19x2": lambda: pgsynth.config2(nx=24, ny=19)}[recipe]()
+    with B.Grid(net, precision=precision, colouring=B.PG_COLOUR_FOUR, lattice_sweeps=-1) as g:
+        assert g.info["n_colours"] == 4
+    _, st4 = check_against_oracle(B, net, net.meta["h"], 40, precision, colouring=B.PG_COLOUR_FOUR,
+                                  lattice_sweeps=-1)
+    _, st2 = check_against_oracle(B, net, net.meta["h"], 40, precision, lattice_sweeps=-1)
+    print(f"{recipe} precision {precision}: sweeps four-colour {st4.total_sweeps}, red-black {st2.total_sweeps}")
+
+
+@pytest.mark.parametrize("recipe,k", [("config1_97x141x3", 3), ("config2_70x75x2", 2), ("config0_83x150", 3)])
+def test_tall_lattice_regions(B, recipe, k):
+    """tile_rows = 66: the lattice inner solve on 34-column by 66-row regions (one block per
+    SM for 2-3 layers).  The same iteration as 34-row regions (the host replay shows the
+    interior equals k global block sweeps for both), so parity with the oracle holds on
+    ragged 3-layer, RLC and single-layer recipes."""
+    net = {"config1_97x141x3": lambda: pgsynth.config1(nx=97, ny=141),
+           "config2_70x75x2": lambda: pgsynth.config2(nx=70, ny=75),
+           "config0_83x150": lambda: pgsynth.config0(nx=83, ny=150)}[recipe]()
+    _, st = check_against_oracle(B, net, net.meta["h"], 30, 1, tile_rows=66, lattice_sweeps=k)
+    assert st.lattice_sweeps == k
+    _, st34 = check_against_oracle(B, net, net.meta["h"], 30, 1, tile_rows=34, lattice_sweeps=k)
+    print(f"{recipe}: sweeps 66-row {st.total_sweeps} ({st.device_ms:.2f} ms), 34-row {st34.total_sweeps} "
+          f"({st34.device_ms:.2f} ms)")
+
+
+def test_tall_regions_on_a_batch(B):
+    """A batch of uneven lattices (1-2 layers, odd offsets: 4-byte staging for most) on
+    66-row regions: every grid of the batch against its own oracle solve."""
+    net = pgsynth.config3(n_grids=6, side_lo=20, side_hi=90)
+    parts = pgsynth.config3_parts(n_grids=6, side_lo=20, side_hi=90)
+    h, S = net.meta["h"], 25
+    V, _, _, _, st = run_gpu(B, net, h, S, 1, tile_rows=66)
+    assert st.failed_step == -1 and st.lattice_sweeps > 0
+    for off, part in parts:
+        Vo, _ = transient.transient(part, h, S)
+        err = np.max(np.abs(V[:, off:off + part.n_nodes] - Vo[1:]))
+        assert err <= TOL_V, f"grid at {off} {part.lattice}: {err:.3e} V"

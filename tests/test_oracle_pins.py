@@ -517,6 +517,19 @@ def _adjoint_case():
     return net
 
 
+def test_generator_config3_single_part_matches_batch():
+    """config3_part(k) draws grid k alone, with the values and offset it has in the batch;
+    config3_shapes lists every grid's side and layer count without drawing them."""
+    parts = pgsynth.config3_parts(n_grids=9, side_lo=16, side_hi=30)
+    shapes = pgsynth.config3_shapes(n_grids=9, side_lo=16, side_hi=30)
+    for k in (0, 4, 8):
+        off, p = pgsynth.config3_part(k, n_grids=9, side_lo=16, side_hi=30)
+        o2, p2 = parts[k]
+        assert off == o2 and p.lattice == p2.lattice and shapes[k] == (p.lattice[0], p.lattice[2])
+        for a in ("r_a", "r_b", "r_g", "c_val", "i_a", "i_t", "i_v"):
+            np.testing.assert_array_equal(getattr(p, a), getattr(p2, a))
+
+
 def test_adjoint_matches_central_differences():
     """The oracle's discrete adjoint against central finite differences of the
     oracle's own forward objective (exact direct solves), for resistors (segments,

@@ -3,13 +3,13 @@
 The FP32 lattice solve (block red-black SOR over (x, y) columns, Eq. 16-17 with
 the via couplings inside the column blocks) runs k exact sweeps per device
 barrier.  Each tile does this:
-- it loads a 34 x 34-column region;
+- it loads a region of 34 columns by 34 or 66 rows;
 - it applies 2k half-sweeps;
-- it stores its (34 - 4k)^2 interior.
+- it stores its (34 - 4k) x (rows - 4k) interior.
 Half-sweep hs updates only the columns farther than hs from the region edge.
-The columns are assigned as in the kernel: each of the 256 threads has 16
-column pairs and two rows per half-sweep, and the half-warps take adjacent
-rows.
+The columns are assigned as in the kernel: each half-warp row has 16 column
+pairs, every thread takes one pair in two rows (34-row regions) or four rows
+(66-row regions) per half-sweep, and the half-warps take adjacent rows.
 
 Rows are staged from the 16-byte boundary at or below the region's first
 column.  A batch of lattices is one flat tile range: each tile's lattice comes
@@ -29,7 +29,7 @@ This model replays that index arithmetic in FP64 and checks four things:
 import numpy as np
 import pytest
 
-SIDE = 34          # region side in columns
+SIDE = 34          # region width in columns
 W = 36             # shared-memory row stride (the region plus a lead of 0 or 2 columns)
 THREADS = 256
 
@@ -45,22 +45,23 @@ def _column_update(f, m, p, u, NL):
     return x
 
 
-def tile_apply(off, nx, ny, NL, k, tile, srcs, dnew, stored, omega):
+def tile_apply(off, nx, ny, NL, k, tile, srcs, dnew, stored, omega, rows=SIDE):
     """One tile of the lattice at global offset ``off``; ``srcs`` are the flat global
     arrays (d, r, wE, wN, wU, m, 1/pivot) and ``dnew`` the flat output."""
     H = 2 * k
-    T = SIDE - 2 * H
+    T, TY = SIDE - 2 * H, rows - 2 * H
+    J = (rows - 2) // 16
     tiles_x = -(-nx // T)
     plane = nx * ny
-    x0, y0 = (tile % tiles_x) * T - H, (tile // tiles_x) * T - H
+    x0, y0 = (tile % tiles_x) * T - H, (tile // tiles_x) * TY - H
     assert x0 % 2 == 0
     lead = x0 & 3
     xa = x0 - lead
     assert xa % 4 == 0 and lead in (0, 2)
-    sm = np.zeros((7, NL, SIDE * W))
+    sm = np.zeros((7, NL, rows * W))
     if nx % 4 == 0 and off % 4 == 0:
         chunks = W // 4
-        pieces = SIDE * chunks
+        pieces = rows * chunks
         for q in range(pieces * 7):
             a, pos = divmod(q, pieces)
             ry, c4 = pos // chunks, 4 * (pos % chunks)
@@ -68,14 +69,14 @@ def tile_apply(off, nx, ny, NL, k, tile, srcs, dnew, stored, omega):
             inside = 0 <= yy < ny and 0 <= xx < nx
             assert inside == (0 <= yy < ny and 0 <= xx + 3 < nx)
             sa = ry * W + c4
-            assert 0 <= sa and sa + 3 < SIDE * W
+            assert 0 <= sa and sa + 3 < rows * W
             if inside:
                 for l in range(NL):
                     o = off + yy * nx + xx + l * plane
                     assert o % 4 == 0                       # a 16-byte aligned source
                     sm[a, l, sa:sa + 4] = srcs[a][o:o + 4]
     else:
-        for q in range(SIDE * W):
+        for q in range(rows * W):
             ry, c = divmod(q, W)
             xx, yy = xa + c, y0 + ry
             if 0 <= yy < ny and 0 <= xx < nx:
@@ -88,17 +89,17 @@ def tile_apply(off, nx, ny, NL, k, tile, srcs, dnew, stored, omega):
         for t in range(THREADS):
             lane, warp = t & 31, t >> 5
             pair, rsub = lane & 15, lane >> 4
-            for j in range(2):
+            for j in range(J):
                 ry = 1 + 2 * (warp + 8 * j) + rsub
                 y = y0 + ry
                 cx = 1 + 2 * pair + ((hs + x0 + 1 + y) & 1)
                 x = x0 + cx
                 assert (x + y) % 2 == hs % 2               # this half-sweep's colour
-                edge = min(cx, ry, SIDE - 1 - cx, SIDE - 1 - ry)
+                edge = min(cx, ry, SIDE - 1 - cx, rows - 1 - ry)
                 if edge <= hs or not (0 <= x < nx and 0 <= y < ny):
                     continue
                 a0 = ry * W + cx + lead
-                assert 1 <= cx <= SIDE - 2 and 1 <= ry <= SIDE - 2 and cx + lead + 1 < W
+                assert 1 <= cx <= SIDE - 2 and 1 <= ry <= rows - 2 and cx + lead + 1 < W
                 assert a0 not in touched
                 touched.add(a0)
                 f = [sr[l, a0] + se[l, a0] * sd[l, a0 + 1] + se[l, a0 - 1] * sd[l, a0 - 1]
@@ -108,7 +109,7 @@ def tile_apply(off, nx, ny, NL, k, tile, srcs, dnew, stored, omega):
                 for l in range(NL):
                     dv = sd[l, a0]
                     sd[l, a0] = omega * (xv[l] - dv) + dv
-    for q in range(T * T):
+    for q in range(T * TY):
         iy, ix = divmod(q, T)
         x, y = x0 + H + ix, y0 + H + iy
         if x >= nx or y >= ny:
@@ -119,14 +120,14 @@ def tile_apply(off, nx, ny, NL, k, tile, srcs, dnew, stored, omega):
             stored[o] += 1
 
 
-def lattice_round(lats, k, srcs, omega, converged=(), first=True):
+def lattice_round(lats, k, srcs, omega, converged=(), first=True, rows=SIDE):
     """One round over every lattice of a batch, as the kernel schedules it: a flat
     tile index, its lattice found by binary search over the first-tile table, and
     converged lattices skipped (their correction zeroed on the first round)."""
-    T = SIDE - 4 * k
+    T, TY = SIDE - 4 * k, rows - 4 * k
     tile0 = [0]
     for (off, nx, ny, nl) in lats:
-        tile0.append(tile0[-1] + (-(-nx // T)) * (-(-ny // T)))
+        tile0.append(tile0[-1] + (-(-nx // T)) * (-(-ny // TY)))
     dnew = np.full_like(srcs[0], np.nan)
     stored = np.zeros(srcs[0].size, int)
     for t in range(tile0[-1]):
@@ -143,8 +144,8 @@ def lattice_round(lats, k, srcs, omega, converged=(), first=True):
         if lo in converged:
             if first:
                 tiles_x = -(-nx // T)
-                tx0, ty0 = (tile % tiles_x) * T, (tile // tiles_x) * T
-                for q in range(T * T):
+                tx0, ty0 = (tile % tiles_x) * T, (tile // tiles_x) * TY
+                for q in range(T * TY):
                     x, y = tx0 + q % T, ty0 + q // T
                     if x < nx and y < ny:
                         for l in range(nl):
@@ -152,14 +153,14 @@ def lattice_round(lats, k, srcs, omega, converged=(), first=True):
                             dnew[o] = 0.0
                             stored[o] += 1
             continue
-        tile_apply(off, nx, ny, nl, k, tile, srcs, dnew, stored, omega)
+        tile_apply(off, nx, ny, nl, k, tile, srcs, dnew, stored, omega, rows)
     assert (stored == 1).all(), "every node of the batch written exactly once"
     return dnew
 
 
-def tile_round(nx, ny, NL, k, arrs, dold, omega):
+def tile_round(nx, ny, NL, k, arrs, dold, omega, rows=SIDE):
     srcs = [dold.ravel()] + [a.ravel() for a in arrs]
-    return lattice_round([(0, nx, ny, NL)], k, srcs, omega).reshape(dold.shape)
+    return lattice_round([(0, nx, ny, NL)], k, srcs, omega, rows=rows).reshape(dold.shape)
 
 
 def global_sweeps(nx, ny, NL, k, arrs, d, omega):
@@ -194,6 +195,18 @@ def test_tile_round_is_k_global_block_sweeps(nx, ny, NL, k):
     arrs = [rng.uniform(-1, 1, (NL, ny, nx))] + [rng.uniform(0.05, 0.2, (NL, ny, nx)) for _ in range(5)]
     d = rng.uniform(-1, 1, (NL, ny, nx))
     got = tile_round(nx, ny, NL, k, arrs, d, 1.3)
+    want = global_sweeps(nx, ny, NL, k, arrs, d, 1.3)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("nx,ny,NL,k", [(32, 130, 3, 2), (61, 75, 2, 3), (44, 70, 1, 1), (8, 6, 2, 2),
+                                        (36, 140, 3, 3)])
+def test_tall_tile_round_is_k_global_block_sweeps(nx, ny, NL, k):
+    """66-row regions (four rows per thread per half-sweep): the same sweeps, exactly."""
+    rng = np.random.default_rng(nx * 1000 + ny + 7)
+    arrs = [rng.uniform(-1, 1, (NL, ny, nx))] + [rng.uniform(0.05, 0.2, (NL, ny, nx)) for _ in range(5)]
+    d = rng.uniform(-1, 1, (NL, ny, nx))
+    got = tile_round(nx, ny, NL, k, arrs, d, 1.3, rows=66)
     want = global_sweeps(nx, ny, NL, k, arrs, d, 1.3)
     assert np.array_equal(got, want)
 

@@ -47,6 +47,44 @@ def test_noalloc_matches_pg_solve_twice(B, precision):
                 assert st.failed_step == -1 and st.total_sweeps > 0
 
 
+def test_noalloc_allocates_nothing_and_serves_two_grids(B):
+    """After grid creation (which sets up the fixed array) and one warm-up call, further
+    calls must leave the device's free memory unchanged: they take no new allocation of
+    any kind.  Two grids, solved alternately, both read and write the same array and must
+    each still match their own pg_solve; the statistics must be pg_solve's."""
+    nets = [pgsynth.config1(nx=61, ny=47), pgsynth.config0(nx=83, ny=71)]
+    rng = np.random.default_rng(5)
+    grids = [B.Grid(n, precision=p) for n, p in zip(nets, (1, 0))]
+    try:
+        stream = torch.cuda.current_stream().cuda_stream
+        cases = []
+        for g, net in zip(grids, nets):
+            B.pg_set_stream(g.handle, stream)
+            h = net.meta["h"]
+            b = torch.tensor(rng.uniform(-1e-3, 1e-3, net.n_nodes), device="cuda")
+            x_ref, x = torch.empty_like(b), torch.empty_like(b)
+            st_ref = B.pg_solve(g.handle, h, b, x_ref, TOL_X)
+            B.pg_solve_noalloc(g.handle, h, b, x, TOL_X)            # warm-up
+            cases.append((g, h, b, x_ref, x, st_ref))
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for rep in range(3):
+            for g, h, b, x_ref, x, st_ref in cases:
+                x.fill_(float("nan"))
+                st = B.pg_solve_noalloc(g.handle, h, b, x, TOL_X)
+                torch.cuda.synchronize()
+                diff = float((x - x_ref).abs().max())
+                assert diff <= 2 * TOL_X, f"rep {rep}: |x - x_ref| = {diff:.3e}"
+                for k in ("kappa", "kacc", "step_tol", "omega", "lattice_sweeps"):
+                    assert getattr(st, k) == getattr(st_ref, k), k
+                assert st.failed_step == -1
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] >= free0, "pg_solve_noalloc changed the free device memory"
+    finally:
+        for g in grids:
+            g.close()
+
+
 def test_noalloc_rejects_unassembled_h_and_oversize(B):
     net = pgsynth.config0(nx=20, ny=20)
     with B.Grid(net) as g:
