@@ -258,6 +258,7 @@ pg_status alloc_device(pg_grid* g) {
     c.stats = g->alloc<double>(kStatCount);
     if (!c.bar_count || !c.bar_gen || !c.err || !c.red || !c.blk_min || !c.blk_arg || !c.stats) return PG_ERR_OOM;
     if (d.lwE && !(c.lat_R = g->alloc<unsigned long long>(2 * (size_t)d.n_lats))) return PG_ERR_OOM;
+    if (!(c.tile_ctr = g->alloc<unsigned>(1))) return PG_ERR_OOM;
     if (!(c.ld_flags = g->alloc<unsigned>(4))) return PG_ERR_OOM;
     CK(cudaMemsetAsync(c.bar_gen, 0, sizeof(unsigned), g->stream));
     CK(cudaEventCreate(&g->ev0));
@@ -387,6 +388,7 @@ pg_status clear_ctl(pg_grid* g) {
     CK(cudaMemsetAsync(g->dc.bar_gen, 0, sizeof(unsigned), g->stream));
     CK(cudaMemsetAsync(g->dc.err, 0, sizeof(int32_t), g->stream));
     CK(cudaMemsetAsync(g->dc.red, 0, kRedSlots * sizeof(unsigned long long), g->stream));
+    CK(cudaMemsetAsync(g->dc.tile_ctr, 0, sizeof(unsigned), g->stream));
     if (g->dc.lat_R)
         CK(cudaMemsetAsync(g->dc.lat_R, 0, 2 * (size_t)g->dg.n_lats * sizeof(unsigned long long), g->stream));
     return PG_OK;

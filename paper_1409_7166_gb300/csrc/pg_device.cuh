@@ -72,39 +72,53 @@ __device__ __forceinline__ T nanmax_t(T a, T b) { return (a > b || a != a) ? a :
 // warp keeps a running (lattice, max) pair (warp-uniform) and publishes it with
 // one atomic when the lattice changes and at the end of the pass (lat_flush);
 // a slice that straddles lattices publishes its values directly.
-struct LatAcc {
+// V: the type of the maxima (double in the FP64 kernel, float in the mixed one, where
+// the monitored values are FP32 upper bounds); published as double bits either way.
+template <typename V>
+struct LatAccT {
     int L = -1;
-    double m = 0.0;
+    V m = V(0);
 };
-__device__ __forceinline__ void lat_flush(unsigned long long* latR, LatAcc& acc) {
-    if ((threadIdx.x & 31) == 0 && acc.L >= 0 && acc.m != 0.0)
-        atomicMax(latR + acc.L, (unsigned long long)__double_as_longlong(acc.m));
+using LatAcc = LatAccT<double>;
+template <typename V>
+__device__ __forceinline__ void lat_flush(unsigned long long* latR, LatAccT<V>& acc) {
+    if ((threadIdx.x & 31) == 0 && acc.L >= 0 && acc.m != V(0))
+        atomicMax(latR + acc.L, (unsigned long long)__double_as_longlong((double)acc.m));
     acc.L = -1;
-    acc.m = 0.0;
+    acc.m = V(0);
 }
 // `L` holds node_lat[i0 .. i0 + 3], loaded by the caller with the slice's other operands.
-__device__ __forceinline__ void lattice_max(unsigned long long* latR, const int (&L)[4], const double (&val)[4],
-                                            LatAcc& acc) {
+template <typename V>
+__device__ __forceinline__ void lattice_max(unsigned long long* latR, const int (&L)[4], const V (&val)[4],
+                                            LatAccT<V>& acc) {
     bool same = true;
     const int L0 = __shfl_sync(0xffffffffu, L[0], 0);
-    double m = 0.0;
+    V m = V(0);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         same = same && (L[j] == L0 || L[j] < 0);
-        if (L[j] >= 0) m = nanmax(m, val[j]);
+        if (L[j] >= 0) m = nanmax_t<V>(m, val[j]);
     }
     if (__all_sync(0xffffffffu, same)) {
-        for (int o = 16; o; o >>= 1) m = nanmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        for (int o = 16; o; o >>= 1) m = nanmax_t<V>(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (L0 < 0) return;
         if (L0 != acc.L) lat_flush(latR, acc);
         acc.L = L0;
-        acc.m = nanmax(acc.m, m);
+        acc.m = nanmax_t<V>(acc.m, m);
     } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (L[j] >= 0 && val[j] != 0.0) atomicMax(latR + L[j], (unsigned long long)__double_as_longlong(val[j]));
+            if (L[j] >= 0 && val[j] != V(0))
+                atomicMax(latR + L[j], (unsigned long long)__double_as_longlong((double)val[j]));
     }
 }
+
+// Upper bound of |r| / D from the FP32 copies r32 = fl(r) and invD32 = fl(1 / D): each of
+// the three roundings (r32, invD32, their product) is within 2^-24 relative, so scaling the
+// product by 1 + 2^-21 (itself rounded) can only raise it above the exact value.  The FP32
+// monitor costs no FP64 instructions, which GB300 issues at a small fraction of its FP32 rate.
+constexpr float kMonUp = 1.0f + 0x1p-21f;
+__device__ __forceinline__ float scaled_upper(float r32, float inv_d32) { return fabsf(r32) * inv_d32 * kMonUp; }
 
 // Order-preserving map of a double to an unsigned key (for min reductions).
 __device__ __forceinline__ unsigned long long order_key(double x) {
@@ -216,6 +230,23 @@ __device__ __forceinline__ float* dbuf<float>(const DevState& st, int k) { retur
 
 __device__ __forceinline__ double term_volt(const DevGrid& g, const double* v, int t) {
     return t >= 0 ? v[t] : (t == PG_GROUND ? 0.0 : g.vdd[-2 - t]);
+}
+
+// ---- shared-memory staging
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Asynchronous global -> shared copies (no registers held while in flight);
+// src_bytes = 0 fills the destination with zeros.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, unsigned src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, unsigned src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
 // ---- SELL slice descriptors

@@ -191,6 +191,7 @@ struct DevCtl {
     int32_t* blk_arg;               // [2 * nblocks]
     double* stats;                  // device statistics, see kStat*
     unsigned long long* lat_R;      // [2 * n_lats] per-lattice max |r| / D of the latest FP64 pass
+    unsigned int* tile_ctr;         // lattice tiles handed out so far in the launch, modulo 2^32 (cleared before it)
     unsigned int* ld_flags;         // [4] ring: word S & 3 is nonzero if a load current changed
                                     // between (S-1) h and S h; null disables the damped warm start
 };

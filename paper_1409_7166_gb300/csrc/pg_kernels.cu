@@ -203,14 +203,19 @@ template <bool MIXED, bool DAMP>
 __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* wc, const SliceDesc& sd,
                                             const DevState& st, const RunParams& rp, int s, int lane, int vL, int vP,
                                             int vF, bool extrap, bool three, bool inc, long long sabs, int dsel,
-                                            unsigned long long* latR, LatAcc& lacc, float th_in) {
+                                            unsigned long long* latR,
+                                            LatAccT<typename std::conditional<MIXED, float, double>::type>& lacc,
+                                            float th_in) {
+    using MonT = typename std::conditional<MIXED, float, double>::type;   // monitored max |r| / D
     const float th = DAMP ? th_in : 1.0f;
     const int i0 = s * kSlice + lane * kVec;
     const double* vl = vbuf(st, vL);
     const double* vp = vbuf(st, vP);
-    double vw[4], b[4], D[4], iD[4];
+    double vw[4], b[4], D[4];
+    MonT iD[4];                                  // 1 / D: FP32 for the mixed kernel's FP32 monitor
     ldg4(g.D64 + i0, D);
-    ldg4(g.invD64 + i0, iD);
+    if constexpr (MIXED) ldg4(g.invD32 + i0, iD);
+    else ldg4(g.invD64 + i0, iD);
 
     double base[4] = {0.0, 0.0, 0.0, 0.0};       // the residual is taken of M (x0 - base)
     if (rp.mode == kModeSolve) {
@@ -305,12 +310,19 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* w
     // a full step's md (M (x0 - v(s-1))) is written by md_slice before phase A; an
     // incremental step stores it here when it differs from the carried value
     if (track && inc && (!extrap || th != 1.0)) st4(st.md + i0, mdv);
-    double r[4], sc[4], mon = 0.0;
+    double r[4];
+    MonT sc[4], mon = MonT(0);
+    float r32[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         r[j] = inc ? b[j] : b[j] + sig[j] - D[j] * (vw[j] - base[j]);
-        sc[j] = fabs(r[j]) * iD[j];
-        mon = nanmax(mon, sc[j]);
+        if constexpr (MIXED) {
+            r32[j] = (float)r[j];
+            sc[j] = scaled_upper(r32[j], iD[j]);      // an FP32 upper bound of |r| / D
+        } else {
+            sc[j] = fabs(r[j]) * iD[j];
+        }
+        mon = nanmax_t<MonT>(mon, sc[j]);
     }
     if (latR) {
         int Lid[4];
@@ -325,10 +337,9 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* w
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int o = __ldg(g.orig + i0 + j);
-            if (o >= 0) { st.r32[o] = (float)r[j]; dz[o] = 0.f; }
+            if (o >= 0) { st.r32[o] = r32[j]; dz[o] = 0.f; }
         }
     } else if (MIXED) {
-        float r32[4] = {(float)r[0], (float)r[1], (float)r[2], (float)r[3]};
         float z[4] = {0.f, 0.f, 0.f, 0.f};
         st4(st.r32 + i0, r32);
         st4(dbuf<float>(st, dsel) + i0, z);
@@ -336,7 +347,7 @@ __device__ __forceinline__ double phase_rhs(const DevGrid& g, const WarpCache* w
         double z[4] = {0.0, 0.0, 0.0, 0.0};
         st4(dbuf<double>(st, dsel) + i0, z);
     }
-    return mon;
+    return (double)mon;
 }
 
 // One colour's SOR half-sweep on M delta = r (Eq. 16-17): returns max |unrelaxed update|.
@@ -400,7 +411,6 @@ __host__ __device__ constexpr int tma_stage_bytes(int elem_size) { return kStage
 // per warp: two stages and two mbarriers (padded to keep stages 128-byte aligned)
 __host__ __device__ constexpr int tma_warp_bytes(int elem_size) { return 2 * tma_stage_bytes(elem_size) + 128; }
 
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -577,20 +587,6 @@ __device__ double sweep_colour_tma(const DevGrid& g, const WarpCache* wc, TmaWar
 // count times ROWS rows).
 static_assert(kLatSide - 2 == 32, "the first half-sweep covers 32 columns, 16 pairs per half-warp row");
 
-// Asynchronous global -> shared copies (no registers held while in flight);
-// src_bytes = 0 fills the destination with zeros.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, unsigned src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src, unsigned src_bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
 // One tile (region of lattice L): load, 2k half-sweeps, store the interior.
 // Returns the max unrelaxed column update of the last sweep over the interior.
 // NL (layers) is a template parameter: the column solve unrolls completely.
@@ -715,9 +711,31 @@ __device__ float lattice_tile(const DevGrid& g, int off, int nx, int ny, int til
 template <int ROWS>
 __device__ double lattice_round(const DevGrid& g, const float* dold, float* dnew, const float* r, float omega,
                                 int k, unsigned char* smem, const unsigned long long* latR, double target,
-                                bool first) {
+                                bool first, unsigned* tile_ctr, unsigned round_base) {
+    // Tiles are handed out from a launch-wide counter, so a block that finishes early takes
+    // the next one: the round ends one tile after the last block starts its final tile,
+    // whatever the spread of tile times.  Each block claims its next tile while it works on
+    // the current one and stops at its first claim past the round's T tiles, so a round
+    // takes exactly T + gridDim.x claims: round n owns the counter values from
+    // round_base = n (T + gridDim.x) on, modulo 2^32 like the counter itself (the index
+    // claim - round_base is exact while one round takes fewer than 2^32 claims).  Any
+    // assignment gives the same result: a tile reads only the previous round's corrections
+    // and writes only its own interior.
+    __shared__ int s_tile;
+    const unsigned T = (unsigned)g.lat_tiles;
+    unsigned claim = 0;
+    if (threadIdx.x == 0) claim = atomicAdd(tile_ctr, 1u);
     float mon = 0.f;
-    for (int t = blockIdx.x; t < g.lat_tiles; t += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned t = claim - round_base;
+            s_tile = t < T ? (int)t : -1;
+            if (t < T) claim = atomicAdd(tile_ctr, 1u);        // the next one, in flight meanwhile
+        }
+        __syncthreads();
+        const int t = s_tile;
+        __syncthreads();
+        if (t < 0) break;
         int lo = 0, hi = g.n_lats;                      // lattice with lat_tile0[L] <= t < lat_tile0[L+1]
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -754,8 +772,10 @@ __device__ double lattice_round(const DevGrid& g, const float* dold, float* dnew
 template <typename T>
 __device__ __forceinline__ double outer_slice(const DevGrid& g, const WarpCache* wc, const SliceDesc& sd,
                                               const DevState& st, const T* d, T* dnext, float* r32, int s, int lane,
-                                              double* v, bool lat, unsigned long long* latR, LatAcc& lacc,
+                                              double* v, bool lat, unsigned long long* latR, LatAccT<T>& lacc,
                                               double* md) {
+    // T = float (mixed precision): the monitored max |r| / D is an FP32 upper bound from the
+    // FP32 residual copy this pass writes anyway (scaled_upper); T = double: exact FP64
     const int i0 = s * kSlice + lane * kVec;
     T dv[4];
     if (lat) {
@@ -768,8 +788,10 @@ __device__ __forceinline__ double outer_slice(const DevGrid& g, const WarpCache*
     } else {
         ld4(d + i0, dv);
     }
-    double iD[4], r[4], vv[4];
-    ldg4(g.invD64 + i0, iD);
+    double r[4], vv[4];
+    T iD[4];
+    if constexpr (std::is_same<T, float>::value) ldg4(g.invD32 + i0, iD);
+    else ldg4(g.invD64 + i0, iD);
     ld4(st.r64 + i0, r);
     ld4(v + i0, vv);
     double Md[4];                                      // (M delta)_i
@@ -791,7 +813,12 @@ __device__ __forceinline__ double outer_slice(const DevGrid& g, const WarpCache*
         for (int j = 0; j < 4; ++j) {
             float ph = 0.f, pl = 0.f;
             df_acc(ph, pl, dh[j], dl[j], dv[j]);           // D delta
-            Md[j] = ((double)ph - (double)hi[j]) + ((double)pl - (double)lo[j]);
+            // (ph + pl) - (hi + lo): ph - hi = sd + ed exactly (TwoSum), the rest in FP32, so
+            // that only two values cross to FP64 (GB300 issues FP64 and conversions slowly)
+            const float sd = __fsub_rn(ph, hi[j]);
+            const float bd = __fsub_rn(sd, ph);
+            const float ed = __fadd_rn(__fsub_rn(ph, __fsub_rn(sd, bd)), __fsub_rn(-hi[j], bd));
+            Md[j] = (double)sd + (double)(ed + (pl - lo[j]));
         }
     } else {
         double D[4], sig[4];
@@ -807,13 +834,16 @@ __device__ __forceinline__ double outer_slice(const DevGrid& g, const WarpCache*
         for (int j = 0; j < 4; ++j) m4[j] += Md[j];
         st4(md + i0, m4);
     }
-    double mon = 0.0, sc[4];
+    T mon = T(0), sc[4];
+    float f[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         r[j] -= Md[j];
         vv[j] += (double)dv[j];
-        sc[j] = fabs(r[j]) * iD[j];
-        mon = nanmax(mon, sc[j]);
+        f[j] = (float)r[j];
+        if constexpr (std::is_same<T, float>::value) sc[j] = scaled_upper(f[j], iD[j]);
+        else sc[j] = fabs(r[j]) * iD[j];
+        mon = nanmax_t<T>(mon, sc[j]);
     }
     if (latR) {
         int Lid[4];
@@ -826,17 +856,14 @@ __device__ __forceinline__ double outer_slice(const DevGrid& g, const WarpCache*
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int o = __ldg(g.orig + i0 + j);
-            if (o >= 0) { dnext[o] = T(0); r32[o] = (float)r[j]; }
+            if (o >= 0) { dnext[o] = T(0); r32[o] = f[j]; }
         }
     } else {
         T z[4] = {T(0), T(0), T(0), T(0)};
         st4(dnext + i0, z);
-        if (r32) {
-            float f[4] = {(float)r[0], (float)r[1], (float)r[2], (float)r[3]};
-            st4(r32 + i0, f);
-        }
+        if (r32) st4(r32 + i0, f);
     }
-    return mon;
+    return (double)mon;
 }
 
 }  // namespace
@@ -968,6 +995,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
     const double target = rp.target_scale ? rp.target * __longlong_as_double((long long)*rp.target_scale) : rp.target;
     int vL = rp.cur, vP = rp.prev, vF = 3 - rp.cur - rp.prev;
     bool have_prev = rp.have_prev != 0;
+    unsigned lat_rounds = 0;     // lattice rounds run in this launch (the same in every block), modulo 2^32
     // per-lattice residual maxima (lattice inner solve): two buffers, `lat_par` is the one
     // the latest FP64 pass wrote; the host clears both before the launch
     const bool per_lat = MIXED && rp.lat_k > 0 && ctl.lat_R != nullptr;
@@ -1072,7 +1100,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
                 }
         }
         {
-            LatAcc lacc;
+            LatAccT<T> lacc;
             unsigned long long* lb = lat_buf(lat_par ^ 1);
             for (int c = 0; c < g.ncol; ++c)
                 for (int tt = 0; tt < wc->cnt[c]; ++tt) {
@@ -1116,7 +1144,9 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
                 const float* dold = dbuf<float>(st, dsel);
                 float* dnew = dbuf<float>(st, dsel ^ 1);
                 const double m = lattice_round<ROWS>(g, dold, dnew, st.r32, (float)omega, rp.lat_k, s_dyn,
-                                               lat_buf(lat_par), target, inner == 0);
+                                               lat_buf(lat_par), target, inner == 0, ctl.tile_ctr,
+                                               lat_rounds * ((unsigned)g.lat_tiles + nblocks));
+                ++lat_rounds;
                 const BarrierResult be = barrier(true, m);
                 if (!be.ok) { publish(-1); return; }
                 const double est = be.val;
@@ -1191,7 +1221,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
             double m = 0.0;
             T* dn = dbuf<T>(st, dsel ^ 1);
             {
-                LatAcc lacc;
+                LatAccT<T> lacc;
                 unsigned long long* lb = lat_buf(lat_par ^ 1);
                 for (int c = 0; c < g.ncol; ++c)
                     for (int tt = 0; tt < wc->cnt[c]; ++tt) {

@@ -38,7 +38,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Byte layout of the scratch for a grid with n_pad permuted nodes and `blocks` CTAs.
 struct Layout {
-    size_t ctl, red, stats, blk_min, blk_arg, rhs, v, r64, r32, d0, d1, total;
+    size_t ctl, red, tile, stats, blk_min, blk_arg, rhs, v, r64, r32, d0, d1, total;
 };
 
 Layout layout(int n_pad, int blocks, bool mixed) {
@@ -46,6 +46,7 @@ Layout layout(int n_pad, int blocks, bool mixed) {
     size_t o = 0;
     L.ctl = o;      o = align256(o + 3 * sizeof(uint32_t));              // barrier count, generation, error
     L.red = o;      o = align256(o + pg::kRedSlots * sizeof(unsigned long long));
+    L.tile = o;     o = align256(o + sizeof(unsigned));                      // lattice tile counter
     L.stats = o;    o = align256(o + pg::kStatCount * sizeof(double));
     L.blk_min = o;  o = align256(o + 2 * size_t(blocks) * sizeof(unsigned long long));
     L.blk_arg = o;  o = align256(o + 2 * size_t(blocks) * sizeof(int32_t));
@@ -116,6 +117,7 @@ extern "C" pg_status pg_solve_noalloc(pg_grid* g, double h, const double* b, dou
     c.bar_gen = c.bar_count + 1;
     c.err = reinterpret_cast<int32_t*>(c.bar_count + 2);
     c.red = reinterpret_cast<unsigned long long*>(base + L.red);
+    c.tile_ctr = reinterpret_cast<unsigned*>(base + L.tile);
     c.stats = reinterpret_cast<double*>(base + L.stats);
     c.blk_min = reinterpret_cast<unsigned long long*>(base + L.blk_min);
     c.blk_arg = reinterpret_cast<int32_t*>(base + L.blk_arg);
@@ -139,7 +141,8 @@ extern "C" pg_status pg_solve_noalloc(pg_grid* g, double h, const double* b, dou
     cudaStream_t s = g->stream;
     cudaError_t e = cudaSuccess;
     if ((e = cudaMemsetAsync(base + L.ctl, 0, 3 * sizeof(uint32_t), s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(base + L.red, 0, pg::kRedSlots * sizeof(unsigned long long), s)) != cudaSuccess)
+        (e = cudaMemsetAsync(base + L.red, 0, pg::kRedSlots * sizeof(unsigned long long), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(base + L.tile, 0, sizeof(unsigned), s)) != cudaSuccess)
         return fail(PG_ERR_CUDA, cudaGetErrorString(e));
     if ((e = pg::launch_permute_in(g->dg.orig, b, 0.0, rhs, g->P.n_pad, g->n_sm, s)) != cudaSuccess)
         return fail(PG_ERR_CUDA, cudaGetErrorString(e));

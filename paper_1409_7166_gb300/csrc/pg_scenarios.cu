@@ -1,5 +1,7 @@
 // Many load scenarios of one grid in one persistent launch, sharing every
-// coefficient of the system.
+// coefficient of the system.  Grids built for the lattice inner solve relax the
+// scenarios with its column-block tiles (four scenarios per shared-memory region);
+// other grids with the coloured neighbour-list sweeps.
 //
 // Every scenario has the same nodal matrix M = C/h + G + G0 (Eq. 2) and its own
 // right-hand side (its own load currents), so the relaxation of Eq. 16-17 runs
@@ -46,7 +48,180 @@ struct ScenParams {
     int32_t max_sweeps, max_outer;
     long long timeout_ns;
     double* v_all;             // [nsteps][n_scen][n_real] or null
+    int32_t lat_k;             // > 0: lattice inner solve, lat_k exact block sweeps per round
+    int32_t lat_maxnl;         // layers held per region (the grid's largest lattice layer count)
 };
+
+// ---- lattice inner solve for scenario groups
+//
+// The column-block red-black SOR of the single-scenario lattice solve (k exact block
+// sweeps per device barrier on 34 x 34-column regions with ghost zones of 2k columns;
+// each (x, y) column's layers solved exactly with the precomputed Thomas factors), with a
+// group's four scenarios in one region: their corrections and residuals as one float4
+// per column and layer, the coefficients staged once for all four.
+constexpr int kScW = 36;                       // shared-memory row stride (columns)
+constexpr int kScPlane = kLatSide * kScW;      // one layer of one staged array
+
+__host__ __device__ inline size_t scen_region_bytes(int maxnl) {
+    return (size_t)maxnl * kScPlane * (2 * sizeof(float4) + 5 * sizeof(float));
+}
+
+template <int NL>
+__device__ float scen_lattice_tile(const DevGrid& g, int off, int nx, int ny, int tile, int q, const float* dold,
+                                   float* dnew, const float* r, float omega, int k, int maxnl, unsigned char* smem) {
+    const int H = 2 * k, T = kLatSide - 2 * H;
+    const int tiles_x = (nx + T - 1) / T;
+    const int A = maxnl * kScPlane;                          // elements per staged array
+    float4* sd = reinterpret_cast<float4*>(smem);
+    float4* sr = sd + A;
+    float* se = reinterpret_cast<float*>(sr + A);
+    float* sn = se + A;
+    float* su = se + 2 * A;
+    float* sm = se + 3 * A;
+    float* sp = se + 4 * A;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pair = lane & 15, rsub = lane >> 4;
+    const long long plane = (long long)nx * ny;
+    const long long gq = (long long)q * g.n_pad;            // the group's first node
+    const int x0 = (tile % tiles_x) * T - H, y0 = (tile / tiles_x) * T - H;
+    const int lead = x0 & 3;
+    const int xa = x0 - lead;
+    // corrections and residuals: one 16-byte copy per column and layer
+    for (int qq = threadIdx.x; qq < kScPlane; qq += blockDim.x) {
+        const int ry = qq / kScW, c = qq - ry * kScW;
+        const int xx = xa + c, yy = y0 + ry;
+        const bool in = yy >= 0 && yy < ny && xx >= 0 && xx < nx;
+        const long long o = in ? off + (long long)yy * nx + xx : 0;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            const long long e = in ? (gq + o + l * plane) * kGroup : 0;
+            cp_async16(sd + l * kScPlane + qq, dold + e, in ? 16u : 0u);
+            cp_async16(sr + l * kScPlane + qq, r + e, in ? 16u : 0u);
+        }
+    }
+    // the coefficients, shared by the group: 16-byte pieces where the lattice allows them
+    auto src_of = [&](int arr) -> const float* {
+        return arr == 0 ? g.lwE : arr == 1 ? g.lwN : arr == 2 ? g.lwU : arr == 3 ? g.lm : g.lip;
+    };
+    if ((nx & 3) == 0 && (off & 3) == 0) {
+        constexpr int kChunks = kScW / 4;
+        constexpr int kPieces = kLatSide * kChunks;
+        for (int qq = threadIdx.x; qq < kPieces * 5; qq += blockDim.x) {
+            const int arr = qq / kPieces, pos = qq - arr * kPieces;
+            const int ry = pos / kChunks, c4 = 4 * (pos - ry * kChunks);
+            const int xx = xa + c4, yy = y0 + ry;
+            const bool in = yy >= 0 && yy < ny && xx >= 0 && xx < nx;
+            const long long o = in ? off + (long long)yy * nx + xx : 0;
+            float* dst = se + arr * A + ry * kScW + c4;
+#pragma unroll
+            for (int l = 0; l < NL; ++l)
+                cp_async16(dst + l * kScPlane, src_of(arr) + (in ? o + l * plane : 0), in ? 16u : 0u);
+        }
+    } else {
+        for (int qq = threadIdx.x; qq < kScPlane; qq += blockDim.x) {
+            const int ry = qq / kScW, c = qq - ry * kScW;
+            const int xx = xa + c, yy = y0 + ry;
+            const bool in = yy >= 0 && yy < ny && xx >= 0 && xx < nx;
+            const long long o = in ? off + (long long)yy * nx + xx : 0;
+#pragma unroll
+            for (int arr = 0; arr < 5; ++arr)
+#pragma unroll
+                for (int l = 0; l < NL; ++l)
+                    cp_async4(se + arr * A + l * kScPlane + qq, src_of(arr) + (in ? o + l * plane : 0), in ? 4u : 0u);
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    float mon = 0.f;
+    for (int hs = 0; hs < 2 * k; ++hs) {
+        const bool last = hs >= 2 * k - 2;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int ry = 1 + 2 * (warp + 8 * j) + rsub, y = y0 + ry;
+            const int cx = 1 + 2 * pair + ((hs + x0 + 1 + y) & 1);
+            const int x = x0 + cx;
+            const int edge = min(min(cx, ry), min(kLatSide - 1 - cx, kLatSide - 1 - ry));
+            if (edge <= hs || x < 0 || x >= nx || y < 0 || y >= ny) continue;
+            const int a0 = ry * kScW + cx + lead;
+            float4 f[NL], xv[NL];
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                const int a = a0 + l * kScPlane;
+                const float we = se[a], ww = se[a - 1], wn = sn[a], ws = sn[a - kScW];
+                const float4 rr = sr[a], de = sd[a + 1], dw = sd[a - 1], dn = sd[a + kScW], ds = sd[a - kScW];
+                f[l].x = rr.x + we * de.x + ww * dw.x + wn * dn.x + ws * ds.x;
+                f[l].y = rr.y + we * de.y + ww * dw.y + wn * dn.y + ws * ds.y;
+                f[l].z = rr.z + we * de.z + ww * dw.z + wn * dn.z + ws * ds.z;
+                f[l].w = rr.w + we * de.w + ww * dw.w + wn * dn.w + ws * ds.w;
+            }
+#pragma unroll
+            for (int l = 1; l < NL; ++l) {
+                const float m = sm[a0 + l * kScPlane];
+                f[l].x = fmaf(m, f[l - 1].x, f[l].x); f[l].y = fmaf(m, f[l - 1].y, f[l].y);
+                f[l].z = fmaf(m, f[l - 1].z, f[l].z); f[l].w = fmaf(m, f[l - 1].w, f[l].w);
+            }
+            {
+                const float p = sp[a0 + (NL - 1) * kScPlane];
+                xv[NL - 1] = make_float4(f[NL - 1].x * p, f[NL - 1].y * p, f[NL - 1].z * p, f[NL - 1].w * p);
+            }
+#pragma unroll
+            for (int l = NL - 2; l >= 0; --l) {
+                const float u = su[a0 + l * kScPlane], p = sp[a0 + l * kScPlane];
+                xv[l] = make_float4(fmaf(u, xv[l + 1].x, f[l].x) * p, fmaf(u, xv[l + 1].y, f[l].y) * p,
+                                    fmaf(u, xv[l + 1].z, f[l].z) * p, fmaf(u, xv[l + 1].w, f[l].w) * p);
+            }
+            const bool interior = edge >= H;
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                const int a = a0 + l * kScPlane;
+                const float4 dv = sd[a];
+                const float4 up = make_float4(xv[l].x - dv.x, xv[l].y - dv.y, xv[l].z - dv.z, xv[l].w - dv.w);
+                sd[a] = make_float4(fmaf(omega, up.x, dv.x), fmaf(omega, up.y, dv.y), fmaf(omega, up.z, dv.z),
+                                    fmaf(omega, up.w, dv.w));
+                if (last && interior)
+                    mon = nanmaxf(nanmaxf(mon, nanmaxf(fabsf(up.x), fabsf(up.y))), nanmaxf(fabsf(up.z), fabsf(up.w)));
+            }
+        }
+        __syncthreads();
+    }
+    for (int qq = threadIdx.x; qq < T * T; qq += blockDim.x) {
+        const int iy = qq / T, ix = qq - iy * T;
+        const int x = x0 + H + ix, y = y0 + H + iy;
+        if (x >= nx || y >= ny) continue;
+        const long long b = off + (long long)y * nx + x;
+        const int a = (H + iy) * kScW + H + ix + lead;
+#pragma unroll
+        for (int l = 0; l < NL; ++l)
+            *reinterpret_cast<float4*>(dnew + (gq + b + l * plane) * kGroup) = sd[l * kScPlane + a];
+    }
+    __syncthreads();   // the next tile overwrites the region
+    return mon;
+}
+
+// One round over every (tile, scenario group) of every lattice; the max unrelaxed update
+// of the last sweep over the tile interiors.
+__device__ double scen_lattice_round(const DevGrid& g, const float* dold, float* dnew, const float* r, float omega,
+                                     int k, int maxnl, int n_groups, unsigned char* smem) {
+    float mon = 0.f;
+    const long long tasks = (long long)g.lat_tiles * n_groups;
+    for (long long task = blockIdx.x; task < tasks; task += gridDim.x) {
+        const int t = (int)(task / n_groups), q = (int)(task - (long long)t * n_groups);
+        int lo = 0, hi = g.n_lats;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(g.lat_tile0 + mid) <= t) lo = mid; else hi = mid;
+        }
+        const int off = __ldg(g.lat_info + 4 * lo), nx = __ldg(g.lat_info + 4 * lo + 1),
+                  ny = __ldg(g.lat_info + 4 * lo + 2), nl = __ldg(g.lat_info + 4 * lo + 3);
+        const int tile = t - __ldg(g.lat_tile0 + lo);
+        float m;
+        if (nl == 1) m = scen_lattice_tile<1>(g, off, nx, ny, tile, q, dold, dnew, r, omega, k, maxnl, smem);
+        else if (nl == 2) m = scen_lattice_tile<2>(g, off, nx, ny, tile, q, dold, dnew, r, omega, k, maxnl, smem);
+        else m = scen_lattice_tile<3>(g, off, nx, ny, tile, q, dold, dnew, r, omega, k, maxnl, smem);
+        mon = nanmaxf(mon, m);
+    }
+    return (double)mon;
+}
 
 __device__ __forceinline__ long long vbase(const DevGrid& g, int q, int i) {
     return ((long long)q * g.n_pad + i) * kGroup;
@@ -252,7 +427,27 @@ __global__ void __launch_bounds__(256, 2) scenario_kernel(DevGrid g, ScenState s
             double est_mark = INFINITY;
             int inner = 0;
             bool bad = false;
-            while (true) {
+            while (MIXED && sp.lat_k > 0) {
+                // lattice rounds: lat_k exact block sweeps per device barrier, four scenarios per region
+                extern __shared__ __align__(16) unsigned char s_dyn[];
+                const double m = scen_lattice_round(g, (const float*)ss.d[dsel], (float*)ss.d[dsel ^ 1], ss.r32,
+                                                    (float)sp.omega, sp.lat_k, sp.lat_maxnl, NG, s_dyn);
+                const BarrierResult be = barrier(true, m);
+                if (!be.ok) { publish(-1); return; }
+                const double est = be.val;
+                dsel ^= 1;
+                dd = (T*)ss.d[dsel];
+                const int before = inner;
+                sweeps += sp.lat_k;
+                inner += sp.lat_k;
+                if (!(est == est)) { bad = true; break; }
+                if (est <= inner_tgt || sweeps >= sp.max_sweeps) break;
+                if ((inner >> 4) != (before >> 4)) {
+                    if (est > 0.9 * est_mark) break;
+                    est_mark = est;
+                }
+            }
+            while (!(MIXED && sp.lat_k > 0)) {
                 double est = 0.0;
                 for (int c = 0; c < g.ncol; ++c) {
                     const int c0 = __ldg(g.colour_slice + c), c1 = __ldg(g.colour_slice + c + 1);
@@ -439,8 +634,8 @@ extern "C" pg_status pg_transient_scenarios(pg_grid* g, double h, int32_t nsteps
     if (!g || nsteps < 1 || n_scen < 1 || !i_v) return fail(PG_ERR_INVALID_ARG, "null grid or values, or no steps");
     if (g->P.n_l > 0) return fail(PG_ERR_UNSUPPORTED, "load scenarios run on RC grids (no inductors)");
     if (g->opt.form != PG_FORM_EXPLICIT) return fail(PG_ERR_UNSUPPORTED, "load scenarios need the explicit form");
-    if (g->dg.lwE) return fail(PG_ERR_UNSUPPORTED, "load scenarios run the neighbour-list sweeps: create the grid "
-                                                   "with lattice_sweeps = -1");
+    if (g->dg.lwE && g->dg.lat_rows != kLatSide)
+        return fail(PG_ERR_UNSUPPORTED, "load scenarios on the lattice inner solve take 34-row regions (tile_rows 0 or 34)");
     const NetCopy& nc = g->nc;
     const size_t npts = nc.i_t.size();
     const bool host = out && out->on_host;
@@ -516,6 +711,8 @@ extern "C" pg_status pg_transient_scenarios(pg_grid* g, double h, int32_t nsteps
                     for (int c = 0; c < kGroup; ++c) v0[((size_t)q * n_pad + i) * kGroup + c] = nc.vdd[0];
         if ((s = ck(cudaMemcpyAsync(ss.v[0], v0.data(), nv * sizeof(double), cudaMemcpyHostToDevice, stream))) ||
             (s = ck(cudaMemcpyAsync(ss.v[1], v0.data(), nv * sizeof(double), cudaMemcpyHostToDevice, stream))) ||
+            (s = ck(cudaMemsetAsync(ss.d[0], 0, nv * ds, stream))) ||
+            (s = ck(cudaMemsetAsync(ss.d[1], 0, nv * ds, stream))) ||
             (s = ck(cudaMemsetAsync(ss.inode[0], 0, nv * sizeof(double), stream))) ||
             (s = ck(cudaMemsetAsync(ss.inode[1], 0, nv * sizeof(double), stream))) ||
             (hv.size() && (s = ck(cudaMemcpyAsync(pv, hv.data(), hv.size() * sizeof(double), cudaMemcpyHostToDevice,
@@ -533,17 +730,24 @@ extern "C" pg_status pg_transient_scenarios(pg_grid* g, double h, int32_t nsteps
     sp.max_outer = 50;
     sp.timeout_ns = (long long)(g->opt.barrier_timeout_s * 1e9);
     sp.v_all = v_all;
+    sp.lat_k = g->dg.lwE ? g->lat_k : 0;             // grids built for the lattice inner solve
+    sp.lat_maxnl = g->P.lat_maxnl;
+    const size_t smem = sp.lat_k > 0 ? scen_region_bytes(sp.lat_maxnl) : 0;
     // launch: at most the co-resident blocks, no more than the work of a colour sweep needs
     const void* fn = g->mixed ? (const void*)scenario_kernel<true> : (const void*)scenario_kernel<false>;
+    if (smem > 0 && (s = ck(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))))
+        return s;
     int bps = 0;
-    if ((s = ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 256, 0)))) return s;
+    if ((s = ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 256, smem)))) return s;
     if (g->opt.blocks_per_sm > 0) bps = std::min(bps, g->opt.blocks_per_sm);
     if (bps < 1) return fail(PG_ERR_CUDA, "scenario kernel does not fit on an SM");
     int smax = 1;
     for (int c = 0; c < g->P.ncol; ++c)
         smax = std::max(smax, (g->P.colour_start[c + 1] - g->P.colour_start[c]) / kSlice);
     const long long warps = (long long)smax * NG;
-    const int blocks = (int)std::max<long long>(1, std::min<long long>((long long)g->n_sm * bps, (warps + 7) / 8));
+    long long want = (warps + 7) / 8;
+    if (sp.lat_k > 0) want = std::max<long long>(want, (long long)g->dg.lat_tiles * NG);   // one task per block
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((long long)g->n_sm * bps, want));
     // the launch's own barrier and reduction words (the grid's, cleared first)
     DevCtl ctl = g->dc;
     if ((s = ck(cudaMemsetAsync(ctl.bar_count, 0, sizeof(unsigned), stream))) ||
@@ -554,7 +758,7 @@ extern "C" pg_status pg_transient_scenarios(pg_grid* g, double h, int32_t nsteps
     DevGrid dg = g->dg;
     void* args[] = {(void*)&dg, (void*)&ss, (void*)&ctl, (void*)&sp};
     if ((s = ck(cudaEventRecord(g->ev0, stream))) ||
-        (s = ck(cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(256), args, 0, stream))) ||
+        (s = ck(cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(256), args, smem, stream))) ||
         (s = ck(cudaEventRecord(g->ev1, stream))))
         return s;
     int32_t err = 0;

@@ -141,3 +141,24 @@ def test_colouring_and_tile_rows_validation():
         assert ei.value.status == B.PG_ERR_INVALID_ARG
     o = B.pg_default_options()
     assert (o.colouring, o.tile_rows) == (B.PG_COLOUR_AUTO, 0)
+
+
+def test_block_half_sweep_and_scenarios_validate_arguments():
+    """pg_block_half_sweep refuses null arrays, empty blocks, colours other than 0 and 1 and
+    omega outside (0, 2), and pg_transient_scenarios a null grid or no steps, all before
+    touching the device (status PG_ERR_INVALID_ARG)."""
+    import ctypes as C
+    from paper_1409_7166_gb300 import binding as B
+    L = B.lib()
+    blk = B.pg_row_block()
+    mx = C.c_double(0.0)
+    assert L.pg_block_half_sweep(C.byref(blk), 0, 1.5, C.byref(mx), None) == B.PG_ERR_INVALID_ARG
+    buf = (C.c_double * 64)()
+    ptr = C.cast(buf, C.c_void_p)
+    blk = B.pg_row_block(4, 2, 1, 0, ptr, ptr, ptr, ptr, ptr, ptr)
+    for colour, omega in ((2, 1.5), (-1, 1.5), (0, 0.0), (1, 2.0)):
+        assert L.pg_block_half_sweep(C.byref(blk), colour, omega, C.byref(mx), None) == B.PG_ERR_INVALID_ARG
+    empty = B.pg_row_block(4, 0, 1, 0, ptr, ptr, ptr, ptr, ptr, ptr)
+    assert L.pg_block_half_sweep(C.byref(empty), 0, 1.5, C.byref(mx), None) == B.PG_ERR_INVALID_ARG
+    st = B.pg_run_stats()
+    assert L.pg_transient_scenarios(None, 1e-12, 10, 2, ptr, None, C.byref(st)) == B.PG_ERR_INVALID_ARG
