@@ -141,16 +141,15 @@ def solve_scenarios_shared(net, load_values: Sequence, h: float, nsteps: int, de
                            **options) -> np.ndarray:
     """Like :func:`solve_scenarios`, but the scenarios share one copy of the grid: one
     launch of ``pg_transient_scenarios`` relaxes every right-hand side together, each
-    coefficient read once for all of them.  Needs an RC grid on the neighbour-list
-    sweeps (``lattice_sweeps = -1`` is set here).  Returns ``[nsteps, len(load_values)]``."""
+    coefficient read once for all of them.  Needs an RC grid; ``options`` as for
+    :class:`binding.Grid` (the lattice inner solve where the grid's options choose it).
+    Returns ``[nsteps, len(load_values)]``."""
     import torch
 
     from . import binding as B
 
     dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
     iv = torch.tensor(np.stack([np.asarray(v, dtype=np.float64) for v in load_values]), device=dev)
-    options = dict(options)
-    options.setdefault("lattice_sweeps", -1)
     with torch.cuda.device(dev):
         with B.Grid(net, **options) as g:
             B.pg_set_stream(g.handle, torch.cuda.current_stream(dev).cuda_stream)

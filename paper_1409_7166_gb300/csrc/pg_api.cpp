@@ -7,6 +7,7 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "pg_grid.h"
@@ -1021,15 +1022,29 @@ pg_status pg_update_values(pg_grid* g, const double* r_g, const double* c_val, c
     view.n_c = (int64_t)trial.c_val.size(); view.c_a = trial.c_a.data(); view.c_b = trial.c_b.data(); view.c_val = trial.c_val.data();
     view.n_l = (int64_t)trial.l_val.size(); view.l_a = trial.l_a.data(); view.l_b = trial.l_b.data(); view.l_val = trial.l_val.data();
     std::string why;
-    Packed backup = g->P;
-    if ((s = refill_values(&view, &g->P, &why))) {
-        g->P = std::move(backup);
+    // refill_values changes only the value arrays: keep those to restore on a refusal
+    Packed& P = g->P;
+    auto keep = std::make_tuple(P.adj_g, P.adj_il, P.g_gnd, P.il_gnd, P.cap, P.inj_g, P.inj_il, P.ind_invL);
+    if ((s = refill_values(&view, &P, &why))) {
+        std::tie(P.adj_g, P.adj_il, P.g_gnd, P.il_gnd, P.cap, P.inj_g, P.inj_il, P.ind_invL) = std::move(keep);
         g_last_error = why;
         return s;
     }
     nc = std::move(trial);
     g->h = -1.0;            // re-assemble the per-h coefficients on the next call
-    g->dcgrid.reset();      // the resistive network changed too
+    // The resistive (DC) network has the same topology: refill its resistor values in place
+    // (capacitors and inductors are not part of it); rebuild it only if that fails.
+    if (g->dcgrid && r_g) {
+        pg_netlist dv = nc.dc_view();
+        std::string why2;
+        if (refill_values(&dv, &g->dcgrid->P, &why2) == PG_OK) {
+            g->dcgrid->nc.r_g = nc.r_g;
+            g->dcgrid->h = -1.0;
+            g->dcgrid->inc_ok = false;
+        } else {
+            g->dcgrid.reset();
+        }
+    }
     return PG_OK;
 }
 

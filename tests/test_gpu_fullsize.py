@@ -297,3 +297,93 @@ def test_config4_full_size_adjoint(B):
         ad = float((torch.tensor(sgn * net.r_g, device=dev) * gG).sum())
         print(f"central difference {fd:.12e} adjoint {ad:.12e}")
         assert fd == pytest.approx(ad, rel=1e-4)
+
+
+def test_config4_full_size_per_parameter_gradients(B):
+    """dJ/dg of 50 random resistors and dJ/dC of 50 random capacitors of the 2048x2048 grid
+    (500 steps), one parameter at a time (the paper has no adjoint; these are properties of
+    the discrete recurrence at any size).
+
+    * Resistors: central differences J(g + eps) - J(g - eps) formed per term of J (every
+      node and step, FP64 on the device), eps 1 % of the resistor's conductance, with omega
+      fixed so that both runs take the same iteration; relative 1e-4.
+    * Capacitors: the tangent-linear recurrence M dv_s = (C/h) dv_(s-1) - (dC/h)(v_s - v_(s-1))
+      along the capacitor's own direction, each solve certified to tol_s; the directional
+      derivative sum dJ/dv dv must equal C dJ/dC within kacc tol_s sum |dJ/dv| plus 1e-7
+      relative."""
+    net = pgsynth.config4()
+    h, S, n = net.meta["h"], net.meta["nsteps"], net.n_nodes
+    vref, margin, vdd = 1.0, 0.05, float(net.vdd[0])
+    dev = "cuda"
+    rng = np.random.default_rng(100)
+    seg = np.where((net.r_a >= 0) & (net.r_b >= 0))[0]
+    pick_r = rng.choice(seg, size=50, replace=False)
+    pick_c = rng.choice(len(net.c_val), size=50, replace=False)
+    with B.Grid(net, precision=B.PG_PREC_MIXED, tol=1e-9) as g0:
+        st0 = B.pg_transient(g0.handle, h, 0)
+        omega = st0.omega
+    opts = dict(precision=B.PG_PREC_MIXED, tol=1e-9, omega=omega)
+    with B.Grid(net, **opts) as g:
+        B.pg_set_stream(g.handle, torch.cuda.current_stream().cuda_stream)
+        gG = torch.zeros(len(net.r_g), dtype=torch.float64, device=dev)
+        gC = torch.zeros(len(net.c_val), dtype=torch.float64, device=dev)
+        J, st = B.pg_adjoint(g.handle, h, S, vref=vref, margin=margin, ckpt_every=50, dJ_dG=gG, dJ_dC=gC)
+        gG, gC = gG.cpu().numpy(), gC.cpu().numpy()
+
+        # resistors: per-term central differences
+        Vp = torch.empty((S, n), dtype=torch.float64, device=dev)
+        Vm = torch.empty_like(Vp)
+        worst = 0.0
+        for e in pick_r:
+            eps = 1e-2 * net.r_g[e]
+            for sign, Vx in ((1.0, Vp), (-1.0, Vm)):
+                rg = np.array(net.r_g, dtype=np.float64)
+                rg[e] += sign * eps
+                B.pg_update_values(g.handle, r_g=rg)
+                B.pg_reset(g.handle)
+                B.pg_transient(g.handle, h, S, v_all=Vx)
+            dJ = 0.0
+            for a in range(0, S, 50):
+                sp_p = torch.nn.functional.softplus(vref - Vp[a:a + 50] - margin, threshold=1e9)
+                sp_m = torch.nn.functional.softplus(vref - Vm[a:a + 50] - margin, threshold=1e9)
+                dJ += float(((sp_p - sp_m) * (sp_p + sp_m)).sum())
+            fd = dJ / (2.0 * eps)
+            rel = abs(fd - gG[e]) / abs(gG[e])
+            worst = max(worst, rel)
+            assert rel <= 1e-4, f"resistor {e}: central difference {fd:.9e}, adjoint {gG[e]:.9e} (rel {rel:.2e})"
+        print(f"50 resistors: worst relative difference {worst:.2e}")
+        del Vp, Vm
+        B.pg_update_values(g.handle, r_g=np.asarray(net.r_g, dtype=np.float64))
+
+        # capacitors: tangent-linear model per capacitor
+        B.pg_reset(g.handle)
+        V = torch.empty((S, n), dtype=torch.float64, device=dev)
+        B.pg_transient(g.handle, h, S, v_all=V)
+        W = torch.empty_like(V)
+        for a in range(0, S, 50):
+            W[a:a + 50] = _dJ_dv(V[a:a + 50], vref, margin)
+        absw = float(W.abs().sum())
+        cnode = np.where(net.c_a >= 0, net.c_a, net.c_b)
+        Ch = torch.tensor(np.bincount(cnode, net.c_val / h, minlength=n), device=dev)
+        tol_s = 1e-10
+        worst = 0.0
+        dv = torch.zeros(n, dtype=torch.float64, device=dev)
+        nxt = torch.empty_like(dv)
+        b = torch.empty_like(dv)
+        for k in pick_c:
+            i, c = int(cnode[k]), float(net.c_val[k])
+            dv.zero_()
+            tl = 0.0
+            for s_ in range(S):
+                # M dv_s = (C/h) dv_(s-1) - (dC/h)(v_s - v_(s-1)), dC = C_k at node i only
+                torch.mul(Ch, dv, out=b)
+                v_prev = V[s_ - 1, i] if s_ > 0 else torch.tensor(vdd, dtype=torch.float64, device=dev)
+                b[i] -= c / h * (V[s_, i] - v_prev)
+                B.pg_solve(g.handle, h, b, nxt, tol_s)
+                tl += float(torch.dot(W[s_], nxt))
+                dv, nxt = nxt, dv
+            ad = c * gC[k]
+            bound = st.kacc * tol_s * absw + 1e-7 * abs(ad)
+            worst = max(worst, abs(tl - ad) / abs(ad))
+            assert abs(tl - ad) <= bound, f"capacitor {k}: tangent linear {tl:.9e}, adjoint {ad:.9e}"
+        print(f"50 capacitors: worst relative difference {worst:.2e}")

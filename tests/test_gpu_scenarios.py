@@ -3,10 +3,11 @@
 Every scenario is one right-hand side of the same backward-Euler system
 (Eq. 2); the launch reads each coefficient once for all of them.  Each
 scenario must match the FP64 oracle's direct solves of its own netlist, node
-by node and step by step, in both precisions and for scenario counts that do
-not fill the last group of four; its worst-drop waveform must equal that of
-the copy-per-scenario batch.  Grids this entry point does not serve are
-refused with PG_ERR_UNSUPPORTED.
+by node and step by step: with the point sweeps in both precisions and with
+the lattice column-block tiles, for scenario counts that do not fill the last
+group of four; its worst-drop waveform must equal that of the
+copy-per-scenario batch.  Grids this entry point does not serve are refused
+with PG_ERR_UNSUPPORTED.
 """
 import numpy as np
 import pytest
@@ -48,16 +49,24 @@ def _with_loads(net, iv):
     return m
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("recipe,n_scen", [("config0_37x29", 6), ("config1_21x17x3", 5), ("config0_20x18", 1)])
-def test_every_scenario_matches_the_oracle(B, recipe, n_scen, precision):
+@pytest.mark.parametrize("solve", ["fp64_point", "mixed_point", "mixed_lattice"])
+@pytest.mark.parametrize("recipe,n_scen", [("config0_37x29", 6), ("config1_21x17x3", 5), ("config0_20x18", 1),
+                                           ("config1_43x39x3", 9)])
+def test_every_scenario_matches_the_oracle(B, recipe, n_scen, solve):
+    """Point sweeps (FP64 or FP32 with FP64 correction) and, on grids built for the
+    lattice inner solve, its column-block tiles with four scenarios per region; the
+    43 x 39 x 3 recipe spans several tiles with a ragged last row and column."""
     net = {"config0_37x29": lambda: pgsynth.config0(nx=37, ny=29),
            "config1_21x17x3": lambda: pgsynth.config1(nx=21, ny=17),
-           "config0_20x18": lambda: pgsynth.config0(nx=20, ny=18)}[recipe]()
+           "config0_20x18": lambda: pgsynth.config0(nx=20, ny=18),
+           "config1_43x39x3": lambda: pgsynth.config1(nx=43, ny=39)}[recipe]()
     h, S = net.meta["h"], 30
     loads = _scenarios(net, n_scen, seed=n_scen)
     iv = torch.tensor(np.stack(loads), device="cuda")
-    with B.Grid(net, precision=precision, lattice_sweeps=-1) as g:
+    opts = {"fp64_point": dict(precision=0, lattice_sweeps=-1), "mixed_point": dict(precision=1, lattice_sweeps=-1),
+            "mixed_lattice": dict(precision=1)}[solve]
+    precision = opts["precision"]
+    with B.Grid(net, **opts) as g:
         B.pg_set_stream(g.handle, torch.cuda.current_stream().cuda_stream)
         V = torch.empty((S, n_scen, net.n_nodes), dtype=torch.float64, device="cuda")
         vmin = torch.empty((S, n_scen), dtype=torch.float64, device="cuda")
@@ -65,6 +74,7 @@ def test_every_scenario_matches_the_oracle(B, recipe, n_scen, precision):
         torch.cuda.synchronize()
         V, vmin = V.cpu().numpy(), vmin.cpu().numpy()
     assert st.steps_done == S and st.failed_step == -1 and st.total_sweeps > 0
+    assert (st.lattice_sweeps > 0) == (solve == "mixed_lattice")
     worst = 0.0
     for k in range(n_scen):
         Vo, _ = transient.transient(_with_loads(net, loads[k]), h, S)
@@ -74,7 +84,7 @@ def test_every_scenario_matches_the_oracle(B, recipe, n_scen, precision):
         assert err <= st.err_bound + 1e-11
         np.testing.assert_array_equal(vmin[:, k], V[:, k].min(axis=1))
     assert st.err_bound <= 0.9 * TOL_V * (1 + 1e-9)
-    print(f"{recipe}, {n_scen} scenarios, precision {precision}: max error {worst:.2e} V, "
+    print(f"{recipe}, {n_scen} scenarios, {solve}: max error {worst:.2e} V, "
           f"bound {st.err_bound:.2e} V, {st.total_sweeps} sweeps")
 
 
@@ -86,9 +96,11 @@ def test_shared_scenarios_match_the_copies(B):
     h, S = net.meta["h"], 40
     loads = _scenarios(net, 9, seed=3)
     shared = batch.solve_scenarios_shared(net, loads, h, S, precision=1)
+    shared_lat = batch.solve_scenarios_shared(net, loads, h, S, precision=1, lattice_sweeps=0)
     copies = batch.solve_scenarios(net, loads, h, S, precision=1)
     assert shared.shape == copies.shape == (S, 9)
     np.testing.assert_allclose(shared, copies, rtol=0, atol=2 * TOL_V)
+    np.testing.assert_allclose(shared_lat, copies, rtol=0, atol=2 * TOL_V)
 
 
 def test_unsupported_grids_are_refused(B):
@@ -100,7 +112,7 @@ def test_unsupported_grids_are_refused(B):
             B.pg_transient_scenarios(g.handle, rlc.meta["h"], 3, iv)
         assert e.value.name == "PG_ERR_UNSUPPORTED"
     rc = pgsynth.config1(nx=12, ny=10)
-    with B.Grid(rc, precision=1) as g:                      # the lattice inner solve
+    with B.Grid(rc, precision=1, tile_rows=66) as g:        # the lattice solve on 66-row regions
         iv = torch.tensor(np.stack([rc.i_v]), device="cuda")
         with pytest.raises(B.PGError) as e:
             B.pg_transient_scenarios(g.handle, rc.meta["h"], 3, iv)

@@ -236,3 +236,34 @@ def test_batched_round(lats_shape, k, converged):
         want = global_sweeps(nx, ny, nl, k, [a[sl].reshape(shape) for a in arrs], d[sl].reshape(shape), 1.3)
         assert np.array_equal(got[sl].reshape(shape), want), f"lattice {L}"
 
+
+
+@pytest.mark.parametrize("tiles,blocks", [(2209, 304), (5, 8), (1, 1), (16, 3), (100, 152)])
+def test_tile_claims_cover_every_round_once(tiles, blocks):
+    """The kernel hands a round's tiles out from one launch-wide counter: each block
+    claims its first tile, then claims the next one while it works on the current one,
+    and stops at its first claim at or past round_base + tiles, with round_base =
+    n (tiles + blocks) for round n (modulo 2^32 like the counter).  Under any order in
+    which the blocks' claims interleave, every tile of every round must be processed
+    exactly once and the counter must stand at (n + 1)(tiles + blocks) after round n."""
+    import random
+    rnd = random.Random(tiles * 31 + blocks)
+    ctr = 0
+    for n in range(6):
+        base = (n * (tiles + blocks)) % 2**32
+        claim = {}
+        for b in rnd.sample(range(blocks), blocks):          # first claims, in any order
+            claim[b] = ctr % 2**32
+            ctr += 1
+        done, active = [], list(range(blocks))
+        while active:
+            b = rnd.choice(active)
+            t = (claim[b] - base) % 2**32
+            if t < tiles:
+                claim[b] = ctr % 2**32
+                ctr += 1
+                done.append(t)
+            else:
+                active.remove(b)
+        assert sorted(done) == list(range(tiles))
+        assert ctr == (n + 1) * (tiles + blocks)
