@@ -120,11 +120,18 @@ pg_status alloc_device(pg_grid* g) {
                     : (g->opt.lattice_sweeps == 0 ? auto_lattice_k(P.lat_maxnl, P.n) : 0);
     std::vector<int32_t> lat_tile0, lat_info;
     std::vector<int64_t> lat_col0;
-    if (g->mixed && P.lattice && lat_k > 0) {
+    // (FP64 grids too, on natural-order packing, with 34-row regions; FP32 copies of the five
+    // arrays serve the omega power iteration)
+    if (P.lattice && lat_k > 0 && (g->mixed || d.natural)) {
         g->lat_k = lat_k;
         float* lw[5];
         for (auto& q : lw) if (!(q = g->alloc<float>(P.n))) return PG_ERR_OOM;
         d.lwE = lw[0]; d.lwN = lw[1]; d.lwU = lw[2]; d.lm = lw[3]; d.lip = lw[4];
+        if (!g->mixed) {
+            double* lw64[5];
+            for (auto& q : lw64) if (!(q = g->alloc<double>(P.n))) return PG_ERR_OOM;
+            d.lwE64 = lw64[0]; d.lwN64 = lw64[1]; d.lwU64 = lw64[2]; d.lm64 = lw64[3]; d.lip64 = lw64[4];
+        }
         // tiles of T x TY interior columns per lattice, and columns per lattice
         const int rows = g->opt.tile_rows > 0 ? g->opt.tile_rows : kLatSide;
         const int nlat = (int)P.lats.size() / 4, T = lattice_tile_side(lat_k), TY = lattice_tile_rows(lat_k, rows);
@@ -236,7 +243,7 @@ pg_status alloc_device(pg_grid* g) {
     if (!g->d_x) return PG_ERR_OOM;
 
     // launch shape: every warp gets the same number of slices per colour sweep
-    g->smem = persistent_smem_bytes(g->mixed, d.lat_rows, d.lwE ? P.lat_maxnl : 0);
+    g->smem = persistent_smem_bytes(g->mixed, d.lat_rows, d.lwE ? P.lat_maxnl : 0);   // FP64: 8-byte elements
     int bps = 0;
     CK(persistent_occupancy(g->mixed, d.lat_rows, g->threads, g->smem, &bps));
     if (g->opt.blocks_per_sm > 0) bps = std::min(bps, g->opt.blocks_per_sm);
@@ -296,12 +303,12 @@ pg_status assemble_h(pg_grid* g, double h) {
     if (g->dg.lwE) {
         // lattice form of the FP32 inner solve: each branch weight once, caller order
         std::vector<float> e(P.n, 0.f), nn(P.n, 0.f), u(P.n, 0.f), mm(P.n, 0.f), ip(P.n, 0.f);
-        std::vector<double> u64(P.n, 0.0);
+        std::vector<double> u64(P.n, 0.0), e64(P.n, 0.0), n64(P.n, 0.0), m64(P.n, 0.0), ip64(P.n, 0.0);
         for (int o = 0; o < P.n; ++o) {
             for (int64_t a = P.adj_ptr[o]; a < P.adj_ptr[o + 1]; ++a) {
                 const double w = P.adj_g[a] + h * P.adj_il[a];
-                if (P.adj_dir[a] == 0) e[o] = (float)w;
-                else if (P.adj_dir[a] == 1) nn[o] = (float)w;
+                if (P.adj_dir[a] == 0) { e[o] = (float)w; e64[o] = w; }
+                else if (P.adj_dir[a] == 1) { nn[o] = (float)w; n64[o] = w; }
                 else if (P.adj_dir[a] == 2) { u[o] = (float)w; u64[o] = w; }
             }
         }
@@ -317,8 +324,10 @@ pg_status assemble_h(pg_grid* g, double h) {
                     const double m = u64[o - plane] / dp_prev;
                     dp -= m * u64[o - plane];
                     mm[o] = (float)m;
+                    m64[o] = m;
                 }
                 ip[o] = (float)(1.0 / dp);
+                ip64[o] = 1.0 / dp;
                 dp_prev = dp;
             }
           }
@@ -326,6 +335,13 @@ pg_status assemble_h(pg_grid* g, double h) {
         if ((s = upload(g, const_cast<float*>(g->dg.lwE), e)) || (s = upload(g, const_cast<float*>(g->dg.lwN), nn)) ||
             (s = upload(g, const_cast<float*>(g->dg.lwU), u)) || (s = upload(g, const_cast<float*>(g->dg.lm), mm)) ||
             (s = upload(g, const_cast<float*>(g->dg.lip), ip)))
+            return s;
+        if (g->dg.lwE64 &&
+            ((s = upload(g, const_cast<double*>(g->dg.lwE64), e64)) ||
+             (s = upload(g, const_cast<double*>(g->dg.lwN64), n64)) ||
+             (s = upload(g, const_cast<double*>(g->dg.lwU64), u64)) ||
+             (s = upload(g, const_cast<double*>(g->dg.lm64), m64)) ||
+             (s = upload(g, const_cast<double*>(g->dg.lip64), ip64))))
             return s;
     }
     if (g->mixed) {
@@ -758,6 +774,10 @@ pg_status create_impl(const pg_netlist* nl, const pg_options* opt, std::unique_p
         g_last_error = "tile_rows must be 0, 34 or 66";
         return PG_ERR_INVALID_ARG;
     }
+    if (o.tile_rows == 66 && o.precision != PG_PREC_MIXED) {
+        g_last_error = "tile_rows 66 needs mixed precision (the FP64 lattice solve takes 34-row regions)";
+        return PG_ERR_INVALID_ARG;
+    }
     if (o.form != PG_FORM_EXPLICIT && o.form != PG_FORM_THREE_LEVEL) {
         g_last_error = "form must be PG_FORM_EXPLICIT or PG_FORM_THREE_LEVEL";
         return PG_ERR_INVALID_ARG;
@@ -765,7 +785,7 @@ pg_status create_impl(const pg_netlist* nl, const pg_options* opt, std::unique_p
     g->threads = o.threads_per_block;
     g->mixed = o.precision == PG_PREC_MIXED;
     std::string why;
-    pg_status s = build_packed(nl, &g->P, &why, g->mixed && !o.jacobi ? o.lattice_sweeps : INT32_MIN, o.colouring);
+    pg_status s = build_packed(nl, &g->P, &why, !o.jacobi ? o.lattice_sweeps : INT32_MIN, o.colouring);
     if (s) { g_last_error = why; return s; }
     g->nc.from(nl);
     compute_dc_trivial(g.get());

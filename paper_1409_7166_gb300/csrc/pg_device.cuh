@@ -245,6 +245,16 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src, unsigned s
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
                  : "memory");
 }
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, unsigned src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+// One element (4 or 8 bytes) or a 16-byte piece.
+template <typename V>
+__device__ __forceinline__ void cp_async_elem(V* dst, const V* src, bool in) {
+    if constexpr (sizeof(V) == 8) cp_async8(dst, src, in ? 8u : 0u);
+    else cp_async4(dst, src, in ? 4u : 0u);
+}
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }

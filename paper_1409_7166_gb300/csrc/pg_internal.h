@@ -96,8 +96,11 @@ constexpr int kLatW = 36;                          // shared-memory row stride (
 constexpr int kLatArrays = 7;                      // delta, r, wE, wN, wU, Thomas m, 1/pivot
 inline int lattice_tile_side(int k) { return kLatSide - 4 * k; }
 inline int lattice_tile_rows(int k, int rows) { return rows - 4 * k; }
-// Dynamic shared memory of one lattice region: kLatArrays arrays of nl layers of rows x kLatW.
-inline size_t lattice_region_bytes(int rows, int nl) { return (size_t)kLatArrays * nl * rows * kLatW * sizeof(float); }
+// Dynamic shared memory of one lattice region: kLatArrays arrays of nl layers of rows x kLatW
+// elements of elem bytes (4 in mixed precision, 8 for the FP64 lattice solve).
+inline size_t lattice_region_bytes(int rows, int nl, size_t elem = sizeof(float)) {
+    return (size_t)kLatArrays * nl * rows * kLatW * elem;
+}
 // Refill the value-dependent parts of a packed grid (merged weights, grounded
 // parts, capacitances, 1/L) from a netlist with the same topology.
 pg_status refill_values(const pg_netlist* nl, Packed* P, std::string* why);
@@ -157,6 +160,12 @@ struct DevGrid {
     const float* lwU;        // weight to (x, y, l+1)
     const float* lm;         // column block (via couplings): Thomas multiplier u_{l-1} / d'_{l-1} (0 for l = 0)
     const float* lip;        // column block: inverse Thomas pivot 1 / d'_l
+    // the same five arrays in FP64, for the FP64 lattice inner solve (null in mixed precision)
+    const double* lwE64;
+    const double* lwN64;
+    const double* lwU64;
+    const double* lm64;
+    const double* lip64;
     int32_t lat_rows;        // region rows of the lattice solve (34 or 66)
     int32_t lat_astride;     // floats per staged array in shared memory: max layers x rows x kLatW
     int32_t natural;         // 1: the permutation is the identity on the real nodes (padding after them)

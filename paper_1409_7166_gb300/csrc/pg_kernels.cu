@@ -590,48 +590,54 @@ static_assert(kLatSide - 2 == 32, "the first half-sweep covers 32 columns, 16 pa
 // One tile (region of lattice L): load, 2k half-sweeps, store the interior.
 // Returns the max unrelaxed column update of the last sweep over the interior.
 // NL (layers) is a template parameter: the column solve unrolls completely.
-template <int NL, int ROWS>
-__device__ float lattice_tile(const DevGrid& g, int off, int nx, int ny, int tile, const float* __restrict__ dold,
-                              float* __restrict__ dnew, const float* __restrict__ r, float omega, int k,
-                              unsigned char* smem) {
-    constexpr int kLatPlane = ROWS * kLatW;           // floats per layer of a staged array
+// V: float (the mixed-precision inner solve on the correction) or double (the FP64 one;
+// every staged array in FP64, twice the shared memory).
+template <int NL, int ROWS, typename V>
+__device__ V lattice_tile(const DevGrid& g, int off, int nx, int ny, int tile, const V* __restrict__ dold,
+                          V* __restrict__ dnew, const V* __restrict__ r, V omega, int k, unsigned char* smem) {
+    constexpr int kLatPlane = ROWS * kLatW;           // elements per layer of a staged array
     constexpr int J = (ROWS - 2) / 16;                // rows per thread in a half-sweep
+    constexpr int kEl = 16 / (int)sizeof(V);          // elements per 16-byte piece
     static_assert(ROWS == 34 || ROWS == 66, "regions of 34 or 66 rows");
     const int H = 2 * k, T = kLatSide - 2 * H, TY = ROWS - 2 * H;
     const int tiles_x = (nx + T - 1) / T;
-    const int A = g.lat_astride;                      // floats per array
-    float* sd = reinterpret_cast<float*>(smem);
-    float* sr = sd + A;
-    float* se = sd + 2 * A;
-    float* sn = sd + 3 * A;
-    float* su = sd + 4 * A;
-    float* sm = sd + 5 * A;
-    float* sp = sd + 6 * A;
+    const int A = g.lat_astride;                      // elements per array
+    V* sd = reinterpret_cast<V*>(smem);
+    V* sr = sd + A;
+    V* se = sd + 2 * A;
+    V* sn = sd + 3 * A;
+    V* su = sd + 4 * A;
+    V* sm = sd + 5 * A;
+    V* sp = sd + 6 * A;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int pair = lane & 15;                        // columns 2 pair, 2 pair + 1 of the slot grid
     const int rsub = lane >> 4;                        // half-warps take adjacent rows (no bank conflicts)
     const long long plane = (long long)nx * ny;
     // region: columns [x0, x0 + 34), rows [y0, y0 + 34); shared column c holds x0 - lead + c
     const int x0 = (tile % tiles_x) * T - H, y0 = (tile / tiles_x) * TY - H;
-    const int lead = x0 & 3;                           // 0 or 2: x0 is even
+    const int lead = x0 & (kEl - 1);                   // FP32: 0 or 2 (x0 is even); FP64: 0
     const int xa = x0 - lead;
-    auto src_of = [&](int arr) -> const float* {       // by value: no local array
-        return arr == 0 ? dold : arr == 1 ? r : arr == 2 ? g.lwE : arr == 3 ? g.lwN : arr == 4 ? g.lwU
-             : arr == 5 ? g.lm : g.lip;
+    auto src_of = [&](int arr) -> const V* {           // by value: no local array
+        if constexpr (sizeof(V) == 8)
+            return arr == 0 ? dold : arr == 1 ? r : arr == 2 ? g.lwE64 : arr == 3 ? g.lwN64 : arr == 4 ? g.lwU64
+                 : arr == 5 ? g.lm64 : g.lip64;
+        else
+            return arr == 0 ? dold : arr == 1 ? r : arr == 2 ? g.lwE : arr == 3 ? g.lwN : arr == 4 ? g.lwU
+                 : arr == 5 ? g.lm : g.lip;
     };
-    if ((nx & 3) == 0 && (off & 3) == 0) {
-        // rows of 16-byte pieces: a piece (xa + 4c, ..., +3) is wholly inside the lattice or
+    if ((nx & (kEl - 1)) == 0 && (off & (kEl - 1)) == 0) {
+        // rows of 16-byte pieces: a piece (xa + kEl c, ...) is wholly inside the lattice or
         // wholly outside; the (piece, array) pairs are spread over the threads
-        constexpr int kChunks = kLatW / 4;
+        constexpr int kChunks = kLatW / kEl;
         constexpr int kPieces = ROWS * kChunks;
         for (int q = threadIdx.x; q < kPieces * kLatArrays; q += blockDim.x) {
             const int arr = q / kPieces, pos = q - arr * kPieces;
-            const int ry = pos / kChunks, c4 = 4 * (pos - ry * kChunks);
+            const int ry = pos / kChunks, c4 = kEl * (pos - ry * kChunks);
             const int xx = xa + c4, yy = y0 + ry;
             const bool in = yy >= 0 && yy < ny && xx >= 0 && xx < nx;
             const long long o = in ? off + (long long)yy * nx + xx : 0;
-            const float* src = src_of(arr);
-            float* dst = sd + arr * A + ry * kLatW + c4;
+            const V* src = src_of(arr);
+            V* dst = sd + arr * A + ry * kLatW + c4;
 #pragma unroll
             for (int l = 0; l < NL; ++l)
                 cp_async16(dst + l * kLatPlane, src + (in ? o + l * plane : 0), in ? 16u : 0u);
@@ -646,12 +652,12 @@ __device__ float lattice_tile(const DevGrid& g, int off, int nx, int ny, int til
             for (int arr = 0; arr < kLatArrays; ++arr)
 #pragma unroll
                 for (int l = 0; l < NL; ++l)
-                    cp_async4(sd + arr * A + l * kLatPlane + q, src_of(arr) + (in ? o + l * plane : 0), in ? 4u : 0u);
+                    cp_async_elem<V>(sd + arr * A + l * kLatPlane + q, src_of(arr) + (in ? o + l * plane : 0), in);
         }
     }
     cp_async_wait_all();
     __syncthreads();
-    float mon = 0.f;
+    V mon = V(0);
     for (int hs = 0; hs < 2 * k; ++hs) {
         const bool last = hs >= 2 * k - 2;
 #pragma unroll
@@ -664,7 +670,7 @@ __device__ float lattice_tile(const DevGrid& g, int off, int nx, int ny, int til
             // would change nearer the edge cannot reach the interior by the last one
             if (edge <= hs || x < 0 || x >= nx || y < 0 || y >= ny) continue;
             const int a0 = ry * kLatW + cx + lead;
-            float f[NL], xv[NL];
+            V f[NL], xv[NL];
 #pragma unroll
             for (int l = 0; l < NL; ++l) {
                 const int a = a0 + l * kLatPlane;
@@ -672,19 +678,19 @@ __device__ float lattice_tile(const DevGrid& g, int off, int nx, int ny, int til
                        sn[a - kLatW] * sd[a - kLatW];
             }
 #pragma unroll
-            for (int l = 1; l < NL; ++l) f[l] = fmaf(sm[a0 + l * kLatPlane], f[l - 1], f[l]);
+            for (int l = 1; l < NL; ++l) f[l] = fma(sm[a0 + l * kLatPlane], f[l - 1], f[l]);
             xv[NL - 1] = f[NL - 1] * sp[a0 + (NL - 1) * kLatPlane];
 #pragma unroll
             for (int l = NL - 2; l >= 0; --l)
-                xv[l] = fmaf(su[a0 + l * kLatPlane], xv[l + 1], f[l]) * sp[a0 + l * kLatPlane];
+                xv[l] = fma(su[a0 + l * kLatPlane], xv[l + 1], f[l]) * sp[a0 + l * kLatPlane];
             const bool interior = edge >= H;
 #pragma unroll
             for (int l = 0; l < NL; ++l) {
                 const int a = a0 + l * kLatPlane;
-                const float dv = sd[a];
-                const float upd = xv[l] - dv;
-                sd[a] = fmaf(omega, upd, dv);
-                if (last && interior) mon = nanmaxf(mon, fabsf(upd));
+                const V dv = sd[a];
+                const V upd = xv[l] - dv;
+                sd[a] = fma(omega, upd, dv);
+                if (last && interior) mon = nanmax_t<V>(mon, fabs(upd));
             }
         }
         __syncthreads();
@@ -708,8 +714,8 @@ __device__ float lattice_tile(const DevGrid& g, int off, int nx, int ny, int til
 // must stay zero in both buffers, which the start buffer is (zeroed by the FP64
 // pass) and which the first round of the inner solve (`first`) writes into the
 // other one; later rounds skip those tiles entirely.
-template <int ROWS>
-__device__ double lattice_round(const DevGrid& g, const float* dold, float* dnew, const float* r, float omega,
+template <int ROWS, typename V>
+__device__ double lattice_round(const DevGrid& g, const V* dold, V* dnew, const V* r, V omega,
                                 int k, unsigned char* smem, const unsigned long long* latR, double target,
                                 bool first, unsigned* tile_ctr, unsigned round_base) {
     // Tiles are handed out from a launch-wide counter, so a block that finishes early takes
@@ -725,7 +731,7 @@ __device__ double lattice_round(const DevGrid& g, const float* dold, float* dnew
     const unsigned T = (unsigned)g.lat_tiles;
     unsigned claim = 0;
     if (threadIdx.x == 0) claim = atomicAdd(tile_ctr, 1u);
-    float mon = 0.f;
+    V mon = V(0);
     for (;;) {
         if (threadIdx.x == 0) {
             const unsigned t = claim - round_base;
@@ -754,16 +760,16 @@ __device__ double lattice_round(const DevGrid& g, const float* dold, float* dnew
                 for (int q = threadIdx.x; q < T * TY; q += blockDim.x) {
                     const int x = tx0 + q % T, y = ty0 + q / T;
                     if (x >= nx || y >= ny) continue;
-                    for (int l = 0; l < nl; ++l) dnew[off + l * plane + (long long)y * nx + x] = 0.f;
+                    for (int l = 0; l < nl; ++l) dnew[off + l * plane + (long long)y * nx + x] = V(0);
                 }
             }
             continue;
         }
-        float m;
-        if (nl == 1) m = lattice_tile<1, ROWS>(g, off, nx, ny, tile, dold, dnew, r, omega, k, smem);
-        else if (nl == 2) m = lattice_tile<2, ROWS>(g, off, nx, ny, tile, dold, dnew, r, omega, k, smem);
-        else m = lattice_tile<3, ROWS>(g, off, nx, ny, tile, dold, dnew, r, omega, k, smem);
-        mon = nanmaxf(mon, m);
+        V m;
+        if (nl == 1) m = lattice_tile<1, ROWS, V>(g, off, nx, ny, tile, dold, dnew, r, omega, k, smem);
+        else if (nl == 2) m = lattice_tile<2, ROWS, V>(g, off, nx, ny, tile, dold, dnew, r, omega, k, smem);
+        else m = lattice_tile<3, ROWS, V>(g, off, nx, ny, tile, dold, dnew, r, omega, k, smem);
+        mon = nanmax_t<V>(mon, m);
     }
     return (double)mon;
 }
@@ -998,7 +1004,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
     unsigned lat_rounds = 0;     // lattice rounds run in this launch (the same in every block), modulo 2^32
     // per-lattice residual maxima (lattice inner solve): two buffers, `lat_par` is the one
     // the latest FP64 pass wrote; the host clears both before the launch
-    const bool per_lat = MIXED && rp.lat_k > 0 && ctl.lat_R != nullptr;
+    const bool per_lat = rp.lat_k > 0 && ctl.lat_R != nullptr;
     int lat_par = 0;
     auto lat_buf = [&](int b) { return per_lat ? ctl.lat_R + (size_t)b * g.n_lats : nullptr; };
     auto lat_clear = [&](int b) {
@@ -1139,11 +1145,12 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
             bool est_nan = false;         // a non-finite update (diverged, or a failed copy)
             int inner = 0;
             lat_clear(lat_par ^ 1);       // the next FP64 pass writes there; its readers are done
-            while (MIXED && rp.lat_k > 0) {
-                // lattice rounds: lat_k exact block sweeps per device barrier
-                const float* dold = dbuf<float>(st, dsel);
-                float* dnew = dbuf<float>(st, dsel ^ 1);
-                const double m = lattice_round<ROWS>(g, dold, dnew, st.r32, (float)omega, rp.lat_k, s_dyn,
+            while (rp.lat_k > 0) {
+                // lattice rounds: lat_k exact block sweeps per device barrier (FP32, or FP64 in
+                // the FP64 kernel)
+                const T* dold = dbuf<T>(st, dsel);
+                T* dnew = dbuf<T>(st, dsel ^ 1);
+                const double m = lattice_round<ROWS, T>(g, dold, dnew, rr, omega, rp.lat_k, s_dyn,
                                                lat_buf(lat_par), target, inner == 0, ctl.tile_ctr,
                                                lat_rounds * ((unsigned)g.lat_tiles + nblocks));
                 ++lat_rounds;
@@ -1151,7 +1158,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
                 if (!be.ok) { publish(-1); return; }
                 const double est = be.val;
                 dsel ^= 1;
-                dd = (T*)dbuf<float>(st, dsel);
+                dd = dbuf<T>(st, dsel);
                 const int before = inner;
                 sweeps += rp.lat_k;
                 inner += rp.lat_k;
@@ -1187,7 +1194,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
                     est_mark = est;
                 }
             }
-            while (!rp.jacobi && !(MIXED && rp.lat_k > 0)) {
+            while (!rp.jacobi && !(rp.lat_k > 0)) {
                 double est = 0.0;
                 for (int c = 0; c < g.ncol; ++c) {
                     double m = 0.0;
@@ -1588,8 +1595,9 @@ __global__ void __launch_bounds__(256) adjoint_lgrad_kernel(DevGrid g, const dou
 
 size_t persistent_smem_bytes(bool mixed, int rows, int nl) {
     const size_t stages = (size_t)kWarpsPerBlock * tma_warp_bytes(sizeof(float));
+    if (!mixed) return nl > 0 ? lattice_region_bytes(rows, nl, sizeof(double)) : 0;   // FP64 lattice region
     const size_t region = nl > 0 ? lattice_region_bytes(rows, nl) : 0;
-    return mixed ? std::max(stages, region) : 0;
+    return std::max(stages, region);
 }
 
 static const void* persistent_fn(bool mixed, int rows) {

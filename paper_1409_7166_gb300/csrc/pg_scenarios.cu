@@ -634,6 +634,9 @@ extern "C" pg_status pg_transient_scenarios(pg_grid* g, double h, int32_t nsteps
     if (!g || nsteps < 1 || n_scen < 1 || !i_v) return fail(PG_ERR_INVALID_ARG, "null grid or values, or no steps");
     if (g->P.n_l > 0) return fail(PG_ERR_UNSUPPORTED, "load scenarios run on RC grids (no inductors)");
     if (g->opt.form != PG_FORM_EXPLICIT) return fail(PG_ERR_UNSUPPORTED, "load scenarios need the explicit form");
+    if (g->dg.lwE && !g->mixed)
+        return fail(PG_ERR_UNSUPPORTED,
+                    "load scenarios in FP64 run on the point inner solve (create the grid with lattice_sweeps = -1)");
     if (g->dg.lwE && g->dg.lat_rows != kLatSide)
         return fail(PG_ERR_UNSUPPORTED, "load scenarios on the lattice inner solve take 34-row regions (tile_rows 0 or 34)");
     const NetCopy& nc = g->nc;

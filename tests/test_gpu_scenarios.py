@@ -117,6 +117,13 @@ def test_unsupported_grids_are_refused(B):
         with pytest.raises(B.PGError) as e:
             B.pg_transient_scenarios(g.handle, rc.meta["h"], 3, iv)
         assert e.value.name == "PG_ERR_UNSUPPORTED"
+    with B.Grid(rc, precision=0, lattice_sweeps=3) as g:    # FP64 on the lattice inner solve
+        assert B.pg_transient(g.handle, rc.meta["h"], 1).lattice_sweeps == 3
+        B.pg_reset(g.handle)
+        iv = torch.tensor(np.stack([rc.i_v]), device="cuda")
+        with pytest.raises(B.PGError) as e:
+            B.pg_transient_scenarios(g.handle, rc.meta["h"], 3, iv)
+        assert e.value.name == "PG_ERR_UNSUPPORTED"
     with B.Grid(rc, precision=1, lattice_sweeps=-1) as g:  # loads on at t = 0: no v = Vdd start
         bad = np.asarray(rc.i_v).copy()
         bad[rc.i_ptr[0]] = 1e-3
