@@ -430,6 +430,9 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -551,6 +554,113 @@ __device__ double sweep_colour_tma(const DevGrid& g, const WarpCache* wc, TmaWar
         cur_t = nxt_t;
     }
     return mon;
+}
+
+// ---- TMA-fed step start (incremental explicit step, FP32 inner solve)
+//
+// Phase A of an incremental step (RC, explicit form, mixed precision, corrections in
+// the packing order) streams its operands: no neighbour is read.  The warp walks its
+// nodes in chunks of kRhsChunk; the Tensor Memory Accelerator copies the contiguous
+// operands of chunk j + 1 (v(s-1), v(s-2), C/h, both load slots, the carried residual
+// and M (v(s-1) - v(s-2)) in FP64, 1/D in FP32) into one stage of the warp's TMA area
+// while chunk j is computed from the other, so the FP64 arithmetic of one chunk
+// overlaps the memory traffic of the next.  Each node takes exactly the operations of
+// phase_rhs's incremental branch, so the results are bit-identical.
+constexpr int kRhsChunk = 64;
+constexpr int kRhsArrays = 7;                                   // FP64 operands per node
+constexpr int kRhsStageBytes = kRhsChunk * (8 * kRhsArrays + 4);
+static_assert(kRhsStageBytes <= kStageElems * 4, "a step-start chunk fits one TMA stage");
+
+__device__ __forceinline__ double phase_rhs_inc_tma(const DevGrid& g, const WarpCache* wc, TmaWarp& tw,
+                                                    const DevState& st, int lane, int vL, int vP, int vF,
+                                                    bool extrap, long long sabs, int dsel, float th, int* err,
+                                                    long long timeout_ns) {
+    const double* vl = vbuf(st, vL);
+    const double* vp = vbuf(st, vP);
+    double* vf = vbuf(st, vF);
+    const double* Ic = st.inode + (sabs & 1) * (long long)g.n_pad;
+    const double* Ip = st.inode + ((sabs - 1) & 1) * (long long)g.n_pad;
+    float* dz = dbuf<float>(st, dsel);
+    constexpr unsigned kB8 = kRhsChunk * 8, kB4 = kRhsChunk * 4;
+    const unsigned bytes = kB8 * (extrap ? 7u : 6u) + kB4;
+    auto issue = [&](long long n0, int sb) {
+        unsigned char* buf = sb ? tw.stage[1] : tw.stage[0];   // no dynamic index: tw stays in registers
+        unsigned long long* bar = tw.bar + sb;
+        mbar_expect_tx(bar, bytes);
+        bulk_g2s(buf + 0 * kB8, vl + n0, kB8, bar);
+        bulk_g2s(buf + 1 * kB8, vp + n0, kB8, bar);
+        bulk_g2s(buf + 2 * kB8, g.ch + n0, kB8, bar);
+        bulk_g2s(buf + 3 * kB8, Ic + n0, kB8, bar);
+        bulk_g2s(buf + 4 * kB8, Ip + n0, kB8, bar);
+        bulk_g2s(buf + 5 * kB8, st.r64 + n0, kB8, bar);
+        if (extrap) bulk_g2s(buf + 6 * kB8, st.md + n0, kB8, bar);
+        bulk_g2s(buf + 7 * kB8, g.invD32 + n0, kB4, bar);
+    };
+    float mon = 0.f;
+    for (int c = 0; c < g.ncol; ++c) {
+        const int cnt = wc->cnt[c];
+        if (cnt == 0) continue;
+        const long long node0 = (long long)wc->lo[c] * kSlice;
+        const int n = cnt * (kSlice / kRhsChunk);
+        if (lane == 0) {
+            fence_proxy_async_global();
+            issue(node0, 0);
+        }
+        unsigned pending = 1u;
+        for (int j = 0; j < n; ++j) {
+            const int sb = j & 1;
+            if (j + 1 < n) {
+                if (lane == 0) issue(node0 + (long long)(j + 1) * kRhsChunk, sb ^ 1);
+                pending |= 1u << (sb ^ 1);
+            }
+            if (!mbar_wait(tw.bar + sb, (tw.parity >> sb) & 1u, timeout_ns)) {
+                if (lane == 0) atomicCAS(err, 0, (int)PG_ERR_TIMEOUT);
+                for (int b = 0; b < 2; ++b)   // let every copy still in flight land
+                    if ((pending >> b) & 1u) mbar_wait(tw.bar + b, (tw.parity >> b) & 1u, timeout_ns);
+                __syncwarp();
+                return __longlong_as_double(0x7ff8000000000000ll);
+            }
+            tw.parity ^= 1u << sb;
+            pending &= ~(1u << sb);
+            const unsigned char* buf = sb ? tw.stage[1] : tw.stage[0];
+            const int q = 2 * lane;                               // this lane's two nodes of the chunk
+            const long long i = node0 + (long long)j * kRhsChunk + q;
+            const double2 a = *reinterpret_cast<const double2*>(buf + 0 * kB8 + q * 8);
+            const double2 pp = *reinterpret_cast<const double2*>(buf + 1 * kB8 + q * 8);
+            const double2 ch = *reinterpret_cast<const double2*>(buf + 2 * kB8 + q * 8);
+            const double2 ic = *reinterpret_cast<const double2*>(buf + 3 * kB8 + q * 8);
+            const double2 ip = *reinterpret_cast<const double2*>(buf + 4 * kB8 + q * 8);
+            const double2 rr = *reinterpret_cast<const double2*>(buf + 5 * kB8 + q * 8);
+            double2 md = make_double2(0.0, 0.0);
+            if (extrap) md = *reinterpret_cast<const double2*>(buf + 6 * kB8 + q * 8);
+            const float2 iD = *reinterpret_cast<const float2*>(buf + 7 * kB8 + q * 4);
+            if (extrap && th != 1.0f) {
+                md.x *= th;
+                md.y *= th;
+            }
+            // the incremental branch of phase_rhs, node by node
+            auto node = [&](double av, double pv, double cv, double icv, double ipv, double rv, double mdv,
+                            float iv, double& vw, double& r, float& r32) {
+                vw = extrap ? warm_value(av, pv, th) : av;
+                double bj = cv * (av - pv) - (icv - ipv);
+                bj += rv - mdv;
+                r = bj;
+                r32 = (float)r;
+                mon = nanmax_t<float>(mon, scaled_upper(r32, iv));
+            };
+            double vw0, vw1, r0, r1;
+            float r320, r321;
+            node(a.x, pp.x, ch.x, ic.x, ip.x, rr.x, md.x, iD.x, vw0, r0, r320);
+            node(a.y, pp.y, ch.y, ic.y, ip.y, rr.y, md.y, iD.y, vw1, r1, r321);
+            __syncwarp();   // stage sb is read by every lane before it is refilled
+            if (!extrap || th != 1.0f) *reinterpret_cast<double2*>(st.md + i) = md;
+            *reinterpret_cast<double2*>(vf + i) = make_double2(vw0, vw1);
+            *reinterpret_cast<double2*>(st.r64 + i) = make_double2(r0, r1);
+            *reinterpret_cast<float2*>(st.r32 + i) = make_float2(r320, r321);
+            *reinterpret_cast<float2*>(dz + i) = make_float2(0.f, 0.f);
+        }
+    }
+    return (double)mon;
 }
 
 // ---- lattice inner solve (FP32, ghost zones, column blocks)
@@ -1004,7 +1114,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
     unsigned lat_rounds = 0;     // lattice rounds run in this launch (the same in every block), modulo 2^32
     // per-lattice residual maxima (lattice inner solve): two buffers, `lat_par` is the one
     // the latest FP64 pass wrote; the host clears both before the launch
-    const bool per_lat = rp.lat_k > 0 && ctl.lat_R != nullptr;
+    const bool per_lat = rp.lat_k > 0 && ctl.lat_R != nullptr && g.n_lats > 1;   // one lattice: R says it all
     int lat_par = 0;
     auto lat_buf = [&](int b) { return per_lat ? ctl.lat_R + (size_t)b * g.n_lats : nullptr; };
     auto lat_clear = [&](int b) {
@@ -1105,7 +1215,30 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
                     md_slice(g, wc, warp_desc(g, *wc, c, tt, s), st, s, lane, vlp, vpp, extrap, th);
                 }
         }
-        {
+        // the incremental explicit RC step streams its operands through the TMA
+        const bool staged_rhs = MIXED && inc && !three && rp.mode == kModeTransient && g.n_l == 0 && !per_lat &&
+                                !(rp.lat_k > 0 && !g.natural);
+        if (staged_rhs) {
+            if (rp.lat_k > 0) {
+                // the lattice tiles use this shared memory between step starts: fresh barriers
+                if (lane == 0) {
+                    fence_proxy_async_smem();
+                    mbar_init(tw.bar + 0, 1);
+                    mbar_init(tw.bar + 1, 1);
+                    fence_proxy_async_smem();
+                }
+                tw.parity = 0;
+                __syncwarp();
+            }
+            mon = phase_rhs_inc_tma(g, wc, tw, st, lane, vL, vP, vF, extrap, sabs, dsel, th, ctl.err, rp.timeout_ns);
+            if (rp.lat_k > 0) {
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_inval(tw.bar + 0);
+                    mbar_inval(tw.bar + 1);
+                }
+            }
+        } else {
             LatAccT<T> lacc;
             unsigned long long* lb = lat_buf(lat_par ^ 1);
             for (int c = 0; c < g.ncol; ++c)
