@@ -97,6 +97,8 @@ pg_status alloc_device(pg_grid* g) {
     int64_t* pwl_ptr = g->alloc<int64_t>(P.pwl_ptr.size());
     double* pwl_t = g->alloc<double>(P.pwl_t.size());
     double* pwl_v = g->alloc<double>(P.pwl_v.size());
+    double* pwl_s = g->alloc<double>(P.pwl_s.size());
+    unsigned long long* pwl_tk = g->alloc<unsigned long long>(P.pwl_tk.size());
     int32_t* ind_a = g->alloc<int32_t>(P.n_l);
     int32_t* ind_b = g->alloc<int32_t>(P.n_l);
     double* ind_hl = g->alloc<double>(P.n_l);
@@ -154,12 +156,12 @@ pg_status alloc_device(pg_grid* g) {
         d.lat_col0 = lc; d.lat_cols = lat_col0[nlat]; d.node_lat = nlatv;
     }
     if (!colour_slice || !slice_off || !slice_w || !slice_doff || !dia_off || !ell_col || !orig || !ld_ptr ||
-        !ld_idx || !pwl_ptr || !pwl_t || !pwl_v || !ind_a || !ind_b || !ind_hl || !ind_ptr || !ind_idx || !vdd ||
+        !ld_idx || !pwl_ptr || !pwl_t || !pwl_v || !pwl_s || !pwl_tk || !ind_a || !ind_b || !ind_hl || !ind_ptr || !ind_idx || !vdd ||
         !w64 || !D64 || !invD64 || !ch || !cinj || (g->mixed && (!w32 || !invD32 || !w32lo || !D32 || !D32lo)))
         return PG_ERR_OOM;
     d.colour_slice = colour_slice; d.slice_off = slice_off; d.slice_w = slice_w; d.slice_doff = slice_doff;
     d.dia_off = dia_off; d.ell_col = ell_col; d.orig = orig; d.ld_ptr = ld_ptr; d.ld_idx = ld_idx;
-    d.pwl_ptr = pwl_ptr; d.pwl_t = pwl_t; d.pwl_v = pwl_v; d.n_l = P.n_l; d.ind_a = ind_a; d.ind_b = ind_b;
+    d.pwl_ptr = pwl_ptr; d.pwl_t = pwl_t; d.pwl_v = pwl_v; d.pwl_s = pwl_s; d.pwl_tk = pwl_tk; d.n_l = P.n_l; d.ind_a = ind_a; d.ind_b = ind_b;
     d.ind_hl = ind_hl; d.ind_ptr = ind_ptr; d.ind_idx = ind_idx; d.vdd = vdd;
     d.w64 = w64; d.D64 = D64; d.invD64 = invD64; d.ch = ch; d.cinj = cinj; d.w32 = w32; d.invD32 = invD32;
     d.w32lo = w32lo; d.D32 = D32; d.D32lo = D32lo;
@@ -186,6 +188,7 @@ pg_status alloc_device(pg_grid* g) {
         (s = upload(g, dia_off, P.dia_off)) || (s = upload(g, ell_col, P.ell_col)) || (s = upload(g, orig, P.orig)) ||
         (s = upload(g, ld_ptr, P.ld_ptr)) || (s = upload(g, ld_idx, P.ld_idx)) ||
         (s = upload(g, pwl_ptr, P.pwl_ptr)) || (s = upload(g, pwl_t, P.pwl_t)) || (s = upload(g, pwl_v, P.pwl_v)) ||
+        (s = upload(g, pwl_s, P.pwl_s)) || (s = upload(g, pwl_tk, P.pwl_tk)) ||
         (s = upload(g, ind_a, P.ind_a)) || (s = upload(g, ind_b, P.ind_b)) || (s = upload(g, ind_ptr, P.ind_ptr)) ||
         (s = upload(g, ind_idx, P.ind_idx)) || (s = upload(g, vdd, P.vdd)))
         return s;
@@ -217,7 +220,9 @@ pg_status alloc_device(pg_grid* g) {
         int32_t* sb = g->alloc<int32_t>(nb.size());
         int32_t* mn = g->alloc<int32_t>(std::max<size_t>(multi.size(), 1));
         st.inode = g->alloc<double>(2 * (size_t)np);
-        if (!sa || !sb || !mn || !st.inode) return PG_ERR_OOM;
+        st.pwl_cur = g->alloc<int32_t>(std::max<size_t>(na.size(), 1));
+        if (!sa || !sb || !mn || !st.inode || !st.pwl_cur) return PG_ERR_OOM;
+        CK(cudaMemsetAsync(st.pwl_cur, 0, std::max<size_t>(na.size(), 1) * sizeof(int32_t), g->stream));
         if ((s = upload(g, sa, na)) || (s = upload(g, sb, nb)) || (s = upload(g, mn, multi))) return s;
         CK(cudaMemsetAsync(st.inode, 0, 2 * (size_t)np * sizeof(double), g->stream));
         d.src_na = sa; d.src_nb = sb; d.n_multi = (int32_t)multi.size(); d.multi_node = mn;
@@ -1018,6 +1023,15 @@ pg_status pg_update_sources(pg_grid* g, const double* i_t, const double* i_v, in
                            on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, g->stream));
         g->nc.i_v = v;
     }
+    // the slopes and time keys follow the new breakpoints
+    pwl_aux(g->P.pwl_ptr, t, v, &g->P.pwl_s, &g->P.pwl_tk);
+    g->P.pwl_t = t;
+    g->P.pwl_v = v;
+    CK(cudaMemcpyAsync(const_cast<double*>(g->dg.pwl_s), g->P.pwl_s.data(), m * sizeof(double),
+                       cudaMemcpyHostToDevice, g->stream));
+    CK(cudaMemcpyAsync(const_cast<unsigned long long*>(g->dg.pwl_tk), g->P.pwl_tk.data(),
+                       m * sizeof(unsigned long long), cudaMemcpyHostToDevice, g->stream));
+    CK(cudaStreamSynchronize(g->stream));        // the host vectors are the copies' sources
     compute_dc_trivial(g);
     g->dcgrid.reset();
     return PG_OK;

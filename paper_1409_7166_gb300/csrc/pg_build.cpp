@@ -5,6 +5,7 @@
 // in pg_api.cu from the merged neighbour lists built here.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <numeric>
 #include <string>
 
@@ -30,6 +31,19 @@ struct Dsu {
 inline bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 }  // namespace
+
+void pwl_aux(const std::vector<int64_t>& ptr, const std::vector<double>& t, const std::vector<double>& v,
+             std::vector<double>* slope, std::vector<unsigned long long>* key) {
+    slope->assign(t.size(), 0.0);
+    key->assign(t.size(), 0ull);
+    for (size_t e = 0; e + 1 < ptr.size(); ++e)
+        for (int64_t k = ptr[e]; k < ptr[e + 1]; ++k) {
+            if (k + 1 < ptr[e + 1] && t[k + 1] > t[k]) (*slope)[k] = (v[k + 1] - v[k]) / (t[k + 1] - t[k]);
+            uint64_t b;
+            std::memcpy(&b, &t[k], sizeof b);
+            (*key)[k] = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+        }
+}
 
 pg_status build_packed(const pg_netlist* nl, Packed* P, std::string* why, int32_t lattice_policy, int32_t colouring) {
     auto fail = [&](pg_status s, const std::string& m) { if (why) *why = m; return s; };
@@ -403,8 +417,9 @@ pg_status build_packed(const pg_netlist* nl, Packed* P, std::string* why, int32_
         P->pwl_ptr.assign(nl->i_ptr, nl->i_ptr + nl->n_i + 1);
         P->pwl_t.assign(nl->i_t, nl->i_t + nl->i_ptr[nl->n_i]);
         P->pwl_v.assign(nl->i_v, nl->i_v + nl->i_ptr[nl->n_i]);
+        pwl_aux(P->pwl_ptr, P->pwl_t, P->pwl_v, &P->pwl_s, &P->pwl_tk);
     } else {
-        P->pwl_ptr.assign(1, 0); P->pwl_t.clear(); P->pwl_v.clear();
+        P->pwl_ptr.assign(1, 0); P->pwl_t.clear(); P->pwl_v.clear(); P->pwl_s.clear(); P->pwl_tk.clear();
     }
 
     // --- inductors

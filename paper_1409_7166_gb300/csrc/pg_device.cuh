@@ -203,17 +203,35 @@ __device__ __forceinline__ BarrierResult grid_barrier(const DevCtl& c, unsigned 
 }
 
 // Value of current source e at time t (piecewise linear, held outside the breakpoints).
-__device__ __forceinline__ double pwl_eval(const DevGrid& g, int e, double t) {
+// Value of PWL source e at time t (tk = order_key(t)): held before the first and after
+// the last breakpoint, linear in between.  The segment is found by integer compares of
+// order keys and interpolated with its precomputed slope (no FP64 compare or divide: both
+// issue slowly on GB300's FP64 pipe).
+__device__ __forceinline__ double pwl_eval(const DevGrid& g, int e, double t, unsigned long long tk) {
     int64_t lo = g.pwl_ptr[e], hi = g.pwl_ptr[e + 1] - 1;
-    const double* T = g.pwl_t;
-    const double* V = g.pwl_v;
-    if (t <= T[lo]) return V[lo];
-    if (t > T[hi]) return V[hi];
-    while (hi - lo > 1) {            // keep T[lo] < t <= T[hi]
-        int64_t mid = (lo + hi) >> 1;
-        if (t <= T[mid]) hi = mid; else lo = mid;
+    const unsigned long long* K = g.pwl_tk;
+    if (tk <= K[lo]) return g.pwl_v[lo];
+    if (tk > K[hi]) return g.pwl_v[hi];
+    while (hi - lo > 1) {            // keep t[lo] < t <= t[hi]
+        const int64_t mid = (lo + hi) >> 1;
+        if (tk <= K[mid]) hi = mid; else lo = mid;
     }
-    return V[lo] + (V[hi] - V[lo]) * ((t - T[lo]) / (T[hi] - T[lo]));
+    return fma(g.pwl_s[lo], t - g.pwl_t[lo], g.pwl_v[lo]);
+}
+
+// Value of PWL source e (breakpoints lo..hi) at t when the cursor segment j does not hold
+// it: the search of pwl_eval, also returning the segment (hi past the last breakpoint).
+__device__ __forceinline__ double pwl_eval_search(const DevGrid& g, int64_t lo, int64_t hi, double t,
+                                                  unsigned long long tk, int64_t& j) {
+    const unsigned long long* K = g.pwl_tk;
+    if (tk <= K[lo]) { j = lo; return g.pwl_v[lo]; }
+    if (tk > K[hi]) { j = hi; return g.pwl_v[hi]; }
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (tk <= K[mid]) hi = mid; else lo = mid;
+    }
+    j = lo;
+    return fma(g.pwl_s[lo], t - g.pwl_t[lo], g.pwl_v[lo]);
 }
 
 // Buffer selection by value (no dynamic indexing of kernel-parameter arrays,

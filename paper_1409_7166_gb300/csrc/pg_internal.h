@@ -49,6 +49,8 @@ struct Packed {
     std::vector<int32_t> ld_ptr, ld_idx;
     std::vector<int64_t> pwl_ptr;
     std::vector<double> pwl_t, pwl_v;
+    std::vector<double> pwl_s;              // per-breakpoint segment slopes (pwl_aux)
+    std::vector<unsigned long long> pwl_tk; // order keys of pwl_t (pwl_aux)
 
     // inductors
     int32_t n_l = 0;
@@ -76,6 +78,11 @@ struct Packed {
 // colour: no point sweep runs on them, and the FP64 passes then read the lattice-ordered
 // corrections contiguously.
 // colouring: PG_COLOUR_* (the order of the neighbour-list sweeps).
+// Slopes and time keys of the PWL sources: slope[k] = (v[k+1] - v[k]) / (t[k+1] - t[k]) for a
+// segment of positive width inside one source, else 0; key[k] orders like t[k] (ordering as
+// unsigned integers: sign-magnitude flipped), so the device searches with integer compares.
+void pwl_aux(const std::vector<int64_t>& ptr, const std::vector<double>& t, const std::vector<double>& v,
+             std::vector<double>* slope, std::vector<unsigned long long>* key);
 pg_status build_packed(const pg_netlist* nl, Packed* out, std::string* why, int32_t lattice_policy,
                        int32_t colouring = PG_COLOUR_AUTO);
 
@@ -140,6 +147,8 @@ struct DevGrid {
     const int64_t* pwl_ptr;
     const double* pwl_t;
     const double* pwl_v;
+    const double* pwl_s;                 // slope of the segment that starts at each breakpoint (0 if none)
+    const unsigned long long* pwl_tk;    // order keys of the breakpoint times (integer search)
     int32_t n_l;
     const int32_t* ind_a;
     const int32_t* ind_b;
@@ -189,6 +198,8 @@ struct DevState {
     double* inode;           // [2 x n_pad] total load current drawn from each node, (A_i^T I_s(S h))_i,
                              // slot S & 1 (transient mode); nodes without loads stay 0
     double* md;              // [n_pad] M (v(s) - v(s-1)) by the end of step s (incremental step start)
+    int32_t* pwl_cur;        // [n_src] breakpoint segment of each source's latest evaluation (a hint:
+                             // checked before use, any value is safe)
 };
 
 struct DevCtl {

@@ -1137,18 +1137,51 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
         double* dst = st.inode + (S & 1) * (long long)g.n_pad;
         const double* prev = st.inode + ((S - 1) & 1) * (long long)g.n_pad;
         const double tS = (double)S * rp.h;
+        const unsigned long long tk = order_key(tS);
         bool changed = false;
-        for (int e = gtid; e < g.n_src; e += nthreads) {
-            const int a = __ldg(g.src_na + e), b = __ldg(g.src_nb + e);
-            if (a < 0 && b < 0) continue;
-            const double I = pwl_eval(g, e, tS);
-            if (a >= 0) {
-                if (flag) changed |= I != prev[a];
-                dst[a] = I;
+        // kQ sources per thread at once, so their load chains overlap; each starts from the
+        // segment of its previous evaluation (time moves forward, so that segment, or the
+        // holds before the first and after the last breakpoint, almost always holds t)
+        constexpr int kQ = 2;
+        for (int e0 = gtid; e0 < g.n_src; e0 += kQ * nthreads) {
+            int a[kQ], b[kQ];
+            int lo[kQ], hi[kQ], j[kQ];          // breakpoint indices (the host keeps them below 2^31)
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                const int e = e0 + q * nthreads;
+                const bool ok = e < g.n_src;
+                a[q] = ok ? __ldg(g.src_na + e) : -1;
+                b[q] = ok ? __ldg(g.src_nb + e) : -1;
+                lo[q] = ok ? (int)__ldg(g.pwl_ptr + e) : 0;
+                hi[q] = ok ? (int)__ldg(g.pwl_ptr + e + 1) - 1 : 0;
+                j[q] = ok ? st.pwl_cur[e] : 0;
             }
-            if (b >= 0) {
-                if (flag) changed |= -I != prev[b];
-                dst[b] = -I;
+            double I[kQ];
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                const int jj = min(max(j[q], lo[q]), hi[q]);
+                const int j1 = min(jj + 1, hi[q]);
+                const unsigned long long k0 = __ldg(g.pwl_tk + jj), k1 = __ldg(g.pwl_tk + j1);
+                const double s0 = __ldg(g.pwl_s + jj), t0 = __ldg(g.pwl_t + jj), v0 = __ldg(g.pwl_v + jj);
+                if (jj < hi[q] && k0 < tk && tk <= k1) I[q] = fma(s0, tS - t0, v0);
+                else if ((jj == hi[q] && tk > k0) || (jj == lo[q] && tk <= k0)) I[q] = v0;
+                else {
+                    int64_t jn;
+                    I[q] = pwl_eval_search(g, lo[q], hi[q], tS, tk, jn);
+                    const int e = e0 + q * nthreads;
+                    if (e < g.n_src) st.pwl_cur[e] = (int32_t)jn;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                if (a[q] >= 0) {
+                    if (flag) changed |= I[q] != prev[a[q]];
+                    dst[a[q]] = I[q];
+                }
+                if (b[q] >= 0) {
+                    if (flag) changed |= -I[q] != prev[b[q]];
+                    dst[b[q]] = -I[q];
+                }
             }
         }
         for (int k = gtid; k < g.n_multi; k += nthreads) {
@@ -1156,7 +1189,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
             double sum = 0.0;
             for (int q = __ldg(g.ld_ptr + i); q < __ldg(g.ld_ptr + i + 1); ++q) {
                 const int sid = __ldg(g.ld_idx + q);
-                const double I = pwl_eval(g, (sid > 0 ? sid : -sid) - 1, tS);
+                const double I = pwl_eval(g, (sid > 0 ? sid : -sid) - 1, tS, tk);
                 sum += sid > 0 ? I : -I;
             }
             if (flag) changed |= sum != prev[i];
