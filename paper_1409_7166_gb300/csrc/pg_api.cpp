@@ -221,7 +221,9 @@ pg_status alloc_device(pg_grid* g) {
         int32_t* mn = g->alloc<int32_t>(std::max<size_t>(multi.size(), 1));
         st.inode = g->alloc<double>(2 * (size_t)np);
         st.pwl_cur = g->alloc<int32_t>(std::max<size_t>(na.size(), 1));
-        if (!sa || !sb || !mn || !st.inode || !st.pwl_cur) return PG_ERR_OOM;
+        st.dinode = g->alloc<double>(np);
+        if (!sa || !sb || !mn || !st.inode || !st.pwl_cur || !st.dinode) return PG_ERR_OOM;
+        CK(cudaMemsetAsync(st.dinode, 0, (size_t)np * sizeof(double), g->stream));
         CK(cudaMemsetAsync(st.pwl_cur, 0, std::max<size_t>(na.size(), 1) * sizeof(int32_t), g->stream));
         if ((s = upload(g, sa, na)) || (s = upload(g, sb, nb)) || (s = upload(g, mn, multi))) return s;
         CK(cudaMemsetAsync(st.inode, 0, 2 * (size_t)np * sizeof(double), g->stream));

@@ -198,6 +198,8 @@ struct DevState {
     double* inode;           // [2 x n_pad] total load current drawn from each node, (A_i^T I_s(S h))_i,
                              // slot S & 1 (transient mode); nodes without loads stay 0
     double* md;              // [n_pad] M (v(s) - v(s-1)) by the end of step s (incremental step start)
+    double* dinode;          // [n_pad] slot S minus slot S - 1 of inode, written with slot S (the load
+                             // change the incremental step start adds); nodes without loads stay 0
     int32_t* pwl_cur;        // [n_src] breakpoint segment of each source's latest evaluation (a hint:
                              // checked before use, any value is safe)
 };

@@ -561,13 +561,14 @@ __device__ double sweep_colour_tma(const DevGrid& g, const WarpCache* wc, TmaWar
 // Phase A of an incremental step (RC, explicit form, mixed precision, corrections in
 // the packing order) streams its operands: no neighbour is read.  The warp walks its
 // nodes in chunks of kRhsChunk; the Tensor Memory Accelerator copies the contiguous
-// operands of chunk j + 1 (v(s-1), v(s-2), C/h, both load slots, the carried residual
+// operands of chunk j + 1 (v(s-1), v(s-2), C/h, the load change, the carried residual
 // and M (v(s-1) - v(s-2)) in FP64, 1/D in FP32) into one stage of the warp's TMA area
 // while chunk j is computed from the other, so the FP64 arithmetic of one chunk
 // overlaps the memory traffic of the next.  Each node takes exactly the operations of
-// phase_rhs's incremental branch, so the results are bit-identical.
+// phase_rhs's incremental branch, with the load change Ic - Ip read as formed when the
+// load slot was written (the same two operands), so the results are bit-identical.
 constexpr int kRhsChunk = 64;
-constexpr int kRhsArrays = 7;                                   // FP64 operands per node
+constexpr int kRhsArrays = 6;                                   // FP64 operands per node
 constexpr int kRhsStageBytes = kRhsChunk * (8 * kRhsArrays + 4);
 static_assert(kRhsStageBytes <= kStageElems * 4, "a step-start chunk fits one TMA stage");
 
@@ -578,11 +579,9 @@ __device__ __forceinline__ double phase_rhs_inc_tma(const DevGrid& g, const Warp
     const double* vl = vbuf(st, vL);
     const double* vp = vbuf(st, vP);
     double* vf = vbuf(st, vF);
-    const double* Ic = st.inode + (sabs & 1) * (long long)g.n_pad;
-    const double* Ip = st.inode + ((sabs - 1) & 1) * (long long)g.n_pad;
     float* dz = dbuf<float>(st, dsel);
     constexpr unsigned kB8 = kRhsChunk * 8, kB4 = kRhsChunk * 4;
-    const unsigned bytes = kB8 * (extrap ? 7u : 6u) + kB4;
+    const unsigned bytes = kB8 * (extrap ? 6u : 5u) + kB4;
     auto issue = [&](long long n0, int sb) {
         unsigned char* buf = sb ? tw.stage[1] : tw.stage[0];   // no dynamic index: tw stays in registers
         unsigned long long* bar = tw.bar + sb;
@@ -590,11 +589,10 @@ __device__ __forceinline__ double phase_rhs_inc_tma(const DevGrid& g, const Warp
         bulk_g2s(buf + 0 * kB8, vl + n0, kB8, bar);
         bulk_g2s(buf + 1 * kB8, vp + n0, kB8, bar);
         bulk_g2s(buf + 2 * kB8, g.ch + n0, kB8, bar);
-        bulk_g2s(buf + 3 * kB8, Ic + n0, kB8, bar);
-        bulk_g2s(buf + 4 * kB8, Ip + n0, kB8, bar);
-        bulk_g2s(buf + 5 * kB8, st.r64 + n0, kB8, bar);
-        if (extrap) bulk_g2s(buf + 6 * kB8, st.md + n0, kB8, bar);
-        bulk_g2s(buf + 7 * kB8, g.invD32 + n0, kB4, bar);
+        bulk_g2s(buf + 3 * kB8, st.dinode + n0, kB8, bar);
+        bulk_g2s(buf + 4 * kB8, st.r64 + n0, kB8, bar);
+        if (extrap) bulk_g2s(buf + 5 * kB8, st.md + n0, kB8, bar);
+        bulk_g2s(buf + 6 * kB8, g.invD32 + n0, kB4, bar);
     };
     float mon = 0.f;
     for (int c = 0; c < g.ncol; ++c) {
@@ -628,21 +626,20 @@ __device__ __forceinline__ double phase_rhs_inc_tma(const DevGrid& g, const Warp
             const double2 a = *reinterpret_cast<const double2*>(buf + 0 * kB8 + q * 8);
             const double2 pp = *reinterpret_cast<const double2*>(buf + 1 * kB8 + q * 8);
             const double2 ch = *reinterpret_cast<const double2*>(buf + 2 * kB8 + q * 8);
-            const double2 ic = *reinterpret_cast<const double2*>(buf + 3 * kB8 + q * 8);
-            const double2 ip = *reinterpret_cast<const double2*>(buf + 4 * kB8 + q * 8);
-            const double2 rr = *reinterpret_cast<const double2*>(buf + 5 * kB8 + q * 8);
+            const double2 di = *reinterpret_cast<const double2*>(buf + 3 * kB8 + q * 8);
+            const double2 rr = *reinterpret_cast<const double2*>(buf + 4 * kB8 + q * 8);
             double2 md = make_double2(0.0, 0.0);
-            if (extrap) md = *reinterpret_cast<const double2*>(buf + 6 * kB8 + q * 8);
-            const float2 iD = *reinterpret_cast<const float2*>(buf + 7 * kB8 + q * 4);
+            if (extrap) md = *reinterpret_cast<const double2*>(buf + 5 * kB8 + q * 8);
+            const float2 iD = *reinterpret_cast<const float2*>(buf + 6 * kB8 + q * 4);
             if (extrap && th != 1.0f) {
                 md.x *= th;
                 md.y *= th;
             }
             // the incremental branch of phase_rhs, node by node
-            auto node = [&](double av, double pv, double cv, double icv, double ipv, double rv, double mdv,
-                            float iv, double& vw, double& r, float& r32) {
+            auto node = [&](double av, double pv, double cv, double div, double rv, double mdv, float iv, double& vw,
+                            double& r, float& r32) {
                 vw = extrap ? warm_value(av, pv, th) : av;
-                double bj = cv * (av - pv) - (icv - ipv);
+                double bj = cv * (av - pv) - div;              // div = Ic - Ip, formed when slot S was written
                 bj += rv - mdv;
                 r = bj;
                 r32 = (float)r;
@@ -650,8 +647,8 @@ __device__ __forceinline__ double phase_rhs_inc_tma(const DevGrid& g, const Warp
             };
             double vw0, vw1, r0, r1;
             float r320, r321;
-            node(a.x, pp.x, ch.x, ic.x, ip.x, rr.x, md.x, iD.x, vw0, r0, r320);
-            node(a.y, pp.y, ch.y, ic.y, ip.y, rr.y, md.y, iD.y, vw1, r1, r321);
+            node(a.x, pp.x, ch.x, di.x, rr.x, md.x, iD.x, vw0, r0, r320);
+            node(a.y, pp.y, ch.y, di.y, rr.y, md.y, iD.y, vw1, r1, r321);
             __syncwarp();   // stage sb is read by every lane before it is refilled
             if (!extrap || th != 1.0f) *reinterpret_cast<double2*>(st.md + i) = md;
             *reinterpret_cast<double2*>(vf + i) = make_double2(vw0, vw1);
@@ -1175,12 +1172,16 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
 #pragma unroll
             for (int q = 0; q < kQ; ++q) {
                 if (a[q] >= 0) {
-                    if (flag) changed |= I[q] != prev[a[q]];
+                    const double p = prev[a[q]];
+                    if (flag) changed |= I[q] != p;
                     dst[a[q]] = I[q];
+                    st.dinode[a[q]] = I[q] - p;
                 }
                 if (b[q] >= 0) {
-                    if (flag) changed |= -I[q] != prev[b[q]];
+                    const double p = prev[b[q]];
+                    if (flag) changed |= -I[q] != p;
                     dst[b[q]] = -I[q];
+                    st.dinode[b[q]] = -I[q] - p;
                 }
             }
         }
@@ -1192,8 +1193,10 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
                 const double I = pwl_eval(g, (sid > 0 ? sid : -sid) - 1, tS, tk);
                 sum += sid > 0 ? I : -I;
             }
-            if (flag) changed |= sum != prev[i];
+            const double p = prev[i];
+            if (flag) changed |= sum != p;
             dst[i] = sum;
+            st.dinode[i] = sum - p;
         }
         if (flag && __any_sync(kFull, changed) && lane == 0) atomicOr(ctl.ld_flags + (S & 3), 1u);
     };
