@@ -120,13 +120,14 @@ typedef struct pg_options {
     int32_t blocks_per_sm;    /* 0 -> as many as fit */
     double barrier_timeout_s; /* device barrier time limit (0 -> 2 s) */
     int32_t debug_flags;      /* PG_DEBUG_* test hooks; 0 in production */
-    int32_t lattice_sweeps;   /* PG_PREC_MIXED on a lattice netlist (lat_nx/ny/nl given, <= 3 layers,
-                                 branches only between lattice neighbours): the inner solve becomes
-                                 column-block red-black SOR (each (x, y) column's layers solved exactly)
-                                 on shared-memory tiles with ghost zones, k exact block sweeps per device
-                                 barrier.  k > 0 (<= 7): that k; 0 (default): k = 3 for 2-3 layers and
-                                 for single-layer lattices of at most 200k nodes, else off; < 0: off
-                                 (neighbour-list point SOR) */
+    int32_t lattice_sweeps;   /* On a lattice netlist (lat_nx/ny/nl given, <= 3 layers, branches only
+                                 between lattice neighbours) the inner solve (FP32 in PG_PREC_MIXED, FP64
+                                 otherwise) becomes column-block red-black SOR (each (x, y) column's
+                                 layers solved exactly) on shared-memory tiles with ghost zones, k exact
+                                 block sweeps per device barrier.  k > 0 (<= 7): that k; 0 (default):
+                                 k = 3 for 2-3 layers and for single-layer lattices of at most 200k
+                                 nodes, in FP64 only for netlists of at most 8 lattices, else off;
+                                 < 0: off (neighbour-list point SOR) */
     int32_t jacobi;           /* 0 (default): coloured Gauss-Seidel / SOR inner sweeps (Eq. 16-17);
                                  1: damped Jacobi, every node updated from the previous iterate with
                                  omega <= 1 (default 1), one device barrier per sweep; no lattice solve */

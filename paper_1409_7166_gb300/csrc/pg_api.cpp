@@ -792,7 +792,11 @@ pg_status create_impl(const pg_netlist* nl, const pg_options* opt, std::unique_p
     g->threads = o.threads_per_block;
     g->mixed = o.precision == PG_PREC_MIXED;
     std::string why;
-    pg_status s = build_packed(nl, &g->P, &why, !o.jacobi ? o.lattice_sweeps : INT32_MIN, o.colouring);
+    // automatic lattice solve: in FP64 only for netlists of at most 8 lattices (one FP64 region
+    // fills an SM, and a batch of small grids runs faster on the point sweeps)
+    int32_t lat_policy = o.jacobi ? INT32_MIN : o.lattice_sweeps;
+    if (lat_policy == 0 && o.precision != PG_PREC_MIXED && nl && nl->n_lat > 8) lat_policy = -1;
+    pg_status s = build_packed(nl, &g->P, &why, lat_policy, o.colouring);
     if (s) { g_last_error = why; return s; }
     g->nc.from(nl);
     compute_dc_trivial(g.get());
