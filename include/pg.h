@@ -345,13 +345,21 @@ pg_status pg_async_stats(pg_grid* g, const void* dstats, pg_run_stats* stats);
  */
 pg_status pg_initial_conditions(pg_grid* g, double h, const double* vc0, const double* il0, int32_t on_host);
 
-/* One step (pg_transient with nsteps = 1); v_out (device, [n_nodes]) may be NULL. */
+/*
+ * One backward-Euler step: the body of Algorithm 1's time loop once (the RHS of
+ * Eq. 2 / Eq. 10 at t = (s + 1) h, the warm start from v(s), relaxation by
+ * Eq. 16-17 to the certified per-step target, the inductor update of Eq. 10).
+ * Same as pg_transient with nsteps = 1; v_out (device, [n_nodes]) may be NULL.
+ * Errors as pg_transient.
+ */
 pg_status pg_step(pg_grid* g, double h, double* v_out, pg_run_stats* stats);
 
 /*
  * Solve M x = b once for the assembled h (b, x: device, [n_nodes], caller
  * numbering) to the absolute error target `tol` (V-like units of x), starting
- * from x = 0.  Exposes the relaxation kernel on its own.  b is read on the
+ * from x = 0: the relaxation of Section IV (Eq. 14-17, with the coefficients of
+ * Eq. 14 for this h) on its own, outside the time loop, under the same
+ * certified stopping rule as a step.  b is read on the
  * grid's stream; the first call allocates one [n_nodes]-sized device buffer that
  * the grid keeps.  tol must exceed kappa * 1e-13 (the rounding allowance of the
  * stopping rule), else PG_ERR_INVALID_ARG.
