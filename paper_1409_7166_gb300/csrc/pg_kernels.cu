@@ -1446,7 +1446,12 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
             double x4[4];
             int o4[4];
             ld4(vnew + i4, x4);
-            ldg4(g.orig + i4, o4);
+            if (g.natural) {               // natural order: node i is caller node i, padding at the end
+#pragma unroll
+                for (int j = 0; j < 4; ++j) o4[j] = i4 + j < g.n_real ? i4 + j : -1;
+            } else {
+                ldg4(g.orig + i4, o4);
+            }
             if (rp.v_perm_all) st4(rp.v_perm_all + (long long)sl * g.n_pad + i4, x4);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
