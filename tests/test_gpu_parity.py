@@ -213,6 +213,49 @@ def test_update_sources_new_scenario(B):
     assert np.max(np.abs(V - Vo[1:])) <= TOL_V
 
 
+def _jump_waveforms(net, h, seed):
+    """Five-point waveforms on the recipe's load sites: a zero-length segment (a jump) at
+    the rise and another at the fall, every breakpoint on an exact step time k h."""
+    rng = np.random.default_rng(seed)
+    m = len(net.i_ptr) - 1
+    ptr = np.arange(0, 5 * m + 1, 5, dtype=np.int64)
+    t = np.empty(5 * m)
+    v = np.empty(5 * m)
+    for e in range(m):
+        peak = float(np.max(np.abs(net.i_v[net.i_ptr[e]:net.i_ptr[e + 1]]))) * rng.uniform(0.5, 1.5)
+        ka = int(rng.integers(1, 60))
+        kb = ka + int(rng.integers(1, 8))
+        kc = kb + int(rng.integers(1, 8))
+        t[5 * e:5 * e + 5] = [ka * h, ka * h, kb * h, kc * h, kc * h]
+        v[5 * e:5 * e + 5] = [0.0, peak, 0.5 * peak, 0.3 * peak, 0.0]
+    return pgsynth.Netlist(**{**net.__dict__, "i_ptr": ptr, "i_t": t, "i_v": v})
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_pwl_jumps_and_breakpoints_on_step_times(B, precision):
+    """Breakpoints hit exactly by step times and zero-length segments: the held value on
+    each side of a jump follows the PWL reading of Section II-A on both sides (left value
+    at the jump's time, the next segment just after)."""
+    net = _jump_waveforms(pgsynth.config1(nx=43, ny=39), pgsynth.config1().meta["h"], 5)
+    check_against_oracle(B, net, net.meta["h"], 90, precision)
+
+
+def test_update_sources_new_breakpoints(B):
+    """New breakpoint times and values through pg_update_sources: the device evaluation
+    (segment cursors, time keys, slopes) follows the new waveforms from the next run."""
+    base = pgsynth.config1(nx=43, ny=39)
+    h = base.meta["h"]
+    net1, net2 = _jump_waveforms(base, h, 5), _jump_waveforms(base, h, 6)
+    Vo, _ = transient.transient(net2, h, 90)
+    with B.Grid(net1, precision=1) as g:
+        B.pg_transient(g.handle, h, 40)              # cursors advanced on the first waveforms
+        B.pg_update_sources(g.handle, net2.i_t, net2.i_v)
+        B.pg_reset(g.handle)
+        V = np.zeros((90, net2.n_nodes))
+        B.pg_transient(g.handle, h, 90, v_all=V)
+    assert np.max(np.abs(V - Vo[1:])) <= TOL_V
+
+
 def test_not_converged_and_timeout_are_reported(B):
     net = pgsynth.config0(nx=30, ny=30)
     h = net.meta["h"]
