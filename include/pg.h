@@ -82,7 +82,7 @@ typedef struct pg_netlist {
     int64_t n_c; const int32_t* c_a; const int32_t* c_b; const double* c_val;
     int64_t n_l; const int32_t* l_a; const int32_t* l_b; const double* l_val;
     int64_t n_i; const int32_t* i_a; const int32_t* i_b;
-    const int64_t* i_ptr;              /* [n_i + 1] */
+    const int64_t* i_ptr;              /* [n_i + 1]; i_ptr[n_i] (all breakpoints) <= 2^31 - 2 */
     const double* i_t; const double* i_v;
     int32_t lat_nx, lat_ny, lat_nl;
     int32_t n_lat;

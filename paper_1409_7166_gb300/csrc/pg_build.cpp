@@ -4,6 +4,7 @@
 // Nothing here depends on the time step h; per-h coefficients are assembled
 // in pg_api.cu from the merged neighbour lists built here.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -414,6 +415,10 @@ pg_status build_packed(const pg_netlist* nl, Packed* P, std::string* why, int32_
         }
     }
     if (nl->n_i) {
+        if (nl->i_ptr[nl->n_i] > (int64_t)INT32_MAX - 1) {   // the device indexes breakpoints in 32 bits
+            *why = "too many PWL breakpoints (at most 2^31 - 2 in one netlist)";
+            return PG_ERR_INVALID_ARG;
+        }
         P->pwl_ptr.assign(nl->i_ptr, nl->i_ptr + nl->n_i + 1);
         P->pwl_t.assign(nl->i_t, nl->i_t + nl->i_ptr[nl->n_i]);
         P->pwl_v.assign(nl->i_v, nl->i_v + nl->i_ptr[nl->n_i]);
