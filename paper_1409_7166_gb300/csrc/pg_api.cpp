@@ -401,6 +401,7 @@ RunParams pg::base_params(const pg_grid* g) {
     rp.three_level = g->opt.form == PG_FORM_THREE_LEVEL;
     rp.jacobi = g->opt.jacobi;
     rp.inc_start = g->inc_ok && g->have_prev;
+    rp.prev_outer = g->last_outer;
     return rp;
 }
 
@@ -433,6 +434,7 @@ pg_status run(pg_grid* g, const RunParams& rp, double* stats, float* ms) {
     // the final residual and M d of an explicit transient carry into the next launch
     g->inc_ok = err == 0 && rp.mode == kModeTransient && !rp.three_level && stats[kStatSteps] >= 1.0 &&
                 stats[kStatSteps] == (double)rp.nsteps;
+    if (g->inc_ok) g->last_outer = (int32_t)stats[kStatLastOuter];
     if (err == PG_ERR_TIMEOUT) { g_last_error = "device barrier timed out"; return PG_ERR_TIMEOUT; }
     if (err == PG_ERR_NOT_CONVERGED) { g_last_error = "relaxation did not converge"; return PG_ERR_NOT_CONVERGED; }
     if (err != 0) { g_last_error = "device error"; return PG_ERR_CUDA; }
@@ -1311,6 +1313,7 @@ pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* o
     double* ck_md = sc.get<double>((size_t)nseg * np);
     if (!ck_r || !ck_md) return PG_ERR_OOM;
     std::vector<char> ck_inc(nseg, 0);
+    std::vector<int32_t> ck_outer(nseg, 0);
     double* mu_l = nl ? sc.get<double>(nl) : nullptr;                   // inductor multipliers
     double* acc_L = nl ? sc.get<double>(nl) : nullptr;
     if (!ck_v || !ck_vp || !part || !vseg || !lam || !lam_next || !rhs || !acc_slot || !acc_lv || !acc_l ||
@@ -1346,6 +1349,7 @@ pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* o
         CK(cudaMemcpyAsync(ck_r + (size_t)k * np, g->ds.r64, np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
         CK(cudaMemcpyAsync(ck_md + (size_t)k * np, g->ds.md, np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
         ck_inc[k] = g->inc_ok;
+        ck_outer[k] = g->last_outer;
         RunParams rp = base_params(g);
         rp.mode = kModeTransient;
         rp.nsteps = len;
@@ -1397,6 +1401,7 @@ pg_status pg_adjoint(pg_grid* g, double h, int32_t nsteps, const pg_objective* o
         CK(cudaMemcpyAsync(g->ds.r64, ck_r + (size_t)k * np, np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
         CK(cudaMemcpyAsync(g->ds.md, ck_md + (size_t)k * np, np * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
         g->inc_ok = ck_inc[k] != 0;
+        g->last_outer = ck_outer[k];
         RunParams rp = base_params(g);
         rp.mode = kModeTransient;
         rp.nsteps = len;

@@ -95,6 +95,7 @@ struct pg_grid {
     int vL = 0, vP = 1;
     bool have_prev = false;
     bool inc_ok = false;          // r64 and md hold the last step's final residual and M d (see run)
+    int32_t last_outer = 0;       // outer passes of that step (a step after more than 4 starts in full)
     // largest certified error bound (V) of the state the series started from (the DC solve;
     // 0 for a state the caller set) and of every step since: the accumulated error of the
     // current state is at most kacc times this

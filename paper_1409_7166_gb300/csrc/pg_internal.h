@@ -222,6 +222,7 @@ enum Stat : int {
     kStatSteps = 0, kStatSweeps, kStatMaxSweeps, kStatOuter, kStatMaxOuter,
     kStatMaxBound, kStatFailedStep, kStatLastR,
     kStatTimeA, kStatTimeInner, kStatTimeOuter, kStatTimePost,   // ns on block 0's clock
+    kStatLastOuter,                                              // outer passes of the last step
     kStatCount
 };
 
@@ -266,6 +267,7 @@ struct RunParams {
     int32_t three_level;      // 1: right-hand side of Eq. 11 (state v(s-1), v(s-2); no i_l)
     int32_t jacobi;           // 1: damped-Jacobi inner sweeps instead of coloured SOR
     int32_t inc_start;        // 1: the residual and M d of the previous launch's last step are current
+    int32_t prev_outer;       // outer passes of the step before the launch's first one (inc_start)
 };
 
 }  // namespace pg

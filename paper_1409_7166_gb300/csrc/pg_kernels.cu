@@ -34,6 +34,7 @@
 #endif
 constexpr int kSweepUnroll = PG_SWEEP_UNROLL;
 constexpr int kIncPeriod = 16;        // full recompute of the step-start residual every 16 steps
+constexpr int kIncMaxOuter = 4;       // ... and after any step that needed more outer passes
 
 namespace pg {
 
@@ -1034,6 +1035,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
     long long tot_sweeps = 0, tot_outer = 0, steps_done = 0;
     int max_sw = 0, max_out = 0;
     double max_bound_R = 0.0, last_R = 0.0;
+    int last_outer = rp.prev_outer;   // outer passes of the previous step (same in every block)
     // time per phase, read by block 0 right after the barriers that end the phases
     double t_phase[4] = {0.0, 0.0, 0.0, 0.0};
     long long t_mark = lead ? global_ns() : 0ll;
@@ -1058,6 +1060,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
             ctl.stats[kStatMaxBound] = max_bound_R;
             ctl.stats[kStatFailedStep] = (double)failed;
             ctl.stats[kStatLastR] = last_R;
+            ctl.stats[kStatLastOuter] = (double)last_outer;
         }
     };
     auto fail = [&](long long step) {
@@ -1236,7 +1239,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
         // except every kIncPeriod-th step (by absolute index, so chunked runs repeat a single
         // launch exactly), which recomputes it (bounds the drift of rounding)
         const bool inc = rp.mode == kModeTransient && !rp.three_level && have_prev && st.md != nullptr &&
-                         (sl > 0 || rp.inc_start) && (sabs % kIncPeriod) != 0;
+                         (sl > 0 || rp.inc_start) && (sabs % kIncPeriod) != 0 && last_outer <= kIncMaxOuter;
         int dsel = 0;
         if (sl > 0) { finalize_vmin(sl - 1); finalize_comp(sl - 1); }
 
@@ -1529,6 +1532,7 @@ __global__ void __launch_bounds__(256, PG_MIN_BLOCKS) persistent_kernel(DevGrid 
         max_sw = max(max_sw, sweeps); max_out = max(max_out, outer);
         max_bound_R = fmax(max_bound_R, R);
         last_R = R;
+        last_outer = outer;
         ++steps_done;
         // rotate: the new state becomes the latest
         vP = vL; vL = vF; vF = 3 - vL - vP;

@@ -374,6 +374,31 @@ def test_load_aware_warm_start(B, precision):
         assert torch.equal(torch.cat(parts), one)
 
 
+def test_full_step_start_after_many_outer_passes(B):
+    """The incremental step start carries the previous step's final residual, whose rounding
+    drift grows with every outer pass; a step that needed more than four passes is followed
+    by a full recompute.  Weak inner solves (inner_reduction 0.5) force such steps: the run
+    still matches the oracle, and a run split over launches (which carries the pass count)
+    repeats the single launch bit for bit."""
+    net = pgsynth.config1(nx=43, ny=39)
+    h, S = net.meta["h"], 80
+    _, st = check_against_oracle(B, net, h, S, 1, inner_reduction=0.5)
+    assert st.max_outer_step > 4, st.max_outer_step
+    with B.Grid(net, precision=1, inner_reduction=0.5) as g:
+        B.pg_set_stream(g.handle, torch.cuda.current_stream().cuda_stream)
+        one = torch.empty(S, dtype=torch.float64, device="cuda")
+        B.pg_transient(g.handle, h, S, vmin=one)
+        B.pg_reset(g.handle)
+        parts = []
+        for a in range(0, S, 9):
+            k = min(9, S - a)
+            v = torch.empty(k, dtype=torch.float64, device="cuda")
+            B.pg_transient(g.handle, h, k, vmin=v)
+            parts.append(v)
+        torch.cuda.synchronize()
+        assert torch.equal(torch.cat(parts), one)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("recipe", ["config0_37x29", "config1_33x27x3", "config2_24x19x2"])
 def test_four_colour_order(B, recipe, precision):
